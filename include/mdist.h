@@ -1,0 +1,214 @@
+/*
+ * mdist.h -- C-ABI of the GB300 minimum-distance library (libmdist.so).
+ *
+ * Computes the minimum distance d of a binary linear [n, k] code by the
+ * Brouwer-Zimmerman enumeration (Hernando, Igual, Quintana-Orti, arXiv:1603.06757,
+ * §2 and Alg. 1): the generator matrix G is split into disjoint information sets
+ * S_1..S_m with matrices Gamma_j = (I | A_j) (the last ones possibly of rank
+ * r_j < k); for g = 1, 2, ... every c in F2^k with wt(c) = g is expanded to the
+ * codeword c * Gamma_j and weighed, the upper bound U is the least weight seen and
+ * the lower bound is L(g) = sum_j max(0, g + 1 - (k - r_j)); the run stops when
+ * L >= U and then d = U.  The enumeration runs in hand-written sm_103a CUDA kernels.
+ *
+ * Conventions (all entry points):
+ *  - Bit matrices are rows of uint64 words, LSB first: bit i of a row is bit (i & 63)
+ *    of word (i >> 6).  Bits at columns >= n must be zero.
+ *  - Set indices j are 0-based (the paper counts from 1).  Combination ranks are
+ *    lexicographic over the rows of Gamma_j, 0-based (§3.1-§3.2 order).
+ *  - Host pointers are read or written only during the call; the caller keeps
+ *    ownership.  Everything behind an mdist_code handle is owned by the library and
+ *    released by mdist_free().
+ *  - Device memory: the library allocates through opts->dev_alloc / dev_free when
+ *    given (e.g. a PyTorch caching allocator), else with cudaMalloc / cudaFree.
+ *  - Work is issued on the stream given to mdist_prepare (NULL = legacy default
+ *    stream).  Calls return after their results are on the host.
+ *  - Return value: MDIST_OK (0) or a negative MDIST_E* code; no exception or signal
+ *    crosses the ABI.  mdist_strerror() names a code.
+ *  - Limits: 1 <= k <= 64, k < n <= 512, at most MDIST_MAX_SETS information sets
+ *    (set formation stops there; fewer sets only weaken L, never the result).
+ *  - A handle is not thread-safe: one call at a time per handle.
+ */
+#ifndef MDIST_H
+#define MDIST_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MDIST_MAX_K 64
+#define MDIST_MAX_N 512
+#define MDIST_MAX_SETS 64
+
+enum {
+    MDIST_OK = 0,
+    MDIST_EINVAL = -1,     /* bad argument or shape (n <= k, k > 64, n > 512, bad W, bits past n) */
+    MDIST_ERANK = -2,      /* rank(G) < k */
+    MDIST_ENOMEM = -3,     /* host or device allocation failed */
+    MDIST_ECUDA = -4,      /* a CUDA runtime call failed (no device, launch error, ...) */
+    MDIST_ETIMEOUT = -5,   /* a bounded device wait ran out */
+    MDIST_ECANCELLED = -6, /* request cancelled */
+    MDIST_ERANGE = -7,     /* C(k, g) >= 2^54: the level is beyond the device key range */
+    MDIST_ESTATE = -8,     /* state blob does not belong to this code / is corrupt */
+    MDIST_EAGAIN = -9      /* resource busy (serving queue full) */
+};
+
+typedef void *(*mdist_alloc_fn)(size_t bytes, void *ctx);
+typedef void (*mdist_free_fn)(void *ptr, void *ctx);
+
+/* Options; a zeroed struct (or NULL) means defaults. */
+typedef struct {
+    int check_per_matrix;    /* 0: check L >= U after each level (Alg. 1, line 7);
+                                1: after each (g, j) unit, with
+                                L = sum_{i<=j} t_i(g) + sum_{i>j} t_i(g-1),
+                                t_i(h) = max(0, h + 1 - (k - r_i)) (the bound rises
+                                "one after each Gamma_j", §2). */
+    int max_sets;            /* 0 = MDIST_MAX_SETS */
+    int blocks_per_sm;       /* enumerator CTAs per SM; 0 = occupancy limit */
+    int reserved0;
+    long long timeout_cycles;/* bound for device-side waits (batched / serving); 0 = default */
+    mdist_alloc_fn dev_alloc;/* optional device allocator */
+    mdist_free_fn dev_free;
+    void *alloc_ctx;
+} mdist_options;
+
+/* Witness key: the least (weight, g, j, rank) over the enumerated units (a total
+ * order, so the witness is unique).  weight = INT32_MAX means "none". */
+typedef struct {
+    int32_t weight;
+    int32_t g;
+    int32_t j;
+    int32_t reserved;
+    uint64_t rank;
+} mdist_key;
+
+typedef struct {
+    int32_t g_final, j_final; /* last unit enumerated */
+    int32_t m;                /* number of information sets */
+    int32_t L_final, U_final;
+    int32_t launches;         /* enumerator kernel launches */
+    int32_t ranks[MDIST_MAX_SETS];
+    uint64_t combos[MDIST_MAX_K + 1][MDIST_MAX_SETS]; /* combinations enumerated per (g, j) */
+    uint64_t total_combos;
+    double seconds;           /* host wall time inside mdist_run / mdist_min_distance */
+    double kernel_ms;         /* summed CUDA-event time of the enumerator launches */
+    uint64_t h2d_bytes;       /* host-to-device bytes copied by mdist_prepare and the run */
+    uint64_t d2h_bytes;       /* device-to-host bytes copied by the run */
+} mdist_stats;
+
+typedef struct mdist_code mdist_code; /* opaque */
+
+/* Split G (k rows of words_per_row uint64, host memory) into disjoint information
+ * sets (§2): for j = 1, 2, ... Gauss-Jordan on the ORIGINAL G over the columns not
+ * used by earlier sets, in ascending column order; a column is a pivot iff it is
+ * independent of the set's earlier pivots; the pivot row is the lowest row at or
+ * below the current pivot position with a 1 there.  Gamma_j row i < r_j carries the
+ * i-th pivot; rows r_j..k-1 are the remaining rows.  Sets are formed while unused
+ * columns of nonzero rank remain.  The packed Gamma_j are copied to the device.
+ * `opts` may be NULL; it is copied.  `cuda_stream` is a cudaStream_t or NULL.
+ * On success *out owns the handle. */
+int mdist_prepare(const uint64_t *G, int n, int k, int words_per_row, const mdist_options *opts,
+                  void *cuda_stream, mdist_code **out);
+
+/* Information sets of a prepared code (§2): *m, ranks[m], pivcols[m*k] (-1 past
+ * r_j), gammas[m*k*words_per_row] (Gamma_j = T_j * G) and transforms[m*k] (row r of
+ * T_j as a k-bit mask of G rows).  Any output pointer except m may be NULL. */
+int mdist_info_sets(const mdist_code *code, int *m, int *ranks, int32_t *pivcols, uint64_t *gammas,
+                    uint64_t *transforms);
+
+/* Enumerate unit(s) (g, j) of Alg. 1 on the GPU: every c with wt(c) = g, codeword
+ * c * Gamma_j, weight (§2; §3: all combinations of g rows).  j = -1 runs every set,
+ * one unit after the other.  Candidates are codewords of weight <= *U_inout; on
+ * return *U_inout = min(*U_inout, least candidate weight) and *key_inout is the
+ * least of itself and the candidates' keys (weight, g, j, rank).  combos_out (may be
+ * NULL) receives the number of combinations enumerated, one entry per unit run
+ * ([m] for j = -1, else [1]).  Does not change the state used by mdist_run. */
+int mdist_enumerate_level(mdist_code *code, int g, int j, int *U_inout, mdist_key *key_inout,
+                          uint64_t *combos_out);
+
+/* Debug / parity form of one unit: the full weight histogram hist[0..n] of the
+ * C(k, g) codewords c * Gamma_j (weights over all n columns) and their count. */
+int mdist_unit_histogram(mdist_code *code, int g, int j, uint64_t *hist, uint64_t *combos_out);
+
+/* Advance Alg. 1 by at most max_units (g, j) units (max_units <= 0: until the end).
+ * *finished = 1 once L >= U or every level is done. */
+int mdist_run(mdist_code *code, int max_units, int *finished);
+
+/* Restart Alg. 1 from its first unit (L := 1, U := n - k + 1, counters cleared); the
+ * information sets and device rows are kept. */
+int mdist_reset(mdist_code *code);
+
+/* Result of a finished run: d, witness[words_per_row] (a codeword of weight d, in
+ * the original column order), message[1] (the k-bit message with message*G =
+ * witness), key and stats.  Any output except d may be NULL.  MDIST_EAGAIN if the
+ * run has not finished. */
+int mdist_result(const mdist_code *code, int *d, uint64_t *witness, uint64_t *message, mdist_key *key,
+                 mdist_stats *stats);
+
+/* mdist_run to the end, then mdist_result. */
+int mdist_min_distance(mdist_code *code, int *d, uint64_t *witness, uint64_t *message, mdist_key *key,
+                       mdist_stats *stats);
+
+/* Checkpoint / resume of the Alg. 1 state after the last completed unit (next unit,
+ * U, L, key, counters).  save: if buf is NULL or *len is too small, *len is set to
+ * the size needed and MDIST_EINVAL is returned.  load: MDIST_ESTATE if the blob was
+ * made for another code or options. */
+int mdist_state_save(const mdist_code *code, void *buf, size_t *len);
+int mdist_state_load(mdist_code *code, const void *buf, size_t len);
+
+/* Change the stream later calls on this handle use. */
+int mdist_set_stream(mdist_code *code, void *cuda_stream);
+
+void mdist_free(mdist_code *code);
+const char *mdist_strerror(int err);
+
+/* SM count and the maximum SM clock (kHz) of the current device, for roofline
+ * arithmetic. */
+int mdist_device_info(int *sm_count, int *max_sm_clock_khz, int *cc_major, int *cc_minor);
+
+/* Instruction-throughput probe on the current device, for roofline arithmetic:
+ * which = 0: 32-bit POPC, 1: 3-input XOR (LOP3), 2: enumerator inner step (XOR + POPC
+ * over 4 words, sum, running min) with operands in registers.  One 1024-thread CTA
+ * per SM, `iters` loop trips; *ops_per_clock_per_sm = operations (or codeword steps)
+ * retired per SM per clock (clock64), *seconds = launch time.  Allocates 64 B + 8 B
+ * per SM of device memory for its duration. */
+int mdist_microbench(int which, int iters, double *ops_per_clock_per_sm, double *seconds);
+
+/* ---- host-only entry points (no CUDA call; usable without a GPU) ---------------- */
+
+/* The information-set partition of mdist_prepare alone (same reading of §2, same
+ * outputs as mdist_info_sets), computed on the host.  max_sets <= 0 means
+ * MDIST_MAX_SETS.  MDIST_ERANK if rank(G) < k. */
+int mdist_partition_host(const uint64_t *G, int n, int k, int words_per_row, int max_sets, int *m, int *ranks,
+                         int32_t *pivcols, uint64_t *gammas, uint64_t *transforms);
+
+/* Row layout the enumerator reads for set j (0-based): a full-rank set stores its
+ * n - k non-pivot columns (every codeword of a weight-g combination has exactly g
+ * ones on the pivots, §2's identity block); a set of rank < k stores all n columns.
+ * words[k * *nwords] receives the rows as 32-bit words (capacity k * 16). */
+int mdist_debug_set_rows(const uint64_t *G, int n, int k, int words_per_row, int j, int *full_rank, int *n_bits,
+                         int *nwords, uint32_t *words);
+
+/* The combination indexing the kernels run, evaluated on the host:
+ *  unrank_colex: t-subset of {0..kh-1} (kh <= 32) with colex rank `rank`, as a mask;
+ *  next_colex:   the next subset of the same size in colex order;
+ *  lexrank:      lexicographic rank (§3.1 order) of a g-subset of {0..k-1}. */
+int mdist_debug_unrank_colex(int kh, int t, uint32_t rank, uint32_t *mask);
+int mdist_debug_next_colex(uint32_t m, uint32_t *next);
+int mdist_debug_lexrank(uint64_t mask, int k, int g, uint64_t *rank);
+
+/* Work plan of one level (k rows, level g, nwords 32-bit words per row): the product
+ * blocks (i-subsets of rows [0, ceil(k/2)) times (g-i)-subsets of the rest), 7 values
+ * per block in blocks[]: lane_half, lane_t, walk_t, lane_n, walk_n, walk_chunks,
+ * tile_begin (capacity 34 blocks); the tile count and the tile shape.  MDIST_ERANGE
+ * if C(k, g) >= 2^54. */
+int mdist_debug_level_plan(int k, int g, int nwords, int *nblocks, uint64_t *blocks, uint64_t *total_tiles,
+                           int *lane_chunk, int *walk_chunk);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MDIST_H */

@@ -1,0 +1,150 @@
+"""ctypes declarations of libmdist.so (mirror of include/mdist.h).
+
+Loading fails loudly when the library has not been built: there is no CPU fallback.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libmdist.so")
+
+MAX_K = 64
+MAX_N = 512
+MAX_SETS = 64
+
+OK = 0
+EINVAL = -1
+ERANK = -2
+ENOMEM = -3
+ECUDA = -4
+ETIMEOUT = -5
+ECANCELLED = -6
+ERANGE = -7
+ESTATE = -8
+EAGAIN = -9
+
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
+
+
+class Options(ctypes.Structure):
+    _fields_ = [
+        ("check_per_matrix", ctypes.c_int),
+        ("max_sets", ctypes.c_int),
+        ("blocks_per_sm", ctypes.c_int),
+        ("reserved0", ctypes.c_int),
+        ("timeout_cycles", ctypes.c_longlong),
+        ("dev_alloc", ALLOC_FN),
+        ("dev_free", FREE_FN),
+        ("alloc_ctx", ctypes.c_void_p),
+    ]
+
+
+class Key(ctypes.Structure):
+    _fields_ = [
+        ("weight", ctypes.c_int32),
+        ("g", ctypes.c_int32),
+        ("j", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
+        ("rank", ctypes.c_uint64),
+    ]
+
+    def as_tuple(self):
+        return (int(self.weight), int(self.g), int(self.j), int(self.rank))
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [
+        ("g_final", ctypes.c_int32),
+        ("j_final", ctypes.c_int32),
+        ("m", ctypes.c_int32),
+        ("L_final", ctypes.c_int32),
+        ("U_final", ctypes.c_int32),
+        ("launches", ctypes.c_int32),
+        ("ranks", ctypes.c_int32 * MAX_SETS),
+        ("combos", (ctypes.c_uint64 * MAX_SETS) * (MAX_K + 1)),
+        ("total_combos", ctypes.c_uint64),
+        ("seconds", ctypes.c_double),
+        ("kernel_ms", ctypes.c_double),
+        ("h2d_bytes", ctypes.c_uint64),
+        ("d2h_bytes", ctypes.c_uint64),
+    ]
+
+
+class MdistError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        self.code = code
+        super().__init__(f"{what}: {strerror(code)} ({code})")
+
+
+_lock = threading.Lock()
+_lib = None
+
+P64 = ctypes.POINTER(ctypes.c_uint64)
+PI = ctypes.POINTER(ctypes.c_int)
+PI32 = ctypes.POINTER(ctypes.c_int32)
+PCODE = ctypes.c_void_p
+
+# name -> (restype, argtypes): every entry point of include/mdist.h
+SIGNATURES = {
+    "mdist_prepare": (ctypes.c_int, [P64, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(Options),
+                                     ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]),
+    "mdist_info_sets": (ctypes.c_int, [PCODE, PI, PI, PI32, P64, P64]),
+    "mdist_enumerate_level": (ctypes.c_int, [PCODE, ctypes.c_int, ctypes.c_int, PI, ctypes.POINTER(Key), P64]),
+    "mdist_unit_histogram": (ctypes.c_int, [PCODE, ctypes.c_int, ctypes.c_int, P64, P64]),
+    "mdist_run": (ctypes.c_int, [PCODE, ctypes.c_int, PI]),
+    "mdist_reset": (ctypes.c_int, [PCODE]),
+    "mdist_result": (ctypes.c_int, [PCODE, PI, P64, P64, ctypes.POINTER(Key), ctypes.POINTER(Stats)]),
+    "mdist_min_distance": (ctypes.c_int, [PCODE, PI, P64, P64, ctypes.POINTER(Key), ctypes.POINTER(Stats)]),
+    "mdist_state_save": (ctypes.c_int, [PCODE, ctypes.c_void_p, ctypes.POINTER(ctypes.c_size_t)]),
+    "mdist_state_load": (ctypes.c_int, [PCODE, ctypes.c_void_p, ctypes.c_size_t]),
+    "mdist_set_stream": (ctypes.c_int, [PCODE, ctypes.c_void_p]),
+    "mdist_free": (None, [PCODE]),
+    "mdist_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+    "mdist_device_info": (ctypes.c_int, [PI, PI, PI, PI]),
+    "mdist_microbench": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                        ctypes.POINTER(ctypes.c_double)]),
+    "mdist_partition_host": (ctypes.c_int, [P64, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, PI, PI,
+                                            PI32, P64, P64]),
+    "mdist_debug_set_rows": (ctypes.c_int, [P64, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, PI, PI, PI,
+                                            ctypes.POINTER(ctypes.c_uint32)]),
+    "mdist_debug_unrank_colex": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_uint32,
+                                                ctypes.POINTER(ctypes.c_uint32)]),
+    "mdist_debug_next_colex": (ctypes.c_int, [ctypes.c_uint32, ctypes.POINTER(ctypes.c_uint32)]),
+    "mdist_debug_lexrank": (ctypes.c_int, [ctypes.c_uint64, ctypes.c_int, ctypes.c_int, P64]),
+    "mdist_debug_level_plan": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, PI, P64, P64, PI, PI]),
+}
+
+
+def lib():
+    """The loaded libmdist.so.  Raises ImportError if it has not been built."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise ImportError(
+                    f"{LIB_PATH} is missing: build the CUDA library first "
+                    "(python -c 'import __graft_entry__ as g; g.build()')")
+            handle = ctypes.CDLL(LIB_PATH)
+            for name, (res, args) in SIGNATURES.items():
+                fn = getattr(handle, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = handle
+    return _lib
+
+
+def strerror(code: int) -> str:
+    try:
+        return lib().mdist_strerror(code).decode()
+    except ImportError:
+        return "library not loaded"
+
+
+def check(code: int, what: str) -> None:
+    if code != OK:
+        raise MdistError(code, what)

@@ -1,0 +1,263 @@
+"""Python binding of libmdist.so: argument marshalling only.
+
+Every step of the computation (information sets on the host in C++, the level
+enumeration on the GPU) runs inside the library.  PyTorch supplies the device memory
+(through the library's allocator hooks, so the caching allocator owns it) and the
+CUDA stream.
+"""
+
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import _lib as L
+
+
+def _torch():
+    import torch
+
+    if not torch.cuda.is_available():
+        raise RuntimeError("mdist needs a CUDA device")
+    return torch
+
+
+class _TorchAllocator:
+    """Device allocations for the library, served by torch's caching allocator."""
+
+    def __init__(self, torch, device):
+        self.torch = torch
+        self.device = device
+        self.live = {}
+        self.alloc_cb = L.ALLOC_FN(self._alloc)
+        self.free_cb = L.FREE_FN(self._free)
+
+    def _alloc(self, nbytes, _ctx):
+        try:
+            t = self.torch.empty(max(int(nbytes), 1), dtype=self.torch.uint8, device=self.device)
+        except Exception:  # noqa: BLE001 - out of memory is reported to C as NULL
+            return None
+        ptr = t.data_ptr()
+        self.live[ptr] = t
+        return ptr
+
+    def _free(self, ptr, _ctx):
+        self.live.pop(int(ptr or 0), None)
+
+
+def as_packed(G, n: int) -> np.ndarray:
+    """(k, W) uint64, C-contiguous (the library's bit layout)."""
+    G = np.ascontiguousarray(np.asarray(G, dtype=np.uint64))
+    if G.ndim != 2 or G.shape[1] < (n + 63) // 64:
+        raise ValueError("G must be (k, >= ceil(n/64)) uint64")
+    return G
+
+
+def _p64(a):
+    return a.ctypes.data_as(L.P64)
+
+
+class Code:
+    """A prepared code: information sets on the host, packed Gamma_j on the device."""
+
+    def __init__(self, G, n: int, *, check_per_matrix: bool = False, max_sets: int = 0, blocks_per_sm: int = 0,
+                 stream=None, torch_alloc: bool = True):
+        torch = _torch()
+        self.n = int(n)
+        self.G = as_packed(G, n)
+        self.k, self.W = self.G.shape
+        self._lib = L.lib()
+        self._stream = stream if stream is not None else torch.cuda.current_stream()
+        self._alloc = _TorchAllocator(torch, self._stream.device) if torch_alloc else None
+        opts = L.Options()
+        opts.check_per_matrix = 1 if check_per_matrix else 0
+        opts.max_sets = int(max_sets)
+        opts.blocks_per_sm = int(blocks_per_sm)
+        if self._alloc is not None:
+            opts.dev_alloc = self._alloc.alloc_cb
+            opts.dev_free = self._alloc.free_cb
+        self._opts = opts
+        h = ctypes.c_void_p()
+        with torch.cuda.device(self._stream.device):
+            rc = self._lib.mdist_prepare(_p64(self.G), self.n, self.k, self.W, ctypes.byref(opts),
+                                         ctypes.c_void_p(self._stream.cuda_stream), ctypes.byref(h))
+        L.check(rc, "mdist_prepare")
+        self._h = h
+
+    # -- lifetime ------------------------------------------------------------------
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.mdist_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- information sets ----------------------------------------------------------
+    def info_sets(self) -> dict:
+        m = ctypes.c_int()
+        ranks = np.zeros(L.MAX_SETS, dtype=np.int32)
+        piv = np.zeros(L.MAX_SETS * self.k, dtype=np.int32)
+        gam = np.zeros(L.MAX_SETS * self.k * self.W, dtype=np.uint64)
+        tr = np.zeros(L.MAX_SETS * self.k, dtype=np.uint64)
+        rc = self._lib.mdist_info_sets(self._h, ctypes.byref(m), ranks.ctypes.data_as(L.PI),
+                                       piv.ctypes.data_as(L.PI32), _p64(gam), _p64(tr))
+        L.check(rc, "mdist_info_sets")
+        mm = m.value
+        return {
+            "m": mm,
+            "ranks": ranks[:mm].copy(),
+            "pivcols": piv.reshape(L.MAX_SETS, self.k)[:mm].copy(),
+            "gammas": gam.reshape(L.MAX_SETS, self.k, self.W)[:mm].copy(),
+            "transforms": tr.reshape(L.MAX_SETS, self.k)[:mm].copy(),
+        }
+
+    @property
+    def m(self) -> int:
+        m = ctypes.c_int()
+        L.check(self._lib.mdist_info_sets(self._h, ctypes.byref(m), None, None, None, None), "mdist_info_sets")
+        return m.value
+
+    # -- single units ----------------------------------------------------------------
+    def enumerate_level(self, g: int, j: int = -1, U: int | None = None, key=None):
+        """Units (g, j) (j = -1: every set).  Returns (U, key tuple or None, combos list)."""
+        Uc = ctypes.c_int(self.n if U is None else int(U))
+        k = L.Key(2**31 - 1, 0, 0, 0, 0) if key is None else L.Key(key[0], key[1], key[2], 0, key[3])
+        nunits = self.m if j < 0 else 1
+        combos = np.zeros(nunits, dtype=np.uint64)
+        rc = self._lib.mdist_enumerate_level(self._h, int(g), int(j), ctypes.byref(Uc), ctypes.byref(k),
+                                             _p64(combos))
+        L.check(rc, "mdist_enumerate_level")
+        kt = k.as_tuple()
+        return Uc.value, (None if kt[0] == 2**31 - 1 else kt), [int(c) for c in combos]
+
+    def unit_histogram(self, g: int, j: int):
+        hist = np.zeros(self.n + 1, dtype=np.uint64)
+        cnt = np.zeros(1, dtype=np.uint64)
+        rc = self._lib.mdist_unit_histogram(self._h, int(g), int(j), _p64(hist), _p64(cnt))
+        L.check(rc, "mdist_unit_histogram")
+        return hist, int(cnt[0])
+
+    # -- Alg. 1 ----------------------------------------------------------------------
+    def reset(self) -> None:
+        L.check(self._lib.mdist_reset(self._h), "mdist_reset")
+
+    def run(self, max_units: int = 0) -> bool:
+        fin = ctypes.c_int()
+        L.check(self._lib.mdist_run(self._h, int(max_units), ctypes.byref(fin)), "mdist_run")
+        return bool(fin.value)
+
+    def result(self) -> dict:
+        d = ctypes.c_int()
+        wit = np.zeros(self.W, dtype=np.uint64)
+        msg = np.zeros(1, dtype=np.uint64)
+        key = L.Key()
+        st = L.Stats()
+        rc = self._lib.mdist_result(self._h, ctypes.byref(d), _p64(wit), _p64(msg), ctypes.byref(key),
+                                    ctypes.byref(st))
+        L.check(rc, "mdist_result")
+        return _result_dict(d.value, wit, msg, key, st)
+
+    def min_distance(self) -> dict:
+        d = ctypes.c_int()
+        wit = np.zeros(self.W, dtype=np.uint64)
+        msg = np.zeros(1, dtype=np.uint64)
+        key = L.Key()
+        st = L.Stats()
+        rc = self._lib.mdist_min_distance(self._h, ctypes.byref(d), _p64(wit), _p64(msg), ctypes.byref(key),
+                                          ctypes.byref(st))
+        L.check(rc, "mdist_min_distance")
+        return _result_dict(d.value, wit, msg, key, st)
+
+    # -- checkpoint ------------------------------------------------------------------
+    def state_save(self) -> bytes:
+        n = ctypes.c_size_t(0)
+        self._lib.mdist_state_save(self._h, None, ctypes.byref(n))
+        buf = ctypes.create_string_buffer(n.value)
+        L.check(self._lib.mdist_state_save(self._h, buf, ctypes.byref(n)), "mdist_state_save")
+        return buf.raw[: n.value]
+
+    def state_load(self, blob: bytes) -> None:
+        buf = ctypes.create_string_buffer(blob, len(blob))
+        L.check(self._lib.mdist_state_load(self._h, buf, len(blob)), "mdist_state_load")
+
+
+def _result_dict(d, wit, msg, key, st) -> dict:
+    m = st.m
+    combos = np.ctypeslib.as_array(st.combos).reshape(L.MAX_K + 1, L.MAX_SETS)[:, :m].copy()
+    return {
+        "d": int(d),
+        "key": key.as_tuple(),
+        "message": int(msg[0]),
+        "witness": wit,
+        "g_final": int(st.g_final),
+        "j_final": int(st.j_final),
+        "m": int(m),
+        "ranks": [int(r) for r in st.ranks[:m]],
+        "counts": combos,
+        "L_final": int(st.L_final),
+        "U_final": int(st.U_final),
+        "launches": int(st.launches),
+        "total_combos": int(st.total_combos),
+        "seconds": float(st.seconds),
+        "kernel_ms": float(st.kernel_ms),
+        "h2d_bytes": int(st.h2d_bytes),
+        "d2h_bytes": int(st.d2h_bytes),
+    }
+
+
+def min_distance(G, n: int, **kw) -> dict:
+    """d, witness, key and statistics of the code generated by G (k x W uint64)."""
+    with Code(G, n, **kw) as c:
+        return c.min_distance()
+
+
+def device_info() -> dict:
+    sm = ctypes.c_int()
+    clk = ctypes.c_int()
+    ma = ctypes.c_int()
+    mi = ctypes.c_int()
+    L.check(L.lib().mdist_device_info(ctypes.byref(sm), ctypes.byref(clk), ctypes.byref(ma), ctypes.byref(mi)),
+            "mdist_device_info")
+    return {"sm_count": sm.value, "max_sm_clock_khz": clk.value, "cc": (ma.value, mi.value)}
+
+
+def partition_host(G, n: int, max_sets: int = 0) -> dict:
+    """The information sets mdist_prepare would form, computed on the host only."""
+    G = as_packed(G, n)
+    k, W = G.shape
+    m = ctypes.c_int()
+    ranks = np.zeros(L.MAX_SETS, dtype=np.int32)
+    piv = np.zeros(L.MAX_SETS * k, dtype=np.int32)
+    gam = np.zeros(L.MAX_SETS * k * W, dtype=np.uint64)
+    tr = np.zeros(L.MAX_SETS * k, dtype=np.uint64)
+    rc = L.lib().mdist_partition_host(_p64(G), int(n), k, W, int(max_sets), ctypes.byref(m),
+                                      ranks.ctypes.data_as(L.PI), piv.ctypes.data_as(L.PI32), _p64(gam), _p64(tr))
+    L.check(rc, "mdist_partition_host")
+    mm = m.value
+    return {
+        "m": mm,
+        "ranks": ranks[:mm].copy(),
+        "pivcols": piv.reshape(L.MAX_SETS, k)[:mm].copy(),
+        "gammas": gam.reshape(L.MAX_SETS, k, W)[:mm].copy(),
+        "transforms": tr.reshape(L.MAX_SETS, k)[:mm].copy(),
+    }
+
+
+def microbench(which: str, iters: int = 20000) -> dict:
+    """Per-SM-per-clock throughput of 'popc', 'lop3' or 'step4' (see include/mdist.h)."""
+    idx = {"popc": 0, "lop3": 1, "step4": 2}[which]
+    v = ctypes.c_double()
+    s = ctypes.c_double()
+    L.check(L.lib().mdist_microbench(idx, int(iters), ctypes.byref(v), ctypes.byref(s)), "mdist_microbench")
+    return {"per_clock_per_sm": v.value, "seconds": s.value}

@@ -1,0 +1,486 @@
+// api.cpp -- the C-ABI of libmdist.so (declared in include/mdist.h): code handles,
+// the Alg. 1 driver (levels g = 1, 2, ... over all information sets while L < U,
+// §2), the per-unit GPU launches, results, checkpoint / resume.
+#include <chrono>
+#include <climits>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "internal.h"
+#include "prep.h"
+
+using mdist::DeviceRows;
+using mdist::EnumParams;
+using mdist::Partition;
+using mdist::UnitSlot;
+
+namespace {
+
+struct RunState {
+    int next_g = 1, next_j = 0;
+    int U = 0, L = 1;
+    int have_key = 0;
+    mdist_key key{INT32_MAX, 0, 0, 0, 0};
+    int finished = 0;
+    int g_last = 0, j_last = -1;
+    int launches = 0;
+    double kernel_ms = 0.0;
+    double seconds = 0.0;
+    uint64_t h2d_bytes = 0, d2h_bytes = 0;
+    uint64_t counts[MDIST_MAX_K + 1][MDIST_MAX_SETS];
+};
+
+uint64_t fnv1a(const void *data, size_t len, uint64_t h = 1469598103934665603ull) {
+    const unsigned char *p = (const unsigned char *)data;
+    for (size_t i = 0; i < len; ++i) { h ^= p[i]; h *= 1099511628211ull; }
+    return h;
+}
+
+}  // namespace
+
+struct mdist_code {
+    int n = 0, k = 0, W = 0, m = 0;
+    std::vector<uint64_t> G;
+    Partition part;
+    std::vector<DeviceRows> rows;
+    mdist_options opt{};
+    cudaStream_t stream = nullptr;
+    int device = 0, sm_count = 0;
+    std::vector<uint32_t *> d_rows;
+    UnitSlot *d_slot = nullptr;
+    UnitSlot *h_slot = nullptr;          // pinned
+    unsigned long long *d_hist = nullptr;// n+1 bins, on demand
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    uint64_t rows_bytes = 0;             // Gamma rows copied to the device by mdist_prepare
+    RunState st;
+};
+
+namespace {
+
+void *dev_alloc(mdist_code *c, size_t bytes) {
+    if (c->opt.dev_alloc) return c->opt.dev_alloc(bytes, c->opt.alloc_ctx);
+    void *p = nullptr;
+    return cudaMalloc(&p, bytes) == cudaSuccess ? p : nullptr;
+}
+
+void dev_release(mdist_code *c, void *p) {
+    if (!p) return;
+    if (c->opt.dev_free) c->opt.dev_free(p, c->opt.alloc_ctx);
+    else cudaFree(p);
+}
+
+int check_shape(const uint64_t *G, int n, int k, int W) {
+    if (!G || k < 1 || k > MDIST_MAX_K || n <= k || n > MDIST_MAX_N || W < (n + 63) / 64 || W > 64)
+        return MDIST_EINVAL;
+    for (int r = 0; r < k; ++r)
+        for (int i = n; i < 64 * W; ++i)
+            if ((G[(size_t)r * W + (i >> 6)] >> (i & 63)) & 1ull) return MDIST_EINVAL;
+    return MDIST_OK;
+}
+
+int set_bound(int h, int k, int r) {
+    const int v = h + 1 - (k - r);
+    return v > 0 ? v : 0;
+}
+
+void reset_state(mdist_code *c) {
+    c->st = RunState{};
+    std::memset(c->st.counts, 0, sizeof c->st.counts);
+    c->st.U = c->n - c->k + 1;  // Alg. 1, line 1: L := 1, U := n - k + 1
+    c->st.L = 1;
+}
+
+// One (g, j) unit on the GPU.  Candidates: codewords of weight <= U_thr.
+int run_unit(mdist_code *c, int g, int j, int U_thr, bool hist_mode, bool *found, int *w_out, uint64_t *rank_out,
+             uint64_t *count_out) {
+    const DeviceRows &dr = c->rows[(size_t)j];
+    EnumParams p{};
+    if (!mdist::plan_level(c->k, g, dr.nwords, p)) return MDIST_ERANGE;
+    p.rows = c->d_rows[(size_t)j];
+    p.slot = c->d_slot;
+    p.hist = c->d_hist;
+    p.nwords = dr.nwords;
+    p.n_bits = dr.n_bits;
+    p.base = dr.full_rank ? g : 0;
+    c->h_slot->U = (unsigned)(U_thr < 0 ? 0 : U_thr);
+    c->h_slot->pad0 = 0;
+    c->h_slot->key = mdist::kNoKey;
+    c->h_slot->count = 0;
+    c->h_slot->tile_next = 0;
+    if (cudaMemcpyAsync(c->d_slot, c->h_slot, sizeof(UnitSlot), cudaMemcpyHostToDevice, c->stream) != cudaSuccess)
+        return MDIST_ECUDA;
+    c->st.h2d_bytes += sizeof(UnitSlot);
+    if (cudaEventRecord(c->ev0, c->stream) != cudaSuccess) return MDIST_ECUDA;
+    if (mdist::launch_enum_unit(p, dr.nwords, hist_mode, c->sm_count, c->opt.blocks_per_sm, c->stream) != cudaSuccess)
+        return MDIST_ECUDA;
+    if (cudaEventRecord(c->ev1, c->stream) != cudaSuccess) return MDIST_ECUDA;
+    if (cudaMemcpyAsync(c->h_slot, c->d_slot, sizeof(UnitSlot), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess)
+        return MDIST_ECUDA;
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return MDIST_ECUDA;
+    c->st.d2h_bytes += sizeof(UnitSlot);
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, c->ev0, c->ev1) == cudaSuccess) c->st.kernel_ms += ms;
+    c->st.launches += 1;
+    const unsigned long long key = c->h_slot->key;
+    *found = key != mdist::kNoKey;
+    *w_out = *found ? (int)(key >> mdist::kKeyRankBits) : INT_MAX;
+    *rank_out = *found ? (key & ((1ull << mdist::kKeyRankBits) - 1)) : 0;
+    *count_out = c->h_slot->count;
+    return MDIST_OK;
+}
+
+bool key_less(const mdist_key &a, const mdist_key &b) {
+    if (a.weight != b.weight) return a.weight < b.weight;
+    if (a.g != b.g) return a.g < b.g;
+    if (a.j != b.j) return a.j < b.j;
+    return a.rank < b.rank;
+}
+
+// g-subset of {0..k-1} with lexicographic rank `rank`, as a mask.  With
+// d_i = k-1-c_i the rank satisfies C(k,g)-1-rank = sum_i C(d_i, g-i+1), the
+// combinatorial number system, so the d_i are read off greedily from the top.
+uint64_t unrank_lex_host(int k, int g, uint64_t rank) {
+    uint64_t r = mdist::binom_host(k, g) - 1 - rank;
+    uint64_t mask = 0;
+    int d = k - 1;
+    for (int t = g; t >= 1; --t) {
+        while (mdist::binom_host(d, t) > r) --d;
+        r -= mdist::binom_host(d, t);
+        mask |= 1ull << (k - 1 - d);
+        --d;
+    }
+    return mask;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *mdist_strerror(int err) {
+    switch (err) {
+        case MDIST_OK: return "ok";
+        case MDIST_EINVAL: return "invalid argument";
+        case MDIST_ERANK: return "generator matrix has rank < k";
+        case MDIST_ENOMEM: return "out of memory";
+        case MDIST_ECUDA: return "CUDA error";
+        case MDIST_ETIMEOUT: return "device wait timed out";
+        case MDIST_ECANCELLED: return "cancelled";
+        case MDIST_ERANGE: return "level beyond the device key range (C(k,g) >= 2^54)";
+        case MDIST_ESTATE: return "state blob does not match this code";
+        case MDIST_EAGAIN: return "not ready / busy";
+        default: return "unknown error";
+    }
+}
+
+void mdist_free(mdist_code *c) {
+    if (!c) return;
+    cudaStreamSynchronize(c->stream);
+    for (uint32_t *p : c->d_rows) dev_release(c, p);
+    dev_release(c, c->d_slot);
+    dev_release(c, c->d_hist);
+    if (c->h_slot) cudaFreeHost(c->h_slot);
+    if (c->ev0) cudaEventDestroy(c->ev0);
+    if (c->ev1) cudaEventDestroy(c->ev1);
+    delete c;
+}
+
+int mdist_prepare(const uint64_t *G, int n, int k, int words_per_row, const mdist_options *opts, void *cuda_stream,
+                  mdist_code **out) {
+    if (!out) return MDIST_EINVAL;
+    *out = nullptr;
+    int rc = check_shape(G, n, k, words_per_row);
+    if (rc != MDIST_OK) return rc;
+    mdist_code *c = new (std::nothrow) mdist_code();
+    if (!c) return MDIST_ENOMEM;
+    if (opts) c->opt = *opts;
+    if (c->opt.max_sets <= 0 || c->opt.max_sets > MDIST_MAX_SETS) c->opt.max_sets = MDIST_MAX_SETS;
+    c->n = n;
+    c->k = k;
+    c->W = words_per_row;
+    c->G.assign(G, G + (size_t)k * words_per_row);
+    c->stream = (cudaStream_t)cuda_stream;
+    rc = mdist::partition_info_sets(G, n, k, words_per_row, c->opt.max_sets, c->part);
+    if (rc != MDIST_OK) { delete c; return rc; }
+    c->m = (int)c->part.sets.size();
+    c->rows.resize((size_t)c->m);
+    for (int j = 0; j < c->m; ++j) mdist::build_rows(c->part, j, c->rows[(size_t)j]);
+    if (cudaGetDevice(&c->device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess) {
+        cudaGetLastError();
+        delete c;
+        return MDIST_ECUDA;
+    }
+    if (cudaEventCreate(&c->ev0) != cudaSuccess || cudaEventCreate(&c->ev1) != cudaSuccess ||
+        cudaMallocHost((void **)&c->h_slot, sizeof(UnitSlot)) != cudaSuccess) {
+        mdist_free(c);
+        return MDIST_ECUDA;
+    }
+    c->d_slot = (UnitSlot *)dev_alloc(c, sizeof(UnitSlot));
+    if (!c->d_slot) { mdist_free(c); return MDIST_ENOMEM; }
+    c->d_rows.assign((size_t)c->m, nullptr);
+    for (int j = 0; j < c->m; ++j) {
+        const DeviceRows &dr = c->rows[(size_t)j];
+        const size_t bytes = dr.words.size() * sizeof(uint32_t);
+        c->rows_bytes += bytes;
+        c->d_rows[(size_t)j] = (uint32_t *)dev_alloc(c, bytes);
+        if (!c->d_rows[(size_t)j]) { mdist_free(c); return MDIST_ENOMEM; }
+        if (cudaMemcpyAsync(c->d_rows[(size_t)j], dr.words.data(), bytes, cudaMemcpyHostToDevice, c->stream) !=
+            cudaSuccess) {
+            mdist_free(c);
+            return MDIST_ECUDA;
+        }
+    }
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) { mdist_free(c); return MDIST_ECUDA; }
+    reset_state(c);
+    *out = c;
+    return MDIST_OK;
+}
+
+int mdist_set_stream(mdist_code *c, void *cuda_stream) {
+    if (!c) return MDIST_EINVAL;
+    c->stream = (cudaStream_t)cuda_stream;
+    return MDIST_OK;
+}
+
+int mdist_info_sets(const mdist_code *c, int *m, int *ranks, int32_t *pivcols, uint64_t *gammas,
+                    uint64_t *transforms) {
+    if (!c || !m) return MDIST_EINVAL;
+    *m = c->m;
+    for (int j = 0; j < c->m; ++j) {
+        const mdist::InfoSet &s = c->part.sets[(size_t)j];
+        if (ranks) ranks[j] = s.rank;
+        if (pivcols)
+            for (int i = 0; i < c->k; ++i) pivcols[(size_t)j * c->k + i] = i < s.rank ? s.pivcols[(size_t)i] : -1;
+        if (gammas) std::memcpy(gammas + (size_t)j * c->k * c->W, s.gamma.data(), sizeof(uint64_t) * s.gamma.size());
+        if (transforms) std::memcpy(transforms + (size_t)j * c->k, s.transform.data(), sizeof(uint64_t) * c->k);
+    }
+    return MDIST_OK;
+}
+
+int mdist_enumerate_level(mdist_code *c, int g, int j, int *U_inout, mdist_key *key_inout, uint64_t *combos_out) {
+    if (!c || !U_inout || !key_inout || g < 1 || g > c->k || j < -1 || j >= c->m) return MDIST_EINVAL;
+    const int j0 = j < 0 ? 0 : j;
+    const int j1 = j < 0 ? c->m : j + 1;
+    for (int jj = j0; jj < j1; ++jj) {
+        bool found;
+        int w;
+        uint64_t rank, cnt;
+        const int rc = run_unit(c, g, jj, *U_inout, false, &found, &w, &rank, &cnt);
+        if (rc != MDIST_OK) return rc;
+        if (combos_out) combos_out[jj - j0] = cnt;
+        if (found) {
+            const mdist_key cand{w, g, jj, 0, rank};
+            if (key_less(cand, *key_inout)) *key_inout = cand;
+            if (w < *U_inout) *U_inout = w;
+        }
+    }
+    return MDIST_OK;
+}
+
+int mdist_unit_histogram(mdist_code *c, int g, int j, uint64_t *hist, uint64_t *combos_out) {
+    if (!c || !hist || g < 1 || g > c->k || j < 0 || j >= c->m) return MDIST_EINVAL;
+    const size_t bins = (size_t)c->n + 1;
+    if (!c->d_hist) {
+        c->d_hist = (unsigned long long *)dev_alloc(c, bins * sizeof(unsigned long long));
+        if (!c->d_hist) return MDIST_ENOMEM;
+    }
+    if (cudaMemsetAsync(c->d_hist, 0, bins * sizeof(unsigned long long), c->stream) != cudaSuccess) return MDIST_ECUDA;
+    bool found;
+    int w;
+    uint64_t rank, cnt;
+    const int rc = run_unit(c, g, j, 0, true, &found, &w, &rank, &cnt);
+    if (rc != MDIST_OK) return rc;
+    if (cudaMemcpyAsync(hist, c->d_hist, bins * sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->stream) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(c->stream) != cudaSuccess)
+        return MDIST_ECUDA;
+    if (combos_out) *combos_out = cnt;
+    return MDIST_OK;
+}
+
+int mdist_reset(mdist_code *c) {
+    if (!c) return MDIST_EINVAL;
+    reset_state(c);
+    return MDIST_OK;
+}
+
+int mdist_run(mdist_code *c, int max_units, int *finished) {
+    if (!c) return MDIST_EINVAL;
+    RunState &s = c->st;
+    const auto t0 = std::chrono::steady_clock::now();
+    int units = 0;
+    int rc = MDIST_OK;
+    while (!s.finished && (max_units <= 0 || units < max_units)) {
+        const int g = s.next_g, j = s.next_j;
+        // after a key exists, only strictly lighter codewords can replace it (a tie
+        // in a later unit has a larger (g, j)); before, ties with U = n-k+1 count
+        const int U_thr = s.have_key ? s.key.weight - 1 : s.U;
+        bool found;
+        int w;
+        uint64_t rank, cnt;
+        rc = run_unit(c, g, j, U_thr, false, &found, &w, &rank, &cnt);
+        if (rc != MDIST_OK) break;
+        ++units;
+        s.counts[g][j] = cnt;
+        s.g_last = g;
+        s.j_last = j;
+        if (found) {
+            s.key = mdist_key{w, g, j, 0, rank};
+            s.have_key = 1;
+            if (w < s.U) s.U = w;
+        }
+        if (c->opt.check_per_matrix) {
+            int Lm = 0;
+            for (int i = 0; i < c->m; ++i) Lm += set_bound(i <= j ? g : g - 1, c->k, c->part.sets[(size_t)i].rank);
+            if (Lm > s.L) s.L = Lm;
+            if (s.L >= s.U) s.finished = 1;
+        }
+        s.next_j = j + 1;
+        if (s.next_j == c->m) {
+            s.next_j = 0;
+            if (!c->opt.check_per_matrix) {  // Alg. 1, line 7
+                int Lg = 0;
+                for (int i = 0; i < c->m; ++i) Lg += set_bound(g, c->k, c->part.sets[(size_t)i].rank);
+                s.L = Lg;
+                if (s.L >= s.U) s.finished = 1;
+            }
+            s.next_g = g + 1;
+            if (s.next_g > c->k) s.finished = 1;
+        }
+    }
+    s.seconds += std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (finished) *finished = s.finished;
+    return rc;
+}
+
+int mdist_result(const mdist_code *c, int *d, uint64_t *witness, uint64_t *message, mdist_key *key,
+                 mdist_stats *stats) {
+    if (!c || !d) return MDIST_EINVAL;
+    const RunState &s = c->st;
+    if (!s.finished || !s.have_key) return MDIST_EAGAIN;
+    *d = s.U;
+    const uint64_t comb = unrank_lex_host(c->k, s.key.g, s.key.rank);
+    const mdist::InfoSet &set = c->part.sets[(size_t)s.key.j];
+    uint64_t msg = 0;
+    for (int r = 0; r < c->k; ++r)
+        if ((comb >> r) & 1ull) msg ^= set.transform[(size_t)r];
+    if (message) *message = msg;
+    if (witness) {
+        for (int w = 0; w < c->W; ++w) witness[w] = 0;
+        for (int b = 0; b < c->k; ++b)
+            if ((msg >> b) & 1ull)
+                for (int w = 0; w < c->W; ++w) witness[w] ^= c->G[(size_t)b * c->W + w];
+    }
+    if (key) *key = s.key;
+    if (stats) {
+        std::memset(stats, 0, sizeof *stats);
+        stats->g_final = s.g_last;
+        stats->j_final = s.j_last;
+        stats->m = c->m;
+        stats->L_final = s.L;
+        stats->U_final = s.U;
+        stats->launches = s.launches;
+        for (int j = 0; j < c->m; ++j) stats->ranks[j] = c->part.sets[(size_t)j].rank;
+        uint64_t tot = 0;
+        for (int g = 0; g <= MDIST_MAX_K; ++g)
+            for (int j = 0; j < MDIST_MAX_SETS; ++j) {
+                stats->combos[g][j] = s.counts[g][j];
+                tot += s.counts[g][j];
+            }
+        stats->total_combos = tot;
+        stats->seconds = s.seconds;
+        stats->kernel_ms = s.kernel_ms;
+        stats->h2d_bytes = s.h2d_bytes + c->rows_bytes;
+        stats->d2h_bytes = s.d2h_bytes;
+    }
+    return MDIST_OK;
+}
+
+int mdist_min_distance(mdist_code *c, int *d, uint64_t *witness, uint64_t *message, mdist_key *key,
+                       mdist_stats *stats) {
+    if (!c || !d) return MDIST_EINVAL;
+    int fin = 0;
+    const int rc = mdist_run(c, 0, &fin);
+    if (rc != MDIST_OK) return rc;
+    return mdist_result(c, d, witness, message, key, stats);
+}
+
+// ---- checkpoint / resume --------------------------------------------------------
+
+namespace {
+struct StateBlob {
+    uint64_t magic;
+    uint32_t version, n, k, m;
+    uint64_t code_hash;
+    int32_t per_matrix;
+    RunState st;
+};
+constexpr uint64_t kMagic = 0x6d64697374737431ull;  // "mdistst1"
+
+uint64_t code_hash(const mdist_code *c) {
+    uint64_t h = fnv1a(c->G.data(), c->G.size() * sizeof(uint64_t));
+    const int dims[3] = {c->n, c->k, c->W};
+    return fnv1a(dims, sizeof dims, h);
+}
+}  // namespace
+
+int mdist_state_save(const mdist_code *c, void *buf, size_t *len) {
+    if (!c || !len) return MDIST_EINVAL;
+    if (!buf || *len < sizeof(StateBlob)) {
+        *len = sizeof(StateBlob);
+        return MDIST_EINVAL;
+    }
+    StateBlob b;
+    std::memset(&b, 0, sizeof b);
+    b.magic = kMagic;
+    b.version = 1;
+    b.n = (uint32_t)c->n;
+    b.k = (uint32_t)c->k;
+    b.m = (uint32_t)c->m;
+    b.code_hash = code_hash(c);
+    b.per_matrix = c->opt.check_per_matrix;
+    b.st = c->st;
+    std::memcpy(buf, &b, sizeof b);
+    *len = sizeof b;
+    return MDIST_OK;
+}
+
+int mdist_state_load(mdist_code *c, const void *buf, size_t len) {
+    if (!c || !buf) return MDIST_EINVAL;
+    if (len != sizeof(StateBlob)) return MDIST_ESTATE;
+    StateBlob b;
+    std::memcpy(&b, buf, sizeof b);
+    if (b.magic != kMagic || b.version != 1 || (int)b.n != c->n || (int)b.k != c->k || (int)b.m != c->m ||
+        b.code_hash != code_hash(c) || b.per_matrix != c->opt.check_per_matrix)
+        return MDIST_ESTATE;
+    if (b.st.next_g < 1 || b.st.next_g > c->k + 1 || b.st.next_j < 0 || b.st.next_j >= c->m) return MDIST_ESTATE;
+    c->st = b.st;
+    return MDIST_OK;
+}
+
+int mdist_device_info(int *sm_count, int *max_sm_clock_khz, int *cc_major, int *cc_minor) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); return MDIST_ECUDA; }
+    int v = 0;
+    if (sm_count) {
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return MDIST_ECUDA;
+        *sm_count = v;
+    }
+    if (max_sm_clock_khz) {
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrClockRate, dev) != cudaSuccess) return MDIST_ECUDA;
+        *max_sm_clock_khz = v;
+    }
+    if (cc_major) {
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrComputeCapabilityMajor, dev) != cudaSuccess) return MDIST_ECUDA;
+        *cc_major = v;
+    }
+    if (cc_minor) {
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrComputeCapabilityMinor, dev) != cudaSuccess) return MDIST_ECUDA;
+        *cc_minor = v;
+    }
+    return MDIST_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,77 @@
+// internal.h -- structures shared by the library's translation units (host prep,
+// enumerator kernels, C-ABI).  Not part of the public ABI (include/mdist.h).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+#include "../../include/mdist.h"
+
+namespace mdist {
+
+constexpr int kMaxK = MDIST_MAX_K;
+constexpr int kMaxN = MDIST_MAX_N;
+constexpr int kMaxSets = MDIST_MAX_SETS;
+constexpr int kMaxWords32 = kMaxN / 32;  // 32-bit words of a reduced row
+constexpr int kMaxBlocks = 34;           // product blocks per level: i in [0, 32] (+1 spare)
+constexpr int kWarpsPerCta = 8;
+constexpr int kCtaThreads = 32 * kWarpsPerCta;
+constexpr int kKeyRankBits = 54;         // device key = weight << 54 | lexicographic rank
+constexpr uint64_t kNoKey = ~0ull;
+
+// Device-side result slot of one (g, j) unit.
+struct UnitSlot {
+    unsigned int U;              // candidate threshold: codewords of weight <= U count
+    unsigned int pad0;
+    unsigned long long key;      // least (weight << 54 | rank) among candidates, or kNoKey
+    unsigned long long count;    // combinations enumerated
+    unsigned long long tile_next;// work counter of the persistent grid
+};
+static_assert(sizeof(UnitSlot) == 32, "slot layout");
+
+// One product block of a level: all i-subsets of the first half H1 of the rows,
+// times all (g-i)-subsets of the second half H2.  The larger side is spread over
+// the lanes of a warp ("lane side"); the warp walks the smaller side ("walk side").
+struct ProductBlock {
+    unsigned int lane_half;      // 0: lane side = H1 subsets, 1: lane side = H2 subsets
+    unsigned int lane_t;         // subset size on the lane side
+    unsigned int walk_t;         // subset size on the walk side
+    unsigned int pad;
+    unsigned long long lane_n;   // C(k_lane_half, lane_t)
+    unsigned long long walk_n;   // C(k_walk_half, walk_t)
+    unsigned long long walk_chunks;
+    unsigned long long tile_begin;
+};
+
+// Parameters of one enumerator launch (one unit).
+struct EnumParams {
+    const uint32_t *rows;        // k reduced rows of nwords 32-bit words each (row-major)
+    UnitSlot *slot;
+    unsigned long long *hist;    // n_bits+1 bins (histogram mode only)
+    int k, k1, k2, g;            // rows, half sizes (k1 = ceil(k/2)), level
+    int nwords;                  // 32-bit words per reduced row
+    int base;                    // weight every codeword carries outside the reduced row
+    int n_bits;                  // bits per reduced row
+    int nblocks;
+    unsigned long long total_tiles;
+    ProductBlock blocks[kMaxBlocks];
+};
+
+// Kernel tile geometry per word count (lanes x XP lane entries, YL walk entries).
+constexpr int lane_entries_per_thread(int nwords) { return nwords <= 4 ? 16 : (nwords <= 8 ? 8 : 4); }
+constexpr int walk_len_for(int nwords) { return nwords <= 8 ? 256 : 128; }
+
+// Launch one unit's enumerator (enum_launch.cu).  hist == nullptr for the normal path.
+cudaError_t launch_enum_unit(const EnumParams &p, int nwords, bool hist_mode, int sm_count, int blocks_per_sm,
+                             cudaStream_t stream);
+size_t enum_smem_bytes(int k, int nwords);
+
+// Host-side binomial coefficients C(a, b), a <= 64 (enum_launch.cu).
+unsigned long long binom_host(int a, int b);
+
+// Fill the product-block table of a level; false if C(k, g) >= 2^54.
+bool plan_level(int k, int g, int nwords, EnumParams &p);
+
+}  // namespace mdist
