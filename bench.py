@@ -298,6 +298,33 @@ def run_ours(args):
     return 0
 
 
+def run_profile_unit(args):
+    """One enumerator launch of the dominant level of the workload, at the threshold
+    the full run uses there (U = d - 1 once the witness is known), run twice (the
+    first is a warm-up).  Small, self-contained command for profiler captures."""
+    import torch
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_1603_06757_gb300 import api
+
+    n, k, seed, G = workload(args.workload)
+    g = args.profile_unit
+    with api.Code(G, n) as code:
+        d = code.min_distance()["d"] if args.profile_d <= 0 else args.profile_d
+        out = []
+        for _ in range(2):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            U, key, combos = code.enumerate_level(g, 0, U=d - 1)
+            torch.cuda.synchronize()
+            out.append(time.perf_counter() - t0)
+    print(json.dumps({"workload": args.workload, "g": g, "j": 0, "U": d - 1, "combos": combos[0],
+                      "seconds": out, "codewords_per_s": combos[0] / out[-1]}), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -308,7 +335,11 @@ def main():
     ap.add_argument("--cpu-levels", type=int, default=8)
     ap.add_argument("--ref-levels", type=int, default=7)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-unit", type=int, default=0, help="run one unit of this level (profiling)")
+    ap.add_argument("--profile-d", type=int, default=0, help="d of the workload if known (skips the full run)")
     args = ap.parse_args()
+    if args.profile_unit:
+        return run_profile_unit(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

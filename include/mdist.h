@@ -67,7 +67,11 @@ typedef struct {
                                 "one after each Gamma_j", §2). */
     int max_sets;            /* 0 = MDIST_MAX_SETS */
     int blocks_per_sm;       /* enumerator CTAs per SM; 0 = occupancy limit */
-    int reserved0;
+    int filter_group;        /* enumerator variant: 0 = chosen per unit from the threshold,
+                                1 = exact weight of every codeword, 2..4 = first a lower
+                                bound (popcount of the OR of each group of that many
+                                32-bit words), exact weight only where the bound does not
+                                already exceed the threshold.  Results are identical. */
     long long timeout_cycles;/* bound for device-side waits (batched / serving); 0 = default */
     mdist_alloc_fn dev_alloc;/* optional device allocator */
     mdist_free_fn dev_free;
@@ -170,7 +174,8 @@ int mdist_device_info(int *sm_count, int *max_sm_clock_khz, int *cc_major, int *
 
 /* Instruction-throughput probe on the current device, for roofline arithmetic:
  * which = 0: 32-bit POPC, 1: 3-input XOR (LOP3), 2: enumerator inner step (XOR + POPC
- * over 4 words, sum, running min) with operands in registers.  One 1024-thread CTA
+ * over 4 words, sum, running min), 3 / 4: the lower-bound step of filter groups of 2 /
+ * 4 words (threshold never reached), operands in registers.  One 1024-thread CTA
  * per SM, `iters` loop trips; *ops_per_clock_per_sm = operations (or codeword steps)
  * retired per SM per clock (clock64), *seconds = launch time.  Allocates 64 B + 8 B
  * per SM of device memory for its duration. */
@@ -198,6 +203,11 @@ int mdist_debug_set_rows(const uint64_t *G, int n, int k, int words_per_row, int
 int mdist_debug_unrank_colex(int kh, int t, uint32_t rank, uint32_t *mask);
 int mdist_debug_next_colex(uint32_t m, uint32_t *next);
 int mdist_debug_lexrank(uint64_t mask, int k, int g, uint64_t *rank);
+
+/* Enumerator variant the library picks for a unit (mdist_options.filter_group = 0):
+ * 0 = exact count, 2..4 = OR-group size; nwords 32-bit words of n_bits stored bits,
+ * thr = largest reduced weight that is still a candidate. */
+int mdist_debug_filter_choice(int nwords, int n_bits, int thr, int *group);
 
 /* Work plan of one level (k rows, level g, nwords 32-bit words per row): the product
  * blocks (i-subsets of rows [0, ceil(k/2)) times (g-i)-subsets of the rest), 7 values

@@ -36,7 +36,7 @@ class Options(ctypes.Structure):
         ("check_per_matrix", ctypes.c_int),
         ("max_sets", ctypes.c_int),
         ("blocks_per_sm", ctypes.c_int),
-        ("reserved0", ctypes.c_int),
+        ("filter_group", ctypes.c_int),
         ("timeout_cycles", ctypes.c_longlong),
         ("dev_alloc", ALLOC_FN),
         ("dev_free", FREE_FN),
@@ -116,6 +116,7 @@ SIGNATURES = {
                                                 ctypes.POINTER(ctypes.c_uint32)]),
     "mdist_debug_next_colex": (ctypes.c_int, [ctypes.c_uint32, ctypes.POINTER(ctypes.c_uint32)]),
     "mdist_debug_lexrank": (ctypes.c_int, [ctypes.c_uint64, ctypes.c_int, ctypes.c_int, P64]),
+    "mdist_debug_filter_choice": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, PI]),
     "mdist_debug_level_plan": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, PI, P64, P64, PI, PI]),
 }
 

@@ -62,7 +62,7 @@ class Code:
     """A prepared code: information sets on the host, packed Gamma_j on the device."""
 
     def __init__(self, G, n: int, *, check_per_matrix: bool = False, max_sets: int = 0, blocks_per_sm: int = 0,
-                 stream=None, torch_alloc: bool = True):
+                 filter_group: int = 0, stream=None, torch_alloc: bool = True):
         torch = _torch()
         self.n = int(n)
         self.G = as_packed(G, n)
@@ -74,6 +74,7 @@ class Code:
         opts.check_per_matrix = 1 if check_per_matrix else 0
         opts.max_sets = int(max_sets)
         opts.blocks_per_sm = int(blocks_per_sm)
+        opts.filter_group = int(filter_group)
         if self._alloc is not None:
             opts.dev_alloc = self._alloc.alloc_cb
             opts.dev_free = self._alloc.free_cb
@@ -256,7 +257,7 @@ def partition_host(G, n: int, max_sets: int = 0) -> dict:
 
 def microbench(which: str, iters: int = 20000) -> dict:
     """Per-SM-per-clock throughput of 'popc', 'lop3' or 'step4' (see include/mdist.h)."""
-    idx = {"popc": 0, "lop3": 1, "step4": 2}[which]
+    idx = {"popc": 0, "lop3": 1, "step4": 2, "step4_or2": 3, "step4_or4": 4}[which]
     v = ctypes.c_double()
     s = ctypes.c_double()
     L.check(L.lib().mdist_microbench(idx, int(iters), ctypes.byref(v), ctypes.byref(s)), "mdist_microbench")

@@ -29,6 +29,7 @@ struct RunState {
     double kernel_ms = 0.0;
     double seconds = 0.0;
     uint64_t h2d_bytes = 0, d2h_bytes = 0;
+    int last_group = 0;
     uint64_t counts[MDIST_MAX_K + 1][MDIST_MAX_SETS];
 };
 
@@ -113,7 +114,16 @@ int run_unit(mdist_code *c, int g, int j, int U_thr, bool hist_mode, bool *found
         return MDIST_ECUDA;
     c->st.h2d_bytes += sizeof(UnitSlot);
     if (cudaEventRecord(c->ev0, c->stream) != cudaSuccess) return MDIST_ECUDA;
-    if (mdist::launch_enum_unit(p, dr.nwords, hist_mode, c->sm_count, c->opt.blocks_per_sm, c->stream) != cudaSuccess)
+    int group = 0;
+    if (!hist_mode) {
+        const int fg = c->opt.filter_group;
+        group = fg == 0 ? mdist::choose_filter_group(dr.nwords, dr.n_bits, (U_thr < 0 ? 0 : U_thr) - p.base)
+                        : (fg == 1 ? 0 : fg);
+        if (group > dr.nwords) group = 0;
+    }
+    c->st.last_group = group;
+    if (mdist::launch_enum_unit(p, dr.nwords, group, hist_mode, c->sm_count, c->opt.blocks_per_sm, c->stream) !=
+        cudaSuccess)
         return MDIST_ECUDA;
     if (cudaEventRecord(c->ev1, c->stream) != cudaSuccess) return MDIST_ECUDA;
     if (cudaMemcpyAsync(c->h_slot, c->d_slot, sizeof(UnitSlot), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess)
@@ -195,6 +205,7 @@ int mdist_prepare(const uint64_t *G, int n, int k, int words_per_row, const mdis
     mdist_code *c = new (std::nothrow) mdist_code();
     if (!c) return MDIST_ENOMEM;
     if (opts) c->opt = *opts;
+    if (c->opt.filter_group < 0 || c->opt.filter_group > 4) { delete c; return MDIST_EINVAL; }
     if (c->opt.max_sets <= 0 || c->opt.max_sets > MDIST_MAX_SETS) c->opt.max_sets = MDIST_MAX_SETS;
     c->n = n;
     c->k = k;

@@ -84,6 +84,12 @@ int mdist_debug_lexrank(uint64_t mask, int k, int g, uint64_t *rank) {
     return MDIST_OK;
 }
 
+int mdist_debug_filter_choice(int nwords, int n_bits, int thr, int *group) {
+    if (!group || nwords < 1 || nwords > 16 || n_bits < 1 || n_bits > 32 * nwords) return MDIST_EINVAL;
+    *group = mdist::choose_filter_group(nwords, n_bits, thr);
+    return MDIST_OK;
+}
+
 int mdist_debug_level_plan(int k, int g, int nwords, int *nblocks, uint64_t *blocks /* 34 * 7 */,
                            uint64_t *total_tiles, int *lane_chunk, int *walk_chunk) {
     if (!nblocks || !blocks || !total_tiles || nwords < 1 || nwords > 16) return MDIST_EINVAL;

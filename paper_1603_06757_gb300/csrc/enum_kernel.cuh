@@ -86,7 +86,7 @@ struct EnumCfg {
     static constexpr int YL = walk_len_for(NW);             // walk-side entries per tile
 };
 
-template <int NW, bool HIST>
+template <int NW, int GS, bool HIST>
 __global__ void __launch_bounds__(kCtaThreads) enum_unit_kernel(const __grid_constant__ EnumParams P) {
     constexpr int XP = EnumCfg<NW>::XP;
     constexpr int YL = EnumCfg<NW>::YL;
@@ -184,31 +184,60 @@ __global__ void __launch_bounds__(kCtaThreads) enum_unit_kernel(const __grid_con
         }
         __syncwarp();
 
-        // ---- the walk: XOR, POPC, min, compare ----
+        // ---- the walk ----
         for (int s = 0; s < walk_len; ++s) {
             uint32_t y[NW];
 #pragma unroll
             for (int w = 0; w < NW; ++w) y[w] = wbuf[s * NW + w];
-            int mn = INT_MAX;
-#pragma unroll
-            for (int p = 0; p < XP; ++p) {
-                int acc = 0;
-#pragma unroll
-                for (int w = 0; w < NW; ++w) acc += __popc(x[p][w] ^ y[w]);
-                mn = acc < mn ? acc : mn;
-                if (HIST && p < nvalid) atomicAdd(&s_hist[acc + P.base], 1u);
-            }
-            if (mn <= thr) {
+            if (GS == 0) {
+                // exact: XOR, POPC per word, sum, running min, one compare per step
+                int mn = INT_MAX;
 #pragma unroll
                 for (int p = 0; p < XP; ++p) {
                     int acc = 0;
 #pragma unroll
                     for (int w = 0; w < NW; ++w) acc += __popc(x[p][w] ^ y[w]);
-                    if (p < nvalid && acc <= thr) {
-                        const unsigned long long key =
-                            candidate_key(P, B, s_bn, e0 + (uint32_t)p, (uint32_t)(w_first + s), acc + P.base);
-                        best = key < best ? key : best;
-                        thr = acc;
+                    mn = acc < mn ? acc : mn;
+                    if (HIST && p < nvalid) atomicAdd(&s_hist[acc + P.base], 1u);
+                }
+                if (mn <= thr) {
+#pragma unroll
+                    for (int p = 0; p < XP; ++p) {
+                        int acc = 0;
+#pragma unroll
+                        for (int w = 0; w < NW; ++w) acc += __popc(x[p][w] ^ y[w]);
+                        if (p < nvalid && acc <= thr) {
+                            const unsigned long long key = candidate_key(P, B, s_bn, e0 + (uint32_t)p,
+                                                                         (uint32_t)(w_first + s), acc + P.base);
+                            best = key < best ? key : best;
+                            thr = acc;
+                        }
+                    }
+                }
+            } else {
+                // lower bound first: weight >= sum over groups of GS words of
+                // popc(OR of the group's XORed words); only codewords whose bound
+                // reaches the threshold get the exact count
+#pragma unroll
+                for (int p = 0; p < XP; ++p) {
+                    int lb = 0;
+#pragma unroll
+                    for (int q = 0; q < NW; q += GS) {
+                        uint32_t o = 0;
+#pragma unroll
+                        for (int w = q; w < q + GS && w < NW; ++w) o |= x[p][w] ^ y[w];
+                        lb += __popc(o);
+                    }
+                    if (lb <= thr) {
+                        int acc = 0;
+#pragma unroll
+                        for (int w = 0; w < NW; ++w) acc += __popc(x[p][w] ^ y[w]);
+                        if (p < nvalid && acc <= thr) {
+                            const unsigned long long key = candidate_key(P, B, s_bn, e0 + (uint32_t)p,
+                                                                         (uint32_t)(w_first + s), acc + P.base);
+                            best = key < best ? key : best;
+                            thr = acc;
+                        }
                     }
                 }
             }
@@ -243,11 +272,11 @@ inline size_t enum_smem_bytes_nw(int k, int nw, int hist_bins) {
     return sizeof(uint32_t) * ((size_t)k * nw + kBn * kBn + (size_t)kWarpsPerCta * yl * nw + (size_t)hist_bins);
 }
 
-template <int NW>
-cudaError_t launch_nw(const EnumParams &p, bool hist_mode, int sm_count, int blocks_per_sm, cudaStream_t stream) {
-    const int hist_bins = hist_mode ? p.n_bits + p.base + 1 : 0;
+template <int NW, int GS, bool HIST>
+cudaError_t launch_variant(const EnumParams &p, int sm_count, int blocks_per_sm, cudaStream_t stream) {
+    const int hist_bins = HIST ? p.n_bits + p.base + 1 : 0;
     const size_t smem = enum_smem_bytes_nw(p.k, NW, hist_bins);
-    auto kern = hist_mode ? enum_unit_kernel<NW, true> : enum_unit_kernel<NW, false>;
+    auto kern = enum_unit_kernel<NW, GS, HIST>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int occ = 0;
@@ -261,6 +290,20 @@ cudaError_t launch_nw(const EnumParams &p, bool hist_mode, int sm_count, int blo
     if (grid < 1) grid = 1;
     kern<<<(unsigned int)grid, kCtaThreads, smem, stream>>>(p);
     return cudaGetLastError();
+}
+
+// group: 0 = exact count for every codeword; 2, 3, 4 = OR-group lower bound first
+template <int NW>
+cudaError_t launch_nw(const EnumParams &p, int group, bool hist_mode, int sm_count, int blocks_per_sm,
+                      cudaStream_t stream) {
+    if (hist_mode) return launch_variant<NW, 0, true>(p, sm_count, blocks_per_sm, stream);
+    switch (group) {
+        case 0: return launch_variant<NW, 0, false>(p, sm_count, blocks_per_sm, stream);
+        case 2: return launch_variant<NW, 2, false>(p, sm_count, blocks_per_sm, stream);
+        case 3: return launch_variant<NW, 3, false>(p, sm_count, blocks_per_sm, stream);
+        case 4: return launch_variant<NW, 4, false>(p, sm_count, blocks_per_sm, stream);
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 }  // namespace mdist

@@ -1,11 +1,17 @@
 // enum_launch.cu -- level planning (product blocks and tiles) and the dispatch of
 // the enumerator instantiations by row width.
+#include <cmath>
+#include <map>
+#include <mutex>
+#include <tuple>
+#include <vector>
+
 #include "internal.h"
 
 namespace mdist {
 
 template <int NW>
-cudaError_t launch_nw(const EnumParams &, bool, int, int, cudaStream_t);
+cudaError_t launch_nw(const EnumParams &, int, bool, int, int, cudaStream_t);
 
 unsigned long long binom_host(int a, int b) {
     static unsigned long long tab[kMaxK + 1][kMaxK + 1];
@@ -61,29 +67,90 @@ bool plan_level(int k, int g, int nwords, EnumParams &p) {
     return true;
 }
 
+// Distribution of the OR-group lower bound for a codeword with iid Bernoulli(1/2)
+// bits (what the rows of a random code give): a bit position of a group is 1 in the
+// OR with probability 1 - 2^-c, c = words of the group that store that position.
+// Returned as the CDF over 0..n_bits, cached per (nwords, n_bits, group).
+static const std::vector<double> &lower_bound_cdf(int nwords, int n_bits, int gs) {
+    static std::mutex mu;
+    static std::map<std::tuple<int, int, int>, std::vector<double>> cache;
+    std::lock_guard<std::mutex> lock(mu);
+    auto key = std::make_tuple(nwords, n_bits, gs);
+    auto it = cache.find(key);
+    if (it != cache.end()) return it->second;
+    std::vector<double> dist(1, 1.0);
+    for (int q = 0; q < nwords; q += gs) {
+        for (int pos = 0; pos < 32; ++pos) {
+            int c = 0;
+            for (int w = q; w < q + gs && w < nwords; ++w)
+                if (w * 32 + pos < n_bits) ++c;
+            if (c == 0) continue;
+            const double p1 = 1.0 - std::ldexp(1.0, -c);
+            std::vector<double> nd(dist.size() + 1, 0.0);
+            for (size_t v = 0; v < dist.size(); ++v) {
+                nd[v] += dist[v] * (1.0 - p1);
+                nd[v + 1] += dist[v] * p1;
+            }
+            dist.swap(nd);
+        }
+    }
+    for (size_t v = 1; v < dist.size(); ++v) dist[v] += dist[v - 1];
+    return cache.emplace(key, std::move(dist)).first->second;
+}
+
+// Expected SM clocks per codeword: POPC retire at 16 per SM-clock, issue at 128 per
+// SM-clock (4 schedulers x 32 lanes).  Exact variant: nwords XOR + nwords POPC +
+// ~nwords adds/min.  Group variant: nwords fused XOR/OR (LOP3) + one POPC and one add
+// per group + compare/branch, plus the exact count when any of the 32 lanes of the
+// warp passes the bound (the branch is taken warp-wide).
+int choose_filter_group(int nwords, int n_bits, int thr) {
+    const double exact = std::fmax(nwords / 16.0, 3.0 * nwords / 128.0);
+    if (thr >= n_bits) return 0;
+    double best_cost = exact;
+    int best = 0;
+    for (int gs = 2; gs <= 4; ++gs) {
+        if (gs > nwords) break;
+        const int ng = (nwords + gs - 1) / gs;
+        double p = 0.0;
+        if (thr >= 0) {
+            const std::vector<double> &cdf = lower_bound_cdf(nwords, n_bits, gs);
+            p = cdf[(size_t)(thr < (int)cdf.size() ? thr : (int)cdf.size() - 1)];
+        }
+        const double pw = 1.0 - std::pow(1.0 - p, 32.0);
+        const double popc = ng + pw * nwords;
+        const double instr = nwords + 2.0 * ng + 2.0 + pw * (3.0 * nwords + 4.0);
+        const double cost = std::fmax(popc / 16.0, instr / 128.0);
+        if (cost < best_cost * 0.98) {
+            best_cost = cost;
+            best = gs;
+        }
+    }
+    return best;
+}
+
 size_t enum_smem_bytes(int k, int nwords) {
     return sizeof(uint32_t) * ((size_t)k * nwords + 33 * 33 + (size_t)kWarpsPerCta * walk_len_for(nwords) * nwords);
 }
 
-cudaError_t launch_enum_unit(const EnumParams &p, int nwords, bool hist_mode, int sm_count, int blocks_per_sm,
-                             cudaStream_t stream) {
+cudaError_t launch_enum_unit(const EnumParams &p, int nwords, int group, bool hist_mode, int sm_count,
+                             int blocks_per_sm, cudaStream_t stream) {
     switch (nwords) {
-        case 1: return launch_nw<1>(p, hist_mode, sm_count, blocks_per_sm, stream);
-        case 2: return launch_nw<2>(p, hist_mode, sm_count, blocks_per_sm, stream);
-        case 3: return launch_nw<3>(p, hist_mode, sm_count, blocks_per_sm, stream);
-        case 4: return launch_nw<4>(p, hist_mode, sm_count, blocks_per_sm, stream);
-        case 5: return launch_nw<5>(p, hist_mode, sm_count, blocks_per_sm, stream);
-        case 6: return launch_nw<6>(p, hist_mode, sm_count, blocks_per_sm, stream);
-        case 7: return launch_nw<7>(p, hist_mode, sm_count, blocks_per_sm, stream);
-        case 8: return launch_nw<8>(p, hist_mode, sm_count, blocks_per_sm, stream);
-        case 9: return launch_nw<9>(p, hist_mode, sm_count, blocks_per_sm, stream);
-        case 10: return launch_nw<10>(p, hist_mode, sm_count, blocks_per_sm, stream);
-        case 11: return launch_nw<11>(p, hist_mode, sm_count, blocks_per_sm, stream);
-        case 12: return launch_nw<12>(p, hist_mode, sm_count, blocks_per_sm, stream);
-        case 13: return launch_nw<13>(p, hist_mode, sm_count, blocks_per_sm, stream);
-        case 14: return launch_nw<14>(p, hist_mode, sm_count, blocks_per_sm, stream);
-        case 15: return launch_nw<15>(p, hist_mode, sm_count, blocks_per_sm, stream);
-        case 16: return launch_nw<16>(p, hist_mode, sm_count, blocks_per_sm, stream);
+        case 1: return launch_nw<1>(p, group, hist_mode, sm_count, blocks_per_sm, stream);
+        case 2: return launch_nw<2>(p, group, hist_mode, sm_count, blocks_per_sm, stream);
+        case 3: return launch_nw<3>(p, group, hist_mode, sm_count, blocks_per_sm, stream);
+        case 4: return launch_nw<4>(p, group, hist_mode, sm_count, blocks_per_sm, stream);
+        case 5: return launch_nw<5>(p, group, hist_mode, sm_count, blocks_per_sm, stream);
+        case 6: return launch_nw<6>(p, group, hist_mode, sm_count, blocks_per_sm, stream);
+        case 7: return launch_nw<7>(p, group, hist_mode, sm_count, blocks_per_sm, stream);
+        case 8: return launch_nw<8>(p, group, hist_mode, sm_count, blocks_per_sm, stream);
+        case 9: return launch_nw<9>(p, group, hist_mode, sm_count, blocks_per_sm, stream);
+        case 10: return launch_nw<10>(p, group, hist_mode, sm_count, blocks_per_sm, stream);
+        case 11: return launch_nw<11>(p, group, hist_mode, sm_count, blocks_per_sm, stream);
+        case 12: return launch_nw<12>(p, group, hist_mode, sm_count, blocks_per_sm, stream);
+        case 13: return launch_nw<13>(p, group, hist_mode, sm_count, blocks_per_sm, stream);
+        case 14: return launch_nw<14>(p, group, hist_mode, sm_count, blocks_per_sm, stream);
+        case 15: return launch_nw<15>(p, group, hist_mode, sm_count, blocks_per_sm, stream);
+        case 16: return launch_nw<16>(p, group, hist_mode, sm_count, blocks_per_sm, stream);
         default: return cudaErrorInvalidValue;
     }
 }

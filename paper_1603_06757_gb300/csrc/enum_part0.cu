@@ -3,8 +3,8 @@
 #include "enum_kernel.cuh"
 
 namespace mdist {
-template cudaError_t launch_nw<1>(const EnumParams &, bool, int, int, cudaStream_t);
-template cudaError_t launch_nw<2>(const EnumParams &, bool, int, int, cudaStream_t);
-template cudaError_t launch_nw<3>(const EnumParams &, bool, int, int, cudaStream_t);
-template cudaError_t launch_nw<4>(const EnumParams &, bool, int, int, cudaStream_t);
+template cudaError_t launch_nw<1>(const EnumParams &, int, bool, int, int, cudaStream_t);
+template cudaError_t launch_nw<2>(const EnumParams &, int, bool, int, int, cudaStream_t);
+template cudaError_t launch_nw<3>(const EnumParams &, int, bool, int, int, cudaStream_t);
+template cudaError_t launch_nw<4>(const EnumParams &, int, bool, int, int, cudaStream_t);
 }  // namespace mdist

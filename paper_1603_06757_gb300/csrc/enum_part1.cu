@@ -3,8 +3,8 @@
 #include "enum_kernel.cuh"
 
 namespace mdist {
-template cudaError_t launch_nw<5>(const EnumParams &, bool, int, int, cudaStream_t);
-template cudaError_t launch_nw<6>(const EnumParams &, bool, int, int, cudaStream_t);
-template cudaError_t launch_nw<7>(const EnumParams &, bool, int, int, cudaStream_t);
-template cudaError_t launch_nw<8>(const EnumParams &, bool, int, int, cudaStream_t);
+template cudaError_t launch_nw<5>(const EnumParams &, int, bool, int, int, cudaStream_t);
+template cudaError_t launch_nw<6>(const EnumParams &, int, bool, int, int, cudaStream_t);
+template cudaError_t launch_nw<7>(const EnumParams &, int, bool, int, int, cudaStream_t);
+template cudaError_t launch_nw<8>(const EnumParams &, int, bool, int, int, cudaStream_t);
 }  // namespace mdist

@@ -3,8 +3,8 @@
 #include "enum_kernel.cuh"
 
 namespace mdist {
-template cudaError_t launch_nw<9>(const EnumParams &, bool, int, int, cudaStream_t);
-template cudaError_t launch_nw<10>(const EnumParams &, bool, int, int, cudaStream_t);
-template cudaError_t launch_nw<11>(const EnumParams &, bool, int, int, cudaStream_t);
-template cudaError_t launch_nw<12>(const EnumParams &, bool, int, int, cudaStream_t);
+template cudaError_t launch_nw<9>(const EnumParams &, int, bool, int, int, cudaStream_t);
+template cudaError_t launch_nw<10>(const EnumParams &, int, bool, int, int, cudaStream_t);
+template cudaError_t launch_nw<11>(const EnumParams &, int, bool, int, int, cudaStream_t);
+template cudaError_t launch_nw<12>(const EnumParams &, int, bool, int, int, cudaStream_t);
 }  // namespace mdist

@@ -3,8 +3,8 @@
 #include "enum_kernel.cuh"
 
 namespace mdist {
-template cudaError_t launch_nw<13>(const EnumParams &, bool, int, int, cudaStream_t);
-template cudaError_t launch_nw<14>(const EnumParams &, bool, int, int, cudaStream_t);
-template cudaError_t launch_nw<15>(const EnumParams &, bool, int, int, cudaStream_t);
-template cudaError_t launch_nw<16>(const EnumParams &, bool, int, int, cudaStream_t);
+template cudaError_t launch_nw<13>(const EnumParams &, int, bool, int, int, cudaStream_t);
+template cudaError_t launch_nw<14>(const EnumParams &, int, bool, int, int, cudaStream_t);
+template cudaError_t launch_nw<15>(const EnumParams &, int, bool, int, int, cudaStream_t);
+template cudaError_t launch_nw<16>(const EnumParams &, int, bool, int, int, cudaStream_t);
 }  // namespace mdist

@@ -64,8 +64,12 @@ constexpr int lane_entries_per_thread(int nwords) { return nwords <= 4 ? 16 : (n
 constexpr int walk_len_for(int nwords) { return nwords <= 8 ? 256 : 128; }
 
 // Launch one unit's enumerator (enum_launch.cu).  hist == nullptr for the normal path.
-cudaError_t launch_enum_unit(const EnumParams &p, int nwords, bool hist_mode, int sm_count, int blocks_per_sm,
-                             cudaStream_t stream);
+cudaError_t launch_enum_unit(const EnumParams &p, int nwords, int group, bool hist_mode, int sm_count,
+                             int blocks_per_sm, cudaStream_t stream);
+
+// Filter variant for a unit: 0 (exact count for every codeword) or the OR-group size
+// 2, 3, 4 whose expected cost is least for this row width and threshold.
+int choose_filter_group(int nwords, int n_bits, int thr);
 size_t enum_smem_bytes(int k, int nwords);
 
 // Host-side binomial coefficients C(a, b), a <= 64 (enum_launch.cu).

@@ -80,12 +80,46 @@ __global__ void __launch_bounds__(kProbeThreads) probe_step4(int iters, unsigned
     if (threadIdx.x == 0) cycles[blockIdx.x] = (unsigned long long)(t1 - t0);
 }
 
+// The lower-bound step of the group variants for NW = 4 (GS = 4: one POPC of the OR
+// of the four XORed words; GS = 2: two POPC), threshold never reached.
+template <int GS>
+__global__ void __launch_bounds__(kProbeThreads) probe_step4_group(int iters, unsigned int *sink,
+                                                                   unsigned long long *cycles) {
+    unsigned int x[16][4];
+#pragma unroll
+    for (int p = 0; p < 16; ++p)
+#pragma unroll
+        for (int w = 0; w < 4; ++w) x[p][w] = (threadIdx.x + 1) * 2654435761u ^ (p * 4 + w) * 40503u;
+    unsigned int y0 = sink[1], y1 = sink[2], y2 = sink[3], y3 = sink[4];
+    const int thr = (int)sink[5] - 1;  // sink[5] = 0: bound never <= thr
+    int hits = 0;
+    __syncthreads();
+    const long long t0 = clock64();
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int p = 0; p < 16; ++p) {
+            int lb;
+            if (GS == 4) {
+                lb = __popc((x[p][0] ^ y0) | (x[p][1] ^ y1) | (x[p][2] ^ y2) | (x[p][3] ^ y3));
+            } else {
+                lb = __popc((x[p][0] ^ y0) | (x[p][1] ^ y1)) + __popc((x[p][2] ^ y2) | (x[p][3] ^ y3));
+            }
+            if (lb <= thr) hits += __popc(x[p][0] ^ y0) + __popc(x[p][1] ^ y1) + __popc(x[p][2] ^ y2);
+        }
+        y0 += 0x9e3779b9u; y1 ^= y0; y2 += y1; y3 ^= y2;
+    }
+    __syncthreads();
+    const long long t1 = clock64();
+    if (hits == 0x7fffffff) sink[0] = hits;
+    if (threadIdx.x == 0) cycles[blockIdx.x] = (unsigned long long)(t1 - t0);
+}
+
 }  // namespace
 }  // namespace mdist
 
 extern "C" int mdist_microbench(int which, int iters, double *ops_per_clock_per_sm, double *seconds) {
     using namespace mdist;
-    if (!ops_per_clock_per_sm || which < 0 || which > 2 || iters < 1) return MDIST_EINVAL;
+    if (!ops_per_clock_per_sm || which < 0 || which > 4 || iters < 1) return MDIST_EINVAL;
     int dev = 0, sms = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
         cudaGetLastError();
@@ -102,7 +136,9 @@ extern "C" int mdist_microbench(int which, int iters, double *ops_per_clock_per_
     cudaEventRecord(e0);
     if (which == 0) probe_popc<<<sms, kProbeThreads>>>(iters, sink, cyc);
     else if (which == 1) probe_lop3<<<sms, kProbeThreads>>>(iters, sink, cyc);
-    else probe_step4<<<sms, kProbeThreads>>>(iters, sink, cyc);
+    else if (which == 2) probe_step4<<<sms, kProbeThreads>>>(iters, sink, cyc);
+    else if (which == 3) probe_step4_group<2><<<sms, kProbeThreads>>>(iters, sink, cyc);
+    else probe_step4_group<4><<<sms, kProbeThreads>>>(iters, sink, cyc);
     cudaEventRecord(e1);
     int rc = cudaEventSynchronize(e1) == cudaSuccess && cudaGetLastError() == cudaSuccess ? MDIST_OK : MDIST_ECUDA;
     float ms = 0.f;

@@ -230,3 +230,16 @@ def test_side_stream(api):
     with torch.cuda.stream(s):
         got = api.min_distance(G, n)
     _assert_same_run(got, oracle.min_distance(G, n))
+
+
+@pytest.mark.parametrize("fg", [1, 2, 3, 4])
+@pytest.mark.parametrize("n,k,seed", [(120, 36, 3), (200, 40, 4), (300, 45, 5), (512, 40, 7), (150, 50, 9)])
+def test_filter_variants_identical(api, fg, n, k, seed):
+    # every enumerator variant (exact, OR-groups of 2, 3, 4 words) gives the same run
+    G = synth.random_systematic(n, k, seed)
+    want = oracle.min_distance(G, n)
+    if sum(int(c) for c in want["counts"].ravel()) > 3e9:
+        pytest.skip("oracle too slow for this draw")
+    with api.Code(G, n, filter_group=fg) as c:
+        got = c.min_distance()
+    _assert_same_run(got, want)

@@ -242,3 +242,22 @@ def test_level_plan_covers_level(lib, k, nw):
         assert seen_i == list(range(max(0, g - k2), min(g, k1) + 1))
         assert total == math.comb(k, g)  # Vandermonde: the blocks partition the level
         assert tt == tiles
+
+
+def _choice(lib, nw, nb, thr):
+    g = ctypes.c_int()
+    assert lib.mdist_debug_filter_choice(nw, nb, thr, ctypes.byref(g)) == 0
+    return g.value
+
+
+def test_filter_choice(lib):
+    # threshold at or above the row width: every codeword is a candidate -> exact
+    assert _choice(lib, 4, 128, 128) == 0
+    # one word: nothing to group
+    assert _choice(lib, 1, 20, 3) == 0
+    # the last levels of [192,64] (reduced weight <= 24 of 128 bits): a one-POPC bound
+    assert _choice(lib, 4, 128, 24) in (2, 4)
+    # threshold near the mean of a random codeword: the bound rarely rejects -> exact
+    assert _choice(lib, 4, 128, 62) == 0
+    # [300,50]-like rows (250 bits, threshold ~67): pairs of words
+    assert _choice(lib, 8, 250, 67) in (2, 3)
