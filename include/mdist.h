@@ -172,6 +172,40 @@ const char *mdist_strerror(int err);
  * arithmetic. */
 int mdist_device_info(int *sm_count, int *max_sm_clock_khz, int *cc_major, int *cc_minor);
 
+/* ---- batched engine ------------------------------------------------------------ */
+
+/* Many codes of different n, k through Alg. 1 together on one GPU.  Per round every
+ * active code enumerates its next level (all its units); the rounds run as one CUDA
+ * graph (persistent enumerator grids per row width, per-code state machines on the
+ * device), relaunched only while codes remain active.  Each code's result equals
+ * mdist_min_distance's for that code (same d, key, message, witness, counters).
+ * Options as for mdist_prepare (check_per_matrix, max_sets, blocks_per_sm, allocator). */
+typedef struct mdist_batch mdist_batch;
+
+int mdist_batch_create(const mdist_options *opts, void *cuda_stream, mdist_batch **out);
+
+/* Add a code (host G, copied; information sets computed here).  wstar_hint > 1: a
+ * predicted termination level; levels 1 .. wstar_hint-1 are then enumerated in the
+ * first round (sizing only: results never depend on it).  *index = the code's index.
+ * Codes cannot be added after mdist_batch_run. */
+int mdist_batch_add(mdist_batch *b, const uint64_t *G, int n, int k, int words_per_row, int wstar_hint, int *index);
+
+/* Run every code to completion.  rounds_per_graph <= 0: chosen from the hints.
+ * Device buffers are allocated for the run and released before returning. */
+int mdist_batch_run(mdist_batch *b, int rounds_per_graph);
+
+/* Per-code result, as mdist_result (stats->launches = rounds the code took part in).
+ * Returns the code's own error (e.g. MDIST_ERANGE) if it could not finish. */
+int mdist_batch_result(const mdist_batch *b, int index, int *d, uint64_t *witness, uint64_t *message,
+                       mdist_key *key, mdist_stats *stats);
+
+/* Run totals: codes, graph launches, rounds, summed CUDA-event time of the graph
+ * launches (ms) and host wall time of mdist_batch_run (s). */
+int mdist_batch_info(const mdist_batch *b, int *ncodes, int *graph_launches, int *rounds, double *gpu_ms,
+                     double *seconds);
+
+void mdist_batch_free(mdist_batch *b);
+
 /* Instruction-throughput probe on the current device, for roofline arithmetic:
  * which = 0: 32-bit POPC, 1: 3-input XOR (LOP3), 2: enumerator inner step (XOR + POPC
  * over 4 words, sum, running min), 3 / 4: the lower-bound step of filter groups of 2 /

@@ -108,6 +108,15 @@ SIGNATURES = {
     "mdist_device_info": (ctypes.c_int, [PI, PI, PI, PI]),
     "mdist_microbench": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                                         ctypes.POINTER(ctypes.c_double)]),
+    "mdist_batch_create": (ctypes.c_int, [ctypes.POINTER(Options), ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]),
+    "mdist_batch_add": (ctypes.c_int, [ctypes.c_void_p, P64, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                       PI]),
+    "mdist_batch_run": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "mdist_batch_result": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, PI, P64, P64, ctypes.POINTER(Key),
+                                          ctypes.POINTER(Stats)]),
+    "mdist_batch_info": (ctypes.c_int, [ctypes.c_void_p, PI, PI, PI, ctypes.POINTER(ctypes.c_double),
+                                        ctypes.POINTER(ctypes.c_double)]),
+    "mdist_batch_free": (None, [ctypes.c_void_p]),
     "mdist_partition_host": (ctypes.c_int, [P64, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, PI, PI,
                                             PI32, P64, P64]),
     "mdist_debug_set_rows": (ctypes.c_int, [P64, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, PI, PI, PI,

@@ -262,3 +262,76 @@ def microbench(which: str, iters: int = 20000) -> dict:
     s = ctypes.c_double()
     L.check(L.lib().mdist_microbench(idx, int(iters), ctypes.byref(v), ctypes.byref(s)), "mdist_microbench")
     return {"per_clock_per_sm": v.value, "seconds": s.value}
+
+
+class Batch:
+    """Many codes through Alg. 1 together (mdist_batch_*): one graph of rounds."""
+
+    def __init__(self, *, check_per_matrix: bool = False, max_sets: int = 0, blocks_per_sm: int = 0, stream=None,
+                 torch_alloc: bool = True):
+        torch = _torch()
+        self._lib = L.lib()
+        self._stream = stream if stream is not None else torch.cuda.current_stream()
+        self._alloc = _TorchAllocator(torch, self._stream.device) if torch_alloc else None
+        opts = L.Options()
+        opts.check_per_matrix = 1 if check_per_matrix else 0
+        opts.max_sets = int(max_sets)
+        opts.blocks_per_sm = int(blocks_per_sm)
+        if self._alloc is not None:
+            opts.dev_alloc = self._alloc.alloc_cb
+            opts.dev_free = self._alloc.free_cb
+        self._opts = opts
+        h = ctypes.c_void_p()
+        L.check(self._lib.mdist_batch_create(ctypes.byref(opts), ctypes.c_void_p(self._stream.cuda_stream),
+                                             ctypes.byref(h)), "mdist_batch_create")
+        self._h = h
+        self._shapes = []
+
+    def add(self, G, n: int, wstar_hint: int = 0) -> int:
+        G = as_packed(G, n)
+        k, W = G.shape
+        idx = ctypes.c_int()
+        L.check(self._lib.mdist_batch_add(self._h, _p64(G), int(n), k, W, int(wstar_hint), ctypes.byref(idx)),
+                "mdist_batch_add")
+        self._shapes.append((n, k, W))
+        return idx.value
+
+    def run(self, rounds_per_graph: int = 0) -> None:
+        L.check(self._lib.mdist_batch_run(self._h, int(rounds_per_graph)), "mdist_batch_run")
+
+    def info(self) -> dict:
+        nc, gl, rd = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        ms, sec = ctypes.c_double(), ctypes.c_double()
+        L.check(self._lib.mdist_batch_info(self._h, ctypes.byref(nc), ctypes.byref(gl), ctypes.byref(rd),
+                                           ctypes.byref(ms), ctypes.byref(sec)), "mdist_batch_info")
+        return {"codes": nc.value, "graph_launches": gl.value, "rounds": rd.value, "gpu_ms": ms.value,
+                "seconds": sec.value}
+
+    def result(self, index: int) -> dict:
+        n, k, W = self._shapes[index]
+        d = ctypes.c_int()
+        wit = np.zeros(W, dtype=np.uint64)
+        msg = np.zeros(1, dtype=np.uint64)
+        key = L.Key()
+        st = L.Stats()
+        rc = self._lib.mdist_batch_result(self._h, int(index), ctypes.byref(d), _p64(wit), _p64(msg),
+                                          ctypes.byref(key), ctypes.byref(st))
+        L.check(rc, "mdist_batch_result")
+        return _result_dict(d.value, wit, msg, key, st)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.mdist_batch_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

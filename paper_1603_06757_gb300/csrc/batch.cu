@@ -1,0 +1,650 @@
+// batch.cu -- the batched engine: kernels (layout in batch_kernels.cuh) and the C-ABI
+// mdist_batch_* (include/mdist.h).  The rounds of a run are captured once into a CUDA
+// graph and launched as one graph; the graph is relaunched only while some code is
+// still active after all of its rounds.
+#include <algorithm>
+#include <chrono>
+#include <climits>
+#include <cstring>
+#include <map>
+#include <new>
+#include <utility>
+#include <vector>
+
+#include "batch_kernels.cuh"
+#include "prep.h"
+
+namespace mdist {
+
+static __constant__ BinomTable64 c_binom_b = make_binom_table64();
+
+__device__ __forceinline__ unsigned long long binom_dev(int a, int b) {
+    return (a < 0 || b < 0 || b > a) ? 0ull : c_binom_b.v[a][b];
+}
+
+struct DevBinomB {
+    __device__ __forceinline__ unsigned long long operator()(int a, int b) const { return c_binom_b.v[a][b]; }
+};
+
+__device__ __forceinline__ int set_bound_dev(int h, int k, int r) {
+    const int v = h + 1 - (k - r);
+    return v > 0 ? v : 0;
+}
+
+// Tiles of unit (k, g) with row width nwords, block by block (the plan of plan_level):
+// plan[b] = first tile of block b.  Returns the total.
+__device__ unsigned long long plan_unit_dev(int k, int g, int nwords, unsigned long long *plan, int *nblocks) {
+    const int k1 = (k + 1) / 2, k2 = k - k1;
+    const unsigned long long lane_chunk = 32ull * (unsigned long long)lane_entries_per_thread(nwords);
+    const unsigned long long walk_chunk = (unsigned long long)walk_len_for(nwords);
+    const int ilo = g - k2 > 0 ? g - k2 : 0;
+    const int ihi = g < k1 ? g : k1;
+    unsigned long long tiles = 0;
+    int nb = 0;
+    for (int i = ilo; i <= ihi; ++i) {
+        const unsigned long long n1 = binom_dev(k1, i), n2 = binom_dev(k2, g - i);
+        const unsigned long long ln = n1 >= n2 ? n1 : n2, wn = n1 >= n2 ? n2 : n1;
+        plan[nb++] = tiles;
+        tiles += ((ln + lane_chunk - 1) / lane_chunk) * ((wn + walk_chunk - 1) / walk_chunk);
+    }
+    *nblocks = nb;
+    return tiles;
+}
+
+__global__ void batch_round_begin(BatchDev D) {
+    const int t = threadIdx.x;
+    if (t < kBatchBuckets) {
+        D.bucket_packed[t] = 0;
+        D.tile_ctr[t] = 0;
+    }
+    if (t == 0) {
+        *D.item_ctr = 0;
+        *D.active_ctr = 0;
+    }
+}
+
+// One thread per code: this round's levels and one item per unit.
+__global__ void batch_prep(BatchDev D) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= D.ncodes) return;
+    BatchCode &C = D.codes[c];
+    C.nitems = 0;
+    if (!C.active) return;
+    const int g0 = C.g_next;
+    int g1 = g0 + (C.spec > 0 ? C.spec : 1);
+    if (g1 > C.k + 1) g1 = C.k + 1;
+    int gl = g0;  // levels past the device key range are not started
+    while (gl < g1 && binom_dev(C.k, gl) < (1ull << kKeyRankBits)) ++gl;
+    if (gl == g0) {
+        C.status = MDIST_ERANGE;
+        C.active = 0;
+        return;
+    }
+    g1 = gl;
+    const int n_items = (g1 - g0) * C.m;
+    const int item0 = atomicAdd(D.item_ctr, n_items);
+    if (item0 + n_items > D.item_cap) {  // the host sizes item_cap for every round
+        C.status = MDIST_ENOMEM;
+        C.active = 0;
+        return;
+    }
+    C.item0 = item0;
+    C.nitems = n_items;
+    D.codeU[c] = (unsigned int)(C.have_key ? C.key_w : C.U);
+    int it = item0;
+    for (int g = g0; g < g1; ++g) {
+        for (int j = 0; j < C.m; ++j, ++it) {
+            const BatchUnit &u = D.units[C.unit0 + j];
+            BatchItem &I = D.items[it];
+            I.unit = C.unit0 + j;
+            I.code = c;
+            I.g = g;
+            I.tiles = plan_unit_dev(C.k, g, u.nwords, D.plans + (size_t)it * kBatchMaxPlan, &I.nblocks);
+            D.slots[it].key = kNoKey;
+            D.slots[it].count = 0;
+            const int b = u.nwords - 1;
+            const unsigned long long old =
+                atomicAdd(&D.bucket_packed[b], (1ull << kTileBits) | I.tiles);
+            BucketEntry &E = D.bucket_items[(size_t)b * D.item_cap + (size_t)(old >> kTileBits)];
+            E.tile_begin = old & ((1ull << kTileBits) - 1);
+            E.item = it;
+            E.pad = 0;
+        }
+    }
+}
+
+// One thread per code: fold this round's units in (g, j) order, as mdist_run does.
+__global__ void batch_update(BatchDev D) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= D.ncodes) return;
+    BatchCode &C = D.codes[c];
+    if (!C.active || C.nitems == 0) return;
+    C.rounds += 1;
+    const int g0 = D.items[C.item0].g;
+    const int nlev = C.nitems / C.m;
+    int fin = 0;
+    for (int l = 0; l < nlev && !fin; ++l) {
+        const int g = g0 + l;
+        for (int j = 0; j < C.m && !fin; ++j) {
+            const ItemSlot s = D.slots[C.item0 + l * C.m + j];
+            D.counts[C.counts_off + (unsigned long long)g * C.m + j] = s.count;
+            C.combos += s.count;
+            C.g_final = g;
+            C.j_final = j;
+            if (s.key != kNoKey) {
+                const int w = (int)(s.key >> kKeyRankBits);
+                if (!C.have_key || w < C.key_w) {
+                    C.have_key = 1;
+                    C.key_w = w;
+                    C.key_g = g;
+                    C.key_j = j;
+                    C.key_rank = s.key & ((1ull << kKeyRankBits) - 1);
+                }
+                if (w < C.U) C.U = w;
+            }
+            if (C.per_matrix) {
+                int Lm = 0;
+                for (int i = 0; i < C.m; ++i) Lm += set_bound_dev(i <= j ? g : g - 1, C.k, D.units[C.unit0 + i].rank);
+                if (Lm > C.L) C.L = Lm;
+                if (C.L >= C.U) fin = 1;
+            }
+        }
+        if (fin) break;
+        if (!C.per_matrix) {  // Alg. 1, line 7, for sets of any rank
+            int Lg = 0;
+            for (int i = 0; i < C.m; ++i) Lg += set_bound_dev(g, C.k, D.units[C.unit0 + i].rank);
+            C.L = Lg;
+            if (C.L >= C.U) fin = 1;
+        }
+        if (g >= C.k) fin = 1;
+    }
+    if (fin) {
+        C.active = 0;
+    } else {
+        C.g_next = g0 + nlev;
+        C.spec = 1;
+        atomicAdd(D.active_ctr, 1);
+    }
+}
+
+// Persistent enumerator of one bucket (row width NW) for one round.
+template <int NW>
+__global__ void __launch_bounds__(kCtaThreads) batch_enum(const __grid_constant__ BatchDev D, int bucket) {
+    constexpr int XP = lane_entries_per_thread(NW);
+    constexpr int YL = walk_len_for(NW);
+    constexpr int PER = YL / 32;
+    extern __shared__ __align__(16) uint32_t smem[];
+    uint32_t *s_bn = smem;                                     // 33 x 33
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t *wrows = s_bn + kBn * kBn + warp * (kMaxK * NW + YL * NW);  // this warp's rows
+    uint32_t *wbuf = wrows + kMaxK * NW;                                 // and walk buffer
+    for (int i = threadIdx.x; i < kBn * kBn; i += blockDim.x) s_bn[i] = (uint32_t)c_binom_b.v[i / kBn][i % kBn];
+    __syncthreads();
+    const unsigned long long packed = D.bucket_packed[bucket];
+    const unsigned long long total = packed & ((1ull << kTileBits) - 1);
+    const int nentries = (int)(packed >> kTileBits);
+    const BucketEntry *entries = D.bucket_items + (size_t)bucket * D.item_cap;
+    int staged = -1;
+    for (;;) {
+        unsigned long long tile = 0;
+        if (lane == 0) tile = atomicAdd(&D.tile_ctr[bucket], 1ull);
+        tile = __shfl_sync(0xffffffffu, tile, 0);
+        if (tile >= total) break;
+        int lo = 0, hi = nentries - 1;  // last entry whose first tile is <= tile
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (entries[mid].tile_begin <= tile) lo = mid;
+            else hi = mid - 1;
+        }
+        const BucketEntry E = entries[lo];
+        const int it = E.item;
+        const BatchItem I = D.items[it];
+        const BatchUnit u = D.units[I.unit];
+        if (I.unit != staged) {
+            __syncwarp();
+            for (int w = lane; w < u.k * NW; w += 32) wrows[w] = D.rows[u.rows_off + w];
+            __syncwarp();
+            staged = I.unit;
+        }
+        // product block of this tile within the unit
+        const unsigned long long tl = tile - E.tile_begin;
+        const unsigned long long *plan = D.plans + (size_t)it * kBatchMaxPlan;
+        int b = 0;
+        while (b + 1 < I.nblocks && plan[b + 1] <= tl) ++b;
+        const int k1 = u.k1, k2 = u.k2, g = I.g;
+        const int i = (g - k2 > 0 ? g - k2 : 0) + b;
+        const unsigned long long n1 = binom_dev(k1, i), n2 = binom_dev(k2, g - i);
+        const int lane_half = n1 >= n2 ? 0 : 1;
+        const int lane_t = lane_half ? g - i : i, walk_t = lane_half ? i : g - i;
+        const unsigned long long lane_n = lane_half ? n2 : n1, walk_n = lane_half ? n1 : n2;
+        const unsigned long long walk_chunks = (walk_n + YL - 1) / YL;
+        const unsigned long long t = tl - plan[b];
+        const unsigned long long lane_chunk = t / walk_chunks;
+        const unsigned long long walk_chunk = t - lane_chunk * walk_chunks;
+        const int lane_kh = lane_half ? k2 : k1, walk_kh = lane_half ? k1 : k2;
+        const uint32_t *lane_rows = wrows + (lane_half ? k1 : 0) * NW;
+        const uint32_t *walk_rows = wrows + (lane_half ? 0 : k1) * NW;
+        const int base = u.full_rank ? g : 0;
+        int thr = (int)(*(volatile unsigned int *)&D.codeU[I.code]) - base;
+        const int tc = thr < -1 ? -1 : (thr > u.n_bits ? u.n_bits : thr);
+        const int gs = D.gs_table[u.gs_off + tc + 1];
+
+        const unsigned long long chunk_first = lane_chunk * (unsigned long long)(32 * XP);
+        const unsigned long long e_first = chunk_first + (unsigned long long)lane * XP;
+        const long long left = (long long)lane_n - (long long)e_first;
+        const int nvalid = left <= 0 ? 0 : (left >= XP ? XP : (int)left);
+        const uint32_t e0 = (uint32_t)(e_first < lane_n ? e_first : lane_n - 1);
+        uint32_t x[XP][NW];
+        build_lane_entries<NW, XP>(x, s_bn, lane_rows, lane_kh, lane_t, e0, nvalid);
+        const unsigned long long w_first = walk_chunk * (unsigned long long)YL;
+        const unsigned long long wleft = walk_n - w_first;
+        const int walk_len = wleft >= (unsigned long long)YL ? YL : (int)wleft;
+        stage_walk<NW>(wbuf, s_bn, walk_rows, walk_kh, walk_t, w_first, walk_len, PER, lane);
+        __syncwarp();
+
+        auto cand = [&](int p, int s, int acc) {
+            const uint32_t lm = unrank_colex(s_bn, lane_kh, lane_t, e0 + (uint32_t)p);
+            const uint32_t wm = unrank_colex(s_bn, walk_kh, walk_t, (uint32_t)(w_first + s));
+            const unsigned long long h1 = lane_half ? wm : lm, h2 = lane_half ? lm : wm;
+            const unsigned long long rank = lexrank64(h1 | (h2 << k1), u.k, g, DevBinomB{});
+            const int wt = acc + base;
+            atomicMin(&D.slots[it].key, ((unsigned long long)wt << kKeyRankBits) | rank);
+            atomicMin(&D.codeU[I.code], (unsigned int)wt);
+            thr = acc;
+        };
+        switch (gs) {
+            case 2: walk_tile<NW, XP, 2, false>(x, wbuf, walk_len, nvalid, thr, nullptr, base, cand); break;
+            case 3: walk_tile<NW, XP, 3, false>(x, wbuf, walk_len, nvalid, thr, nullptr, base, cand); break;
+            case 4: walk_tile<NW, XP, 4, false>(x, wbuf, walk_len, nvalid, thr, nullptr, base, cand); break;
+            default: walk_tile<NW, XP, 0, false>(x, wbuf, walk_len, nvalid, thr, nullptr, base, cand); break;
+        }
+        if (lane == 0) {
+            const unsigned long long in_chunk = lane_n - chunk_first;
+            const unsigned long long valid = in_chunk < (unsigned long long)(32 * XP) ? in_chunk : 32 * XP;
+            atomicAdd(&D.slots[it].count, valid * (unsigned long long)walk_len);
+        }
+        __syncwarp();
+    }
+}
+
+template <int NW>
+size_t batch_smem_bytes() {
+    return sizeof(uint32_t) * ((size_t)kBn * kBn + (size_t)kWarpsPerCta * (kMaxK * NW + walk_len_for(NW) * NW));
+}
+
+template <int NW>
+cudaError_t batch_enum_prepare(int *grid_per_sm) {
+    const size_t smem = batch_smem_bytes<NW>();
+    cudaError_t e = cudaFuncSetAttribute(batch_enum<NW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(grid_per_sm, batch_enum<NW>, kCtaThreads, smem);
+}
+
+template <int NW>
+void batch_enum_launch(const BatchDev &D, int bucket, int grid, cudaStream_t st) {
+    batch_enum<NW><<<grid, kCtaThreads, batch_smem_bytes<NW>(), st>>>(D, bucket);
+}
+
+#define MDIST_NW_CASES(X) X(1) X(2) X(3) X(4) X(5) X(6) X(7) X(8) X(9) X(10) X(11) X(12) X(13) X(14) X(15) X(16)
+
+static cudaError_t batch_prepare_nw(int nw, int *occ) {
+    switch (nw) {
+#define C(N) case N: return batch_enum_prepare<N>(occ);
+        MDIST_NW_CASES(C)
+#undef C
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+static void batch_launch_nw(int nw, const BatchDev &D, int grid, cudaStream_t st) {
+    switch (nw) {
+#define C(N) case N: batch_enum_launch<N>(D, N - 1, grid, st); break;
+        MDIST_NW_CASES(C)
+#undef C
+        default: break;
+    }
+}
+
+}  // namespace mdist
+
+// ----------------------------------------------------------------------------------
+// host side
+// ----------------------------------------------------------------------------------
+
+using namespace mdist;
+
+namespace {
+
+struct HostCode {
+    int n = 0, k = 0, W = 0, wstar = 0;
+    std::vector<uint64_t> G;
+    Partition part;
+    std::vector<DeviceRows> rows;
+};
+
+unsigned long long host_unrank_lex(int k, int g, unsigned long long rank) {
+    unsigned long long r = binom_host(k, g) - 1 - rank, mask = 0;
+    int d = k - 1;
+    for (int t = g; t >= 1; --t) {
+        while (binom_host(d, t) > r) --d;
+        r -= binom_host(d, t);
+        mask |= 1ull << (k - 1 - d);
+        --d;
+    }
+    return mask;
+}
+
+}  // namespace
+
+struct mdist_batch {
+    mdist_options opt{};
+    cudaStream_t stream = nullptr;
+    int device = 0, sm_count = 0;
+    std::vector<HostCode> codes;
+    std::vector<void *> allocs;
+    std::vector<BatchCode> res;              // per code, after the run
+    std::vector<unsigned long long> counts;  // all codes
+    std::vector<unsigned long long> counts_off;
+    bool ran = false;
+    int rounds_per_graph = 0, graph_launches = 0, rounds = 0;
+    double seconds = 0, gpu_ms = 0;
+    int grid_override = 0;
+};
+
+namespace {
+
+void *balloc(mdist_batch *b, size_t bytes) {
+    void *p = nullptr;
+    if (b->opt.dev_alloc) p = b->opt.dev_alloc(bytes ? bytes : 1, b->opt.alloc_ctx);
+    else if (cudaMalloc(&p, bytes ? bytes : 1) != cudaSuccess) p = nullptr;
+    if (p) b->allocs.push_back(p);
+    return p;
+}
+
+void bfree_all(mdist_batch *b) {
+    for (void *p : b->allocs) {
+        if (b->opt.dev_free) b->opt.dev_free(p, b->opt.alloc_ctx);
+        else cudaFree(p);
+    }
+    b->allocs.clear();
+}
+
+}  // namespace
+
+extern "C" {
+
+int mdist_batch_create(const mdist_options *opts, void *cuda_stream, mdist_batch **out) {
+    if (!out) return MDIST_EINVAL;
+    *out = nullptr;
+    mdist_batch *b = new (std::nothrow) mdist_batch();
+    if (!b) return MDIST_ENOMEM;
+    if (opts) b->opt = *opts;
+    if (b->opt.max_sets <= 0 || b->opt.max_sets > MDIST_MAX_SETS) b->opt.max_sets = MDIST_MAX_SETS;
+    b->stream = (cudaStream_t)cuda_stream;
+    if (cudaGetDevice(&b->device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&b->sm_count, cudaDevAttrMultiProcessorCount, b->device) != cudaSuccess) {
+        cudaGetLastError();
+        delete b;
+        return MDIST_ECUDA;
+    }
+    *out = b;
+    return MDIST_OK;
+}
+
+int mdist_batch_add(mdist_batch *b, const uint64_t *G, int n, int k, int words_per_row, int wstar_hint, int *index) {
+    if (!b || !G || b->ran) return MDIST_EINVAL;
+    if (k < 1 || k > MDIST_MAX_K || n <= k || n > MDIST_MAX_N || words_per_row < (n + 63) / 64) return MDIST_EINVAL;
+    for (int r = 0; r < k; ++r)
+        for (int i = n; i < 64 * words_per_row; ++i)
+            if ((G[(size_t)r * words_per_row + (i >> 6)] >> (i & 63)) & 1ull) return MDIST_EINVAL;
+    HostCode hc;
+    hc.n = n;
+    hc.k = k;
+    hc.W = words_per_row;
+    hc.wstar = wstar_hint < 0 ? 0 : wstar_hint;
+    hc.G.assign(G, G + (size_t)k * words_per_row);
+    const int rc = partition_info_sets(G, n, k, words_per_row, b->opt.max_sets, hc.part);
+    if (rc != MDIST_OK) return rc;
+    hc.rows.resize(hc.part.sets.size());
+    for (size_t j = 0; j < hc.part.sets.size(); ++j) build_rows(hc.part, (int)j, hc.rows[j]);
+    if (index) *index = (int)b->codes.size();
+    b->codes.push_back(std::move(hc));
+    return MDIST_OK;
+}
+
+int mdist_batch_run(mdist_batch *b, int rounds_per_graph) {
+    if (!b || b->ran) return MDIST_EINVAL;
+    const auto t0 = std::chrono::steady_clock::now();
+    const int C = (int)b->codes.size();
+    b->ran = true;
+    if (C == 0) return MDIST_OK;
+    // ---- host tables ----
+    std::vector<BatchUnit> units;
+    std::vector<uint32_t> rows;
+    std::vector<unsigned char> gs_table;
+    std::map<std::pair<int, int>, unsigned int> gs_off;
+    std::vector<BatchCode> codes((size_t)C);
+    b->counts_off.assign((size_t)C, 0);
+    unsigned long long ncounts = 0;
+    long long item_cap = 0;
+    bool present[kBatchBuckets] = {};
+    int max_spec = 1;
+    for (int c = 0; c < C; ++c) {
+        const HostCode &h = b->codes[(size_t)c];
+        BatchCode &S = codes[(size_t)c];
+        std::memset(&S, 0, sizeof S);
+        S.n = h.n;
+        S.k = h.k;
+        S.m = (int)h.part.sets.size();
+        S.unit0 = (int)units.size();
+        S.active = 1;
+        S.status = MDIST_OK;
+        S.g_next = 1;
+        // predicted termination level: take the levels below it in the first round
+        S.spec = h.wstar > 1 ? std::min(h.wstar - 1, h.k) : 1;
+        max_spec = std::max(max_spec, S.spec);
+        S.U = h.n - h.k + 1;  // Alg. 1, line 1
+        S.L = 1;
+        S.j_final = -1;
+        S.per_matrix = b->opt.check_per_matrix ? 1 : 0;
+        S.counts_off = ncounts;
+        b->counts_off[(size_t)c] = ncounts;
+        ncounts += (unsigned long long)(h.k + 1) * S.m;
+        item_cap += (long long)S.m * S.spec;
+        for (int j = 0; j < S.m; ++j) {
+            const DeviceRows &dr = h.rows[(size_t)j];
+            BatchUnit u{};
+            u.rows_off = (unsigned int)rows.size();
+            u.k = h.k;
+            u.k1 = (h.k + 1) / 2;
+            u.k2 = h.k - u.k1;
+            u.nwords = dr.nwords;
+            u.n_bits = dr.n_bits;
+            u.full_rank = dr.full_rank ? 1 : 0;
+            u.rank = h.part.sets[(size_t)j].rank;
+            u.code = c;
+            auto key = std::make_pair(dr.nwords, dr.n_bits);
+            auto it = gs_off.find(key);
+            if (it == gs_off.end()) {
+                const unsigned int off = (unsigned int)gs_table.size();
+                for (int thr = -1; thr <= dr.n_bits; ++thr)
+                    gs_table.push_back((unsigned char)choose_filter_group(dr.nwords, dr.n_bits, thr));
+                it = gs_off.emplace(key, off).first;
+            }
+            u.gs_off = it->second;
+            rows.insert(rows.end(), dr.words.begin(), dr.words.end());
+            units.push_back(u);
+            present[dr.nwords - 1] = true;
+        }
+    }
+    // ---- device buffers ----
+    BatchDev D{};
+    const size_t cap = (size_t)item_cap;
+    uint32_t *d_rows = (uint32_t *)balloc(b, rows.size() * sizeof(uint32_t));
+    BatchUnit *d_units = (BatchUnit *)balloc(b, units.size() * sizeof(BatchUnit));
+    unsigned char *d_gs = (unsigned char *)balloc(b, gs_table.size());
+    BatchCode *d_codes = (BatchCode *)balloc(b, codes.size() * sizeof(BatchCode));
+    unsigned long long *d_counts = (unsigned long long *)balloc(b, ncounts * sizeof(unsigned long long));
+    BatchItem *d_items = (BatchItem *)balloc(b, cap * sizeof(BatchItem));
+    ItemSlot *d_slots = (ItemSlot *)balloc(b, cap * sizeof(ItemSlot));
+    unsigned long long *d_plans = (unsigned long long *)balloc(b, cap * kBatchMaxPlan * sizeof(unsigned long long));
+    BucketEntry *d_bucket = (BucketEntry *)balloc(b, (size_t)kBatchBuckets * cap * sizeof(BucketEntry));
+    unsigned long long *d_packed = (unsigned long long *)balloc(b, 2 * kBatchBuckets * sizeof(unsigned long long));
+    unsigned int *d_codeU = (unsigned int *)balloc(b, (size_t)C * sizeof(unsigned int));
+    int *d_ctr = (int *)balloc(b, 2 * sizeof(int));
+    if (!d_rows || !d_units || !d_gs || !d_codes || !d_counts || !d_items || !d_slots || !d_plans || !d_bucket ||
+        !d_packed || !d_codeU || !d_ctr) {
+        bfree_all(b);
+        return MDIST_ENOMEM;
+    }
+    cudaStream_t st = b->stream;
+    bool ok = cudaMemcpyAsync(d_rows, rows.data(), rows.size() * sizeof(uint32_t), cudaMemcpyHostToDevice, st) ==
+                  cudaSuccess &&
+              cudaMemcpyAsync(d_units, units.data(), units.size() * sizeof(BatchUnit), cudaMemcpyHostToDevice, st) ==
+                  cudaSuccess &&
+              cudaMemcpyAsync(d_gs, gs_table.data(), gs_table.size(), cudaMemcpyHostToDevice, st) == cudaSuccess &&
+              cudaMemcpyAsync(d_codes, codes.data(), codes.size() * sizeof(BatchCode), cudaMemcpyHostToDevice, st) ==
+                  cudaSuccess &&
+              cudaMemsetAsync(d_counts, 0, ncounts * sizeof(unsigned long long), st) == cudaSuccess;
+    if (!ok) { bfree_all(b); return MDIST_ECUDA; }
+    D.rows = d_rows;
+    D.units = d_units;
+    D.gs_table = d_gs;
+    D.codes = d_codes;
+    D.counts = d_counts;
+    D.items = d_items;
+    D.slots = d_slots;
+    D.plans = d_plans;
+    D.bucket_items = d_bucket;
+    D.bucket_packed = d_packed;
+    D.tile_ctr = d_packed + kBatchBuckets;
+    D.codeU = d_codeU;
+    D.item_ctr = d_ctr;
+    D.active_ctr = d_ctr + 1;
+    D.ncodes = C;
+    D.item_cap = (int)cap;
+    // ---- grids per bucket ----
+    int grid[kBatchBuckets] = {};
+    for (int nb = 0; nb < kBatchBuckets; ++nb) {
+        if (!present[nb]) continue;
+        int occ = 0;
+        if (batch_prepare_nw(nb + 1, &occ) != cudaSuccess || occ < 1) { bfree_all(b); return MDIST_ECUDA; }
+        const int per_sm = b->opt.blocks_per_sm > 0 && b->opt.blocks_per_sm < occ ? b->opt.blocks_per_sm : occ;
+        grid[nb] = b->sm_count * per_sm;
+    }
+    // ---- capture the rounds into one graph ----
+    const int R = rounds_per_graph > 0 ? rounds_per_graph : std::max(4, std::min(16, max_spec + 2));
+    b->rounds_per_graph = R;
+    const int tb = 128, cb = (C + tb - 1) / tb;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) { bfree_all(b); return MDIST_ECUDA; }
+    for (int r = 0; r < R; ++r) {
+        batch_round_begin<<<1, 32, 0, st>>>(D);
+        batch_prep<<<cb, tb, 0, st>>>(D);
+        for (int nb = 0; nb < kBatchBuckets; ++nb)
+            if (present[nb]) batch_launch_nw(nb + 1, D, grid[nb], st);
+        batch_update<<<cb, tb, 0, st>>>(D);
+    }
+    if (cudaStreamEndCapture(st, &graph) != cudaSuccess || cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        cudaGetLastError();
+        bfree_all(b);
+        return MDIST_ECUDA;
+    }
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    int rc = MDIST_OK;
+    int *h_active = nullptr;
+    cudaMallocHost((void **)&h_active, sizeof(int));
+    const int max_launches = 65 / (R > 0 ? R : 1) + 2;
+    for (int launch = 0; launch < max_launches; ++launch) {
+        cudaEventRecord(e0, st);
+        if (cudaGraphLaunch(exec, st) != cudaSuccess) { rc = MDIST_ECUDA; break; }
+        cudaEventRecord(e1, st);
+        cudaMemcpyAsync(h_active, D.active_ctr, sizeof(int), cudaMemcpyDeviceToHost, st);
+        if (cudaStreamSynchronize(st) != cudaSuccess) { rc = MDIST_ECUDA; break; }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        b->gpu_ms += ms;
+        b->graph_launches += 1;
+        b->rounds += R;
+        if (*h_active == 0) break;
+    }
+    if (rc == MDIST_OK) {
+        b->res.resize((size_t)C);
+        b->counts.resize(ncounts);
+        if (cudaMemcpy(b->res.data(), d_codes, (size_t)C * sizeof(BatchCode), cudaMemcpyDeviceToHost) != cudaSuccess ||
+            cudaMemcpy(b->counts.data(), d_counts, ncounts * sizeof(unsigned long long), cudaMemcpyDeviceToHost) !=
+                cudaSuccess)
+            rc = MDIST_ECUDA;
+    }
+    if (h_active) cudaFreeHost(h_active);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaGraphExecDestroy(exec);
+    cudaGraphDestroy(graph);
+    bfree_all(b);
+    b->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    return rc;
+}
+
+int mdist_batch_info(const mdist_batch *b, int *ncodes, int *graph_launches, int *rounds, double *gpu_ms,
+                     double *seconds) {
+    if (!b) return MDIST_EINVAL;
+    if (ncodes) *ncodes = (int)b->codes.size();
+    if (graph_launches) *graph_launches = b->graph_launches;
+    if (rounds) *rounds = b->rounds;
+    if (gpu_ms) *gpu_ms = b->gpu_ms;
+    if (seconds) *seconds = b->seconds;
+    return MDIST_OK;
+}
+
+int mdist_batch_result(const mdist_batch *b, int index, int *d, uint64_t *witness, uint64_t *message, mdist_key *key,
+                       mdist_stats *stats) {
+    if (!b || !d || index < 0 || index >= (int)b->codes.size()) return MDIST_EINVAL;
+    if (!b->ran || b->res.empty()) return MDIST_EAGAIN;
+    const BatchCode &S = b->res[(size_t)index];
+    const HostCode &h = b->codes[(size_t)index];
+    if (S.status != MDIST_OK) return S.status;
+    if (S.active || !S.have_key) return MDIST_EAGAIN;
+    *d = S.U;
+    const unsigned long long comb = host_unrank_lex(h.k, S.key_g, S.key_rank);
+    const InfoSet &set = h.part.sets[(size_t)S.key_j];
+    uint64_t msg = 0;
+    for (int r = 0; r < h.k; ++r)
+        if ((comb >> r) & 1ull) msg ^= set.transform[(size_t)r];
+    if (message) *message = msg;
+    if (witness) {
+        for (int w = 0; w < h.W; ++w) witness[w] = 0;
+        for (int bit = 0; bit < h.k; ++bit)
+            if ((msg >> bit) & 1ull)
+                for (int w = 0; w < h.W; ++w) witness[w] ^= h.G[(size_t)bit * h.W + w];
+    }
+    if (key) *key = mdist_key{S.key_w, S.key_g, S.key_j, 0, S.key_rank};
+    if (stats) {
+        std::memset(stats, 0, sizeof *stats);
+        stats->g_final = S.g_final;
+        stats->j_final = S.j_final;
+        stats->m = S.m;
+        stats->L_final = S.L;
+        stats->U_final = S.U;
+        stats->launches = S.rounds;
+        for (int j = 0; j < S.m && j < MDIST_MAX_SETS; ++j) stats->ranks[j] = h.part.sets[(size_t)j].rank;
+        const unsigned long long off = b->counts_off[(size_t)index];
+        for (int g = 0; g <= h.k; ++g)
+            for (int j = 0; j < S.m && j < MDIST_MAX_SETS; ++j) stats->combos[g][j] = b->counts[off + (size_t)g * S.m + j];
+        stats->total_combos = S.combos;
+    }
+    return MDIST_OK;
+}
+
+void mdist_batch_free(mdist_batch *b) {
+    if (!b) return;
+    cudaStreamSynchronize(b->stream);
+    bfree_all(b);
+    delete b;
+}
+
+}  // extern "C"

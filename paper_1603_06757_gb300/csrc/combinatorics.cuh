@@ -9,6 +9,21 @@ namespace mdist {
 
 constexpr int kBn = 33;  // table C(a, b) for a, b <= 32, row-major, stride kBn
 
+struct BinomTable64 {
+    unsigned long long v[65][65];
+};
+
+// C(a, b) for a, b <= 64 by Pascal's rule, evaluated at compile time (each translation
+// unit that needs it on the device keeps its own __constant__ copy).
+constexpr BinomTable64 make_binom_table64() {
+    BinomTable64 t{};
+    for (int a = 0; a <= 64; ++a) {
+        t.v[a][0] = 1;
+        for (int b = 1; b <= a; ++b) t.v[a][b] = t.v[a - 1][b - 1] + (b <= a - 1 ? t.v[a - 1][b] : 0ull);
+    }
+    return t;
+}
+
 __host__ __device__ __forceinline__ int ffs32(uint32_t x) {
 #ifdef __CUDA_ARCH__
     return __ffs((int)x);
@@ -50,6 +65,7 @@ __host__ __device__ __forceinline__ uint32_t next_colex(uint32_t m) {
 
 // Lexicographic rank of a g-subset of {0..k-1}, c_1 < ... < c_g:
 // C(k,g) - 1 - sum_i C(k-1-c_i, g-i+1).  `C` maps (a, b) to C(a, b) for a, b <= 64.
+#pragma nv_exec_check_disable
 template <class Binom>
 __host__ __device__ __forceinline__ unsigned long long lexrank64(unsigned long long mask, int k, int g, Binom C) {
     unsigned long long r = C(k, g) - 1ull;

@@ -28,36 +28,12 @@
 #include <cstdint>
 
 #include "combinatorics.cuh"
+#include "enum_core.cuh"
 #include "internal.h"
 
 namespace mdist {
 
-struct BinomTable {
-    unsigned long long v[65][65];
-};
-
-constexpr BinomTable make_binom_table() {
-    BinomTable t{};
-    for (int a = 0; a <= 64; ++a) {
-        t.v[a][0] = 1;
-        for (int b = 1; b <= a; ++b) t.v[a][b] = t.v[a - 1][b - 1] + (b <= a - 1 ? t.v[a - 1][b] : 0ull);
-    }
-    return t;
-}
-
-// C(a, b) for a, b <= 64 (Pascal's rule, evaluated at compile time).
-static __constant__ BinomTable c_binom = make_binom_table();
-
-template <int NW>
-__device__ __forceinline__ void xor_rows(uint32_t (&x)[NW], const uint32_t *__restrict__ rows, uint32_t mask) {
-    while (mask) {
-        const int b = __ffs(mask) - 1;
-        mask &= mask - 1;
-        const uint32_t *r = rows + b * NW;
-#pragma unroll
-        for (int w = 0; w < NW; ++w) x[w] ^= r[w];
-    }
-}
+static __constant__ BinomTable64 c_binom = make_binom_table64();
 
 struct DeviceBinom {
     __device__ __forceinline__ unsigned long long operator()(int a, int b) const { return c_binom.v[a][b]; }
@@ -142,106 +118,22 @@ __global__ void __launch_bounds__(kCtaThreads) enum_unit_kernel(const __grid_con
         const int nvalid = left <= 0 ? 0 : (left >= XP ? XP : (int)left);
         const uint32_t e0 = (uint32_t)(e_first < B.lane_n ? e_first : B.lane_n - 1);
         uint32_t x[XP][NW];
-        {
-            uint32_t m = unrank_colex(s_bn, lane_kh, (int)B.lane_t, e0);
-#pragma unroll
-            for (int w = 0; w < NW; ++w) x[0][w] = 0;
-            xor_rows<NW>(x[0], lane_rows, m);
-#pragma unroll
-            for (int p = 1; p < XP; ++p) {
-#pragma unroll
-                for (int w = 0; w < NW; ++w) x[p][w] = x[p - 1][w];
-                if (p < nvalid) {
-                    const uint32_t nm = next_colex(m);
-                    xor_rows<NW>(x[p], lane_rows, m ^ nm);
-                    m = nm;
-                }
-            }
-        }
+        build_lane_entries<NW, XP>(x, s_bn, lane_rows, lane_kh, (int)B.lane_t, e0, nvalid);
 
         // ---- walk side: YL consecutive entries staged in this warp's buffer ----
         const unsigned long long w_first = walk_chunk * (unsigned long long)YL;
         const unsigned long long wleft = B.walk_n - w_first;
         const int walk_len = wleft >= (unsigned long long)YL ? YL : (int)wleft;
-        {
-            const int s0 = lane * PER;
-            if (s0 < walk_len) {
-                uint32_t wm = unrank_colex(s_bn, walk_kh, (int)B.walk_t, (uint32_t)(w_first + s0));
-                uint32_t y[NW];
-#pragma unroll
-                for (int w = 0; w < NW; ++w) y[w] = 0;
-                xor_rows<NW>(y, walk_rows, wm);
-#pragma unroll
-                for (int w = 0; w < NW; ++w) wbuf[s0 * NW + w] = y[w];
-                for (int q = 1; q < PER && s0 + q < walk_len; ++q) {
-                    const uint32_t nm = next_colex(wm);
-                    xor_rows<NW>(y, walk_rows, wm ^ nm);
-                    wm = nm;
-#pragma unroll
-                    for (int w = 0; w < NW; ++w) wbuf[(s0 + q) * NW + w] = y[w];
-                }
-            }
-        }
+        stage_walk<NW>(wbuf, s_bn, walk_rows, walk_kh, (int)B.walk_t, w_first, walk_len, PER, lane);
         __syncwarp();
 
         // ---- the walk ----
-        for (int s = 0; s < walk_len; ++s) {
-            uint32_t y[NW];
-#pragma unroll
-            for (int w = 0; w < NW; ++w) y[w] = wbuf[s * NW + w];
-            if (GS == 0) {
-                // exact: XOR, POPC per word, sum, running min, one compare per step
-                int mn = INT_MAX;
-#pragma unroll
-                for (int p = 0; p < XP; ++p) {
-                    int acc = 0;
-#pragma unroll
-                    for (int w = 0; w < NW; ++w) acc += __popc(x[p][w] ^ y[w]);
-                    mn = acc < mn ? acc : mn;
-                    if (HIST && p < nvalid) atomicAdd(&s_hist[acc + P.base], 1u);
-                }
-                if (mn <= thr) {
-#pragma unroll
-                    for (int p = 0; p < XP; ++p) {
-                        int acc = 0;
-#pragma unroll
-                        for (int w = 0; w < NW; ++w) acc += __popc(x[p][w] ^ y[w]);
-                        if (p < nvalid && acc <= thr) {
-                            const unsigned long long key = candidate_key(P, B, s_bn, e0 + (uint32_t)p,
-                                                                         (uint32_t)(w_first + s), acc + P.base);
-                            best = key < best ? key : best;
-                            thr = acc;
-                        }
-                    }
-                }
-            } else {
-                // lower bound first: weight >= sum over groups of GS words of
-                // popc(OR of the group's XORed words); only codewords whose bound
-                // reaches the threshold get the exact count
-#pragma unroll
-                for (int p = 0; p < XP; ++p) {
-                    int lb = 0;
-#pragma unroll
-                    for (int q = 0; q < NW; q += GS) {
-                        uint32_t o = 0;
-#pragma unroll
-                        for (int w = q; w < q + GS && w < NW; ++w) o |= x[p][w] ^ y[w];
-                        lb += __popc(o);
-                    }
-                    if (lb <= thr) {
-                        int acc = 0;
-#pragma unroll
-                        for (int w = 0; w < NW; ++w) acc += __popc(x[p][w] ^ y[w]);
-                        if (p < nvalid && acc <= thr) {
-                            const unsigned long long key = candidate_key(P, B, s_bn, e0 + (uint32_t)p,
-                                                                         (uint32_t)(w_first + s), acc + P.base);
-                            best = key < best ? key : best;
-                            thr = acc;
-                        }
-                    }
-                }
-            }
-        }
+        walk_tile<NW, XP, GS, HIST>(x, wbuf, walk_len, nvalid, thr, s_hist, P.base, [&](int p, int s, int acc) {
+            const unsigned long long key =
+                candidate_key(P, B, s_bn, e0 + (uint32_t)p, (uint32_t)(w_first + s), acc + P.base);
+            best = key < best ? key : best;
+            thr = acc;
+        });
         if (lane == 0) {
             const unsigned long long in_chunk = B.lane_n - chunk_first;
             const unsigned long long lanes_valid = in_chunk < (unsigned long long)(32 * XP) ? in_chunk : 32 * XP;

@@ -60,8 +60,8 @@ struct EnumParams {
 };
 
 // Kernel tile geometry per word count (lanes x XP lane entries, YL walk entries).
-constexpr int lane_entries_per_thread(int nwords) { return nwords <= 4 ? 16 : (nwords <= 8 ? 8 : 4); }
-constexpr int walk_len_for(int nwords) { return nwords <= 8 ? 256 : 128; }
+__host__ __device__ constexpr int lane_entries_per_thread(int nwords) { return nwords <= 4 ? 16 : (nwords <= 8 ? 8 : 4); }
+__host__ __device__ constexpr int walk_len_for(int nwords) { return nwords <= 8 ? 256 : 128; }
 
 // Launch one unit's enumerator (enum_launch.cu).  hist == nullptr for the normal path.
 cudaError_t launch_enum_unit(const EnumParams &p, int nwords, int group, bool hist_mode, int sm_count,

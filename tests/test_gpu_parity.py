@@ -154,6 +154,9 @@ def test_textbook_codes(api, name, make, n, d, per_matrix):
     _assert_same_run(got, oracle.min_distance(G, n, check_per_matrix=per_matrix))
 
 
+ORACLE_BUDGET = 3e9  # combinations the oracle may need for one run in these tests
+
+
 @pytest.mark.parametrize("seed", range(60))
 def test_min_distance_random_vs_oracle(api, seed):
     rng = synth.SplitMix64(31000 + seed)
@@ -161,11 +164,10 @@ def test_min_distance_random_vs_oracle(api, seed):
     n = rng.uniform_int(k + 1, min(512, 4 * k + 1))
     G = synth.random_systematic(n, k, seed)
     per_matrix = bool(seed % 2)
-    want = oracle.min_distance(G, n, check_per_matrix=per_matrix)
-    if sum(int(c) for c in want["counts"].ravel()) > 3e9:
-        pytest.skip("oracle too slow for this draw")
     got = _gpu_min_distance(api, G, n, per_matrix)
-    _assert_same_run(got, want)
+    if got["total_combos"] > ORACLE_BUDGET:  # size check only; parity below is against the oracle
+        pytest.skip("oracle too slow for this draw")
+    _assert_same_run(got, oracle.min_distance(G, n, check_per_matrix=per_matrix))
     if k <= 24:
         assert got["d"] == oracle.brute_force_distance(G, n)
 
@@ -232,14 +234,16 @@ def test_side_stream(api):
     _assert_same_run(got, oracle.min_distance(G, n))
 
 
+# (n, k, seed): 3, 4, 5, 9 and 15 words per stored row, Alg. 1 work small enough for the oracle
+VARIANT_CASES = [(120, 36, 3), (150, 36, 14), (180, 36, 13), (300, 30, 2), (500, 25, 6), (96, 24, 5)]
+
+
 @pytest.mark.parametrize("fg", [1, 2, 3, 4])
-@pytest.mark.parametrize("n,k,seed", [(120, 36, 3), (200, 40, 4), (300, 45, 5), (512, 40, 7), (150, 50, 9)])
+@pytest.mark.parametrize("n,k,seed", VARIANT_CASES)
 def test_filter_variants_identical(api, fg, n, k, seed):
     # every enumerator variant (exact, OR-groups of 2, 3, 4 words) gives the same run
     G = synth.random_systematic(n, k, seed)
-    want = oracle.min_distance(G, n)
-    if sum(int(c) for c in want["counts"].ravel()) > 3e9:
-        pytest.skip("oracle too slow for this draw")
     with api.Code(G, n, filter_group=fg) as c:
         got = c.min_distance()
-    _assert_same_run(got, want)
+    assert got["total_combos"] <= ORACLE_BUDGET
+    _assert_same_run(got, oracle.min_distance(G, n))
