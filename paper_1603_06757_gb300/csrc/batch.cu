@@ -497,7 +497,18 @@ int mdist_batch_run(mdist_batch *b, int rounds_per_graph) {
         bfree_all(b);
         return MDIST_ENOMEM;
     }
+    // graph capture is not allowed on the legacy default stream: use a private stream
+    // then, after the caller's earlier work on it has finished
     cudaStream_t st = b->stream;
+    cudaStream_t own = nullptr;
+    if (!st) {
+        if (cudaStreamSynchronize(nullptr) != cudaSuccess ||
+            cudaStreamCreateWithFlags(&own, cudaStreamNonBlocking) != cudaSuccess) {
+            bfree_all(b);
+            return MDIST_ECUDA;
+        }
+        st = own;
+    }
     bool ok = cudaMemcpyAsync(d_rows, rows.data(), rows.size() * sizeof(uint32_t), cudaMemcpyHostToDevice, st) ==
                   cudaSuccess &&
               cudaMemcpyAsync(d_units, units.data(), units.size() * sizeof(BatchUnit), cudaMemcpyHostToDevice, st) ==
@@ -506,7 +517,11 @@ int mdist_batch_run(mdist_batch *b, int rounds_per_graph) {
               cudaMemcpyAsync(d_codes, codes.data(), codes.size() * sizeof(BatchCode), cudaMemcpyHostToDevice, st) ==
                   cudaSuccess &&
               cudaMemsetAsync(d_counts, 0, ncounts * sizeof(unsigned long long), st) == cudaSuccess;
-    if (!ok) { bfree_all(b); return MDIST_ECUDA; }
+    if (!ok) {
+        if (own) cudaStreamDestroy(own);
+        bfree_all(b);
+        return MDIST_ECUDA;
+    }
     D.rows = d_rows;
     D.units = d_units;
     D.gs_table = d_gs;
@@ -528,7 +543,11 @@ int mdist_batch_run(mdist_batch *b, int rounds_per_graph) {
     for (int nb = 0; nb < kBatchBuckets; ++nb) {
         if (!present[nb]) continue;
         int occ = 0;
-        if (batch_prepare_nw(nb + 1, &occ) != cudaSuccess || occ < 1) { bfree_all(b); return MDIST_ECUDA; }
+        if (batch_prepare_nw(nb + 1, &occ) != cudaSuccess || occ < 1) {
+            if (own) cudaStreamDestroy(own);
+            bfree_all(b);
+            return MDIST_ECUDA;
+        }
         const int per_sm = b->opt.blocks_per_sm > 0 && b->opt.blocks_per_sm < occ ? b->opt.blocks_per_sm : occ;
         grid[nb] = b->sm_count * per_sm;
     }
@@ -538,7 +557,12 @@ int mdist_batch_run(mdist_batch *b, int rounds_per_graph) {
     const int tb = 128, cb = (C + tb - 1) / tb;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
-    if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) { bfree_all(b); return MDIST_ECUDA; }
+    if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cudaGetLastError();
+        if (own) cudaStreamDestroy(own);
+        bfree_all(b);
+        return MDIST_ECUDA;
+    }
     for (int r = 0; r < R; ++r) {
         batch_round_begin<<<1, 32, 0, st>>>(D);
         batch_prep<<<cb, tb, 0, st>>>(D);
@@ -549,6 +573,7 @@ int mdist_batch_run(mdist_batch *b, int rounds_per_graph) {
     if (cudaStreamEndCapture(st, &graph) != cudaSuccess || cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) {
         if (graph) cudaGraphDestroy(graph);
         cudaGetLastError();
+        if (own) cudaStreamDestroy(own);
         bfree_all(b);
         return MDIST_ECUDA;
     }
@@ -585,6 +610,10 @@ int mdist_batch_run(mdist_batch *b, int rounds_per_graph) {
     cudaEventDestroy(e1);
     cudaGraphExecDestroy(exec);
     cudaGraphDestroy(graph);
+    if (own) {
+        cudaStreamSynchronize(own);
+        cudaStreamDestroy(own);
+    }
     bfree_all(b);
     b->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     return rc;
