@@ -206,6 +206,41 @@ int mdist_batch_info(const mdist_batch *b, int *ncodes, int *graph_launches, int
 
 void mdist_batch_free(mdist_batch *b);
 
+/* ---- work predictor (sizing only) ----------------------------------------------- */
+
+#define MDIST_NFEATURES 24
+
+/* Predictor input features of a code (host only, no GPU): n, k, rate, number of sets,
+ * the first four ranks r_j / k, the Gilbert-Varshamov estimate of d and of the
+ * termination level, the least weights found at levels 1 and <= 2 and the level the
+ * bound needs to pass the latter, and the column-weight histogram of the A_j of the
+ * full-rank sets (8 bins of weight / k, mean, spread, fraction of weight <= 2).
+ * f[MDIST_NFEATURES], each roughly in [0, 1]. */
+int mdist_features(const uint64_t *G, int n, int k, int words_per_row, float *f);
+
+/* Analytic fallback: d_GV = least w with sum_{i<=w} C(n, i) >= 2^(n-k); wstar_GV = least
+ * g with L(g) = sum_j max(0, g + 1 - (k - r_j)) >= d_GV (ranks[m]).  Host only. */
+int mdist_gv_estimate(int n, int k, int m, const int *ranks, int *d_gv, int *wstar_gv);
+
+/* A small fp32 multilayer perceptron on the GPU (hand-written kernels): in_features ->
+ * hidden (ReLU) x hidden_layers -> outputs, He-uniform weights from SplitMix64(seed),
+ * zero biases; mean-squared-error loss, Adam.  Parameters are laid out layer by layer,
+ * W_l (in x out, row-major) then b_l.  X, T, Y are host arrays, row-major. */
+typedef struct mdist_mlp mdist_mlp;
+int mdist_mlp_create(int in_features, int hidden, int hidden_layers, int outputs, uint64_t seed, void *cuda_stream,
+                     mdist_mlp **out);
+int mdist_mlp_num_params(const mdist_mlp *mlp, int *n);
+int mdist_mlp_get_params(const mdist_mlp *mlp, float *params);
+int mdist_mlp_set_params(mdist_mlp *mlp, const float *params);   /* also resets Adam's moments */
+int mdist_mlp_forward(mdist_mlp *mlp, const float *X, int N, float *Y);
+/* loss = mean over N x outputs of (Y - T)^2 and its gradient (grad may be NULL) */
+int mdist_mlp_loss_grad(mdist_mlp *mlp, const float *X, const float *T, int N, float *loss, float *grad);
+/* steps of Adam (lr, betas 0.9 / 0.999) on minibatches of `batch` rows drawn with
+ * replacement by SplitMix64(seed); loss_curve[steps] (may be NULL) */
+int mdist_mlp_train(mdist_mlp *mlp, const float *X, const float *T, int N, int steps, int batch, float lr,
+                    uint64_t seed, float *loss_curve);
+void mdist_mlp_free(mdist_mlp *mlp);
+
 /* Instruction-throughput probe on the current device, for roofline arithmetic:
  * which = 0: 32-bit POPC, 1: 3-input XOR (LOP3), 2: enumerator inner step (XOR + POPC
  * over 4 words, sum, running min), 3 / 4: the lower-bound step of filter groups of 2 /

@@ -88,6 +88,7 @@ P64 = ctypes.POINTER(ctypes.c_uint64)
 PI = ctypes.POINTER(ctypes.c_int)
 PI32 = ctypes.POINTER(ctypes.c_int32)
 PCODE = ctypes.c_void_p
+PF = ctypes.POINTER(ctypes.c_float)
 
 # name -> (restype, argtypes): every entry point of include/mdist.h
 SIGNATURES = {
@@ -117,6 +118,18 @@ SIGNATURES = {
     "mdist_batch_info": (ctypes.c_int, [ctypes.c_void_p, PI, PI, PI, ctypes.POINTER(ctypes.c_double),
                                         ctypes.POINTER(ctypes.c_double)]),
     "mdist_batch_free": (None, [ctypes.c_void_p]),
+    "mdist_features": (ctypes.c_int, [P64, ctypes.c_int, ctypes.c_int, ctypes.c_int, PF]),
+    "mdist_gv_estimate": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, PI, PI, PI]),
+    "mdist_mlp_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_uint64,
+                                        ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]),
+    "mdist_mlp_num_params": (ctypes.c_int, [ctypes.c_void_p, PI]),
+    "mdist_mlp_get_params": (ctypes.c_int, [ctypes.c_void_p, PF]),
+    "mdist_mlp_set_params": (ctypes.c_int, [ctypes.c_void_p, PF]),
+    "mdist_mlp_forward": (ctypes.c_int, [ctypes.c_void_p, PF, ctypes.c_int, PF]),
+    "mdist_mlp_loss_grad": (ctypes.c_int, [ctypes.c_void_p, PF, PF, ctypes.c_int, PF, PF]),
+    "mdist_mlp_train": (ctypes.c_int, [ctypes.c_void_p, PF, PF, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                       ctypes.c_float, ctypes.c_uint64, PF]),
+    "mdist_mlp_free": (None, [ctypes.c_void_p]),
     "mdist_partition_host": (ctypes.c_int, [P64, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, PI, PI,
                                             PI32, P64, P64]),
     "mdist_debug_set_rows": (ctypes.c_int, [P64, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, PI, PI, PI,
