@@ -250,6 +250,39 @@ void mdist_mlp_free(mdist_mlp *mlp);
  * per SM of device memory for its duration. */
 int mdist_microbench(int which, int iters, double *ops_per_clock_per_sm, double *seconds);
 
+/* ---- one unit without any device allocation ---------------------------------------- */
+
+/* Capacity of the fixed scratch array behind mdist_enumerate_unit_noalloc: histogram
+ * bins (n_bits + g + 1 for a full-rank set, n_bits + 1 otherwise). */
+#define MDIST_NOALLOC_MAX_HIST_BINS 513
+
+/* Enumerate one (g, j) unit, as mdist_enumerate_level / mdist_unit_histogram do, for
+ * callers that cannot allocate device memory: code running under a device-memory
+ * pool or budget owned by someone else, or in a context where calling cudaMalloc is
+ * not allowed.  The paper has no counterpart: this is a deployment variant of the
+ * enumerator.
+ *
+ * Inputs: `rows` (device) = the set's stored rows, k rows of nwords 32-bit words (the
+ * layout mdist_debug_set_rows returns: for a full-rank set the n_bits = n - k
+ * non-pivot columns, full_rank = 1; otherwise all n_bits = n columns, full_rank = 0);
+ * level g; candidates are codewords of weight <= U.  Output `out` (device, caller-
+ * owned, 3 + bins uint64): out[0] = min(U, least candidate weight), out[1] = least
+ * key weight << 54 | lexicographic rank, or 2^64-1 if no candidate, out[2] =
+ * combinations enumerated, out[3..] = the weight histogram when want_hist (bins as
+ * above), untouched otherwise.  Work is queued on `cuda_stream` (NULL = legacy default
+ * stream); read `out` after synchronising it.
+ *
+ * Memory: no cudaMalloc, cudaFree or other allocating call.  The unit's scratch state
+ * (threshold, key, count, work counter, histogram) lives in one fixed 8 KiB device
+ * array that every GPU loading the library keeps until the process exits.  The first
+ * call on a device looks up that array's device address (so make it before any stream
+ * capture starts).  Each call clears the scratch it uses, but all calls share it:
+ * calls that may overlap on the GPU (other streams, other host threads) race and must
+ * be serialised by the caller.  MDIST_ERANGE if the histogram needs more than
+ * MDIST_NOALLOC_MAX_HIST_BINS bins or C(k, g) >= 2^54; MDIST_EINVAL for bad sizes. */
+int mdist_enumerate_unit_noalloc(const uint32_t *rows, int k, int nwords, int n_bits, int full_rank, int g, int U,
+                                 int want_hist, unsigned long long *out, void *cuda_stream);
+
 /* ---- host-only entry points (no CUDA call; usable without a GPU) ---------------- */
 
 /* The information-set partition of mdist_prepare alone (same reading of §2, same
