@@ -76,6 +76,10 @@ typedef struct {
     mdist_alloc_fn dev_alloc;/* optional device allocator */
     mdist_free_fn dev_free;
     void *alloc_ctx;
+    int wstar_hint;          /* > 1: predicted termination level; mdist_run then launches
+                                levels 1 .. wstar_hint-1 as one wave (one host
+                                synchronisation).  Sizing only: results never depend on it. */
+    int reserved1;
 } mdist_options;
 
 /* Witness key: the least (weight, g, j, rank) over the enumerated units (a total

@@ -41,6 +41,8 @@ class Options(ctypes.Structure):
         ("dev_alloc", ALLOC_FN),
         ("dev_free", FREE_FN),
         ("alloc_ctx", ctypes.c_void_p),
+        ("wstar_hint", ctypes.c_int),
+        ("reserved1", ctypes.c_int),
     ]
 
 

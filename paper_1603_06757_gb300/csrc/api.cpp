@@ -1,6 +1,7 @@
 // api.cpp -- the C-ABI of libmdist.so (declared in include/mdist.h): code handles,
 // the Alg. 1 driver (levels g = 1, 2, ... over all information sets while L < U,
 // §2), the per-unit GPU launches, results, checkpoint / resume.
+#include <algorithm>
 #include <chrono>
 #include <climits>
 #include <cstdlib>
@@ -55,6 +56,9 @@ struct mdist_code {
     unsigned long long *d_hist = nullptr;// n+1 bins, on demand
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     uint64_t rows_bytes = 0;             // Gamma rows copied to the device by mdist_prepare
+    int wave_cap = 0;                    // units a wave can hold: m * (k + 1)
+    UnitSlot *d_wave = nullptr;          // [wave_cap] per-unit slots + 1 threshold word after them
+    UnitSlot *h_wave = nullptr;          // pinned copy
     RunState st;
 };
 
@@ -100,6 +104,7 @@ int run_unit(mdist_code *c, int g, int j, int U_thr, bool hist_mode, bool *found
     EnumParams p{};
     if (!mdist::plan_level(c->k, g, dr.nwords, p)) return MDIST_ERANGE;
     p.rows = c->d_rows[(size_t)j];
+    p.U = &c->d_slot->U;
     p.slot = c->d_slot;
     p.hist = c->d_hist;
     p.nwords = dr.nwords;
@@ -190,6 +195,8 @@ void mdist_free(mdist_code *c) {
     for (uint32_t *p : c->d_rows) dev_release(c, p);
     dev_release(c, c->d_slot);
     dev_release(c, c->d_hist);
+    dev_release(c, c->d_wave);
+    if (c->h_wave) cudaFreeHost(c->h_wave);
     if (c->h_slot) cudaFreeHost(c->h_slot);
     if (c->ev0) cudaEventDestroy(c->ev0);
     if (c->ev1) cudaEventDestroy(c->ev1);
@@ -230,6 +237,13 @@ int mdist_prepare(const uint64_t *G, int n, int k, int words_per_row, const mdis
     }
     c->d_slot = (UnitSlot *)dev_alloc(c, sizeof(UnitSlot));
     if (!c->d_slot) { mdist_free(c); return MDIST_ENOMEM; }
+    c->wave_cap = c->m * (k + 1);
+    c->d_wave = (UnitSlot *)dev_alloc(c, sizeof(UnitSlot) * ((size_t)c->wave_cap + 1));
+    if (!c->d_wave) { mdist_free(c); return MDIST_ENOMEM; }
+    if (cudaMallocHost((void **)&c->h_wave, sizeof(UnitSlot) * ((size_t)c->wave_cap + 1)) != cudaSuccess) {
+        mdist_free(c);
+        return MDIST_ECUDA;
+    }
     c->d_rows.assign((size_t)c->m, nullptr);
     for (int j = 0; j < c->m; ++j) {
         const DeviceRows &dr = c->rows[(size_t)j];
@@ -311,35 +325,96 @@ int mdist_unit_histogram(mdist_code *c, int g, int j, uint64_t *hist, uint64_t *
     return MDIST_OK;
 }
 
-int mdist_reset(mdist_code *c) {
-    if (!c) return MDIST_EINVAL;
-    reset_state(c);
-    return MDIST_OK;
-}
-
-int mdist_run(mdist_code *c, int max_units, int *finished) {
-    if (!c) return MDIST_EINVAL;
+// One wave: the units from (next_g, next_j) through the end of level g_hi (at most
+// max_units of them) are launched back to back, each with its own slot, sharing one
+// candidate threshold (the current best weight, ties kept); one host synchronisation;
+// then their results are folded in (g, j) order with the bounds checked after every
+// unit (per-matrix mode) or level, exactly as if the units had run one at a time: a
+// codeword first met past the termination level weighs at least L >= U, so the shared
+// threshold never prunes the unit holding the final U, and folding stops at the
+// termination unit.
+static int run_wave(mdist_code *c, int g_hi, int max_units, int *units_done) {
     RunState &s = c->st;
-    const auto t0 = std::chrono::steady_clock::now();
-    int units = 0;
-    int rc = MDIST_OK;
-    while (!s.finished && (max_units <= 0 || units < max_units)) {
-        const int g = s.next_g, j = s.next_j;
-        // after a key exists, only strictly lighter codewords can replace it (a tie
-        // in a later unit has a larger (g, j)); before, ties with U = n-k+1 count
-        const int U_thr = s.have_key ? s.key.weight - 1 : s.U;
-        bool found;
-        int w;
-        uint64_t rank, cnt;
-        rc = run_unit(c, g, j, U_thr, false, &found, &w, &rank, &cnt);
-        if (rc != MDIST_OK) break;
-        ++units;
-        s.counts[g][j] = cnt;
+    struct U2 { int g, j; };
+    std::vector<U2> list;
+    for (int g = s.next_g; g <= g_hi && g <= c->k; ++g)
+        for (int j = (g == s.next_g ? s.next_j : 0); j < c->m; ++j) {
+            if (max_units > 0 && (int)list.size() >= max_units) break;
+            list.push_back({g, j});
+        }
+    if (list.empty()) return MDIST_OK;
+    const int nu = (int)list.size();
+    EnumParams p{};
+    for (int u = 0; u < nu; ++u) {  // every level must be within the device key range
+        if (!mdist::plan_level(c->k, list[(size_t)u].g, c->rows[(size_t)list[(size_t)u].j].nwords, p)) {
+            if (u == 0) return MDIST_ERANGE;
+            list.resize((size_t)u);
+            break;
+        }
+    }
+    const int n_units = (int)list.size();
+    const int U_thr = s.have_key ? s.key.weight : s.U;  // ties are candidates within a wave
+    for (int u = 0; u < n_units; ++u) {
+        c->h_wave[u].U = 0;
+        c->h_wave[u].pad0 = 0;
+        c->h_wave[u].key = mdist::kNoKey;
+        c->h_wave[u].count = 0;
+        c->h_wave[u].tile_next = 0;
+    }
+    UnitSlot &thr_word = c->h_wave[c->wave_cap];
+    thr_word.U = (unsigned)(U_thr < 0 ? 0 : U_thr);
+    thr_word.pad0 = 0;
+    thr_word.key = thr_word.count = thr_word.tile_next = 0;
+    unsigned int *d_U = &c->d_wave[c->wave_cap].U;
+    if (cudaMemcpyAsync(c->d_wave, c->h_wave, sizeof(UnitSlot) * (size_t)n_units, cudaMemcpyHostToDevice, c->stream) !=
+            cudaSuccess ||
+        cudaMemcpyAsync(&c->d_wave[c->wave_cap], &thr_word, sizeof(UnitSlot), cudaMemcpyHostToDevice, c->stream) !=
+            cudaSuccess)
+        return MDIST_ECUDA;
+    s.h2d_bytes += sizeof(UnitSlot) * ((size_t)n_units + 1);
+    if (cudaEventRecord(c->ev0, c->stream) != cudaSuccess) return MDIST_ECUDA;
+    for (int u = 0; u < n_units; ++u) {
+        const int g = list[(size_t)u].g, j = list[(size_t)u].j;
+        const DeviceRows &dr = c->rows[(size_t)j];
+        EnumParams q{};
+        mdist::plan_level(c->k, g, dr.nwords, q);
+        q.rows = c->d_rows[(size_t)j];
+        q.U = d_U;
+        q.slot = &c->d_wave[u];
+        q.hist = nullptr;
+        q.nwords = dr.nwords;
+        q.n_bits = dr.n_bits;
+        q.base = dr.full_rank ? g : 0;
+        const int fg = c->opt.filter_group;
+        int group = fg == 0 ? mdist::choose_filter_group(dr.nwords, dr.n_bits, U_thr - q.base) : (fg == 1 ? 0 : fg);
+        if (group > dr.nwords) group = 0;
+        if (mdist::launch_enum_unit(q, dr.nwords, group, false, c->sm_count, c->opt.blocks_per_sm, c->stream) !=
+            cudaSuccess)
+            return MDIST_ECUDA;
+    }
+    if (cudaEventRecord(c->ev1, c->stream) != cudaSuccess) return MDIST_ECUDA;
+    if (cudaMemcpyAsync(c->h_wave, c->d_wave, sizeof(UnitSlot) * (size_t)n_units, cudaMemcpyDeviceToHost, c->stream) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(c->stream) != cudaSuccess)
+        return MDIST_ECUDA;
+    s.d2h_bytes += sizeof(UnitSlot) * (size_t)n_units;
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, c->ev0, c->ev1) == cudaSuccess) s.kernel_ms += ms;
+    s.launches += n_units;
+    // fold in (g, j) order
+    for (int u = 0; u < n_units && !s.finished; ++u) {
+        const int g = list[(size_t)u].g, j = list[(size_t)u].j;
+        const UnitSlot &r = c->h_wave[u];
+        s.counts[g][j] = r.count;
         s.g_last = g;
         s.j_last = j;
-        if (found) {
-            s.key = mdist_key{w, g, j, 0, rank};
-            s.have_key = 1;
+        ++*units_done;
+        if (r.key != mdist::kNoKey) {
+            const int w = (int)(r.key >> mdist::kKeyRankBits);
+            if (!s.have_key || w < s.key.weight) {
+                s.key = mdist_key{w, g, j, 0, r.key & ((1ull << mdist::kKeyRankBits) - 1)};
+                s.have_key = 1;
+            }
             if (w < s.U) s.U = w;
         }
         if (c->opt.check_per_matrix) {
@@ -360,6 +435,29 @@ int mdist_run(mdist_code *c, int max_units, int *finished) {
             s.next_g = g + 1;
             if (s.next_g > c->k) s.finished = 1;
         }
+    }
+    return MDIST_OK;
+}
+
+int mdist_reset(mdist_code *c) {
+    if (!c) return MDIST_EINVAL;
+    reset_state(c);
+    return MDIST_OK;
+}
+
+int mdist_run(mdist_code *c, int max_units, int *finished) {
+    if (!c) return MDIST_EINVAL;
+    RunState &s = c->st;
+    const auto t0 = std::chrono::steady_clock::now();
+    int units = 0;
+    int rc = MDIST_OK;
+    while (!s.finished && (max_units <= 0 || units < max_units)) {
+        // first wave: every level below the predicted termination level at once
+        int g_hi = s.next_g;
+        if (c->opt.wstar_hint > 1 && s.next_g == 1 && s.next_j == 0) g_hi = std::min(c->k, c->opt.wstar_hint - 1);
+        if (g_hi < s.next_g) g_hi = s.next_g;
+        rc = run_wave(c, g_hi, max_units > 0 ? max_units - units : 0, &units);
+        if (rc != MDIST_OK) break;
     }
     s.seconds += std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     if (finished) *finished = s.finished;

@@ -76,9 +76,9 @@ __device__ __forceinline__ void stage_walk(uint32_t *__restrict__ wbuf, const ui
 // The walk over one tile.  GS = 0: exact weight of every codeword (XOR, POPC per
 // word, sum, running min, one compare per step).  GS = 2, 3, 4: a lower bound first,
 // the popcount of the OR of each group of GS XORed words (weight >= bound), and the
-// exact weight only where the bound reaches the threshold.  `thr` is the largest
-// reduced weight still a candidate; `cand(p, s, reduced_weight)` handles a candidate
-// and may lower thr.  HIST adds every valid codeword's weight to s_hist.
+// exact weights only in the walk steps where the bound reaches the threshold.  `thr`
+// is the largest reduced weight still a candidate; `cand(p, s, reduced_weight)`
+// handles a candidate and may lower thr.  HIST adds every valid codeword's weight to s_hist.
 template <int NW, int XP, int GS, bool HIST, class Cand>
 __device__ __forceinline__ void walk_tile(const uint32_t (&x)[XP][NW], const uint32_t *__restrict__ wbuf,
                                           int walk_len, int nvalid, int &thr, unsigned int *s_hist, int base,
@@ -107,6 +107,10 @@ __device__ __forceinline__ void walk_tile(const uint32_t (&x)[XP][NW], const uin
                 }
             }
         } else {
+            // lower bound first (weight >= sum over groups of GS words of the popcount of
+            // their OR), minimum over the lane's entries, one branch per step; the exact
+            // weights are computed only in steps where some bound reaches the threshold
+            int mn = INT_MAX;
 #pragma unroll
             for (int p = 0; p < XP; ++p) {
                 int lb = 0;
@@ -117,7 +121,11 @@ __device__ __forceinline__ void walk_tile(const uint32_t (&x)[XP][NW], const uin
                     for (int w = q; w < q + GS && w < NW; ++w) o |= x[p][w] ^ y[w];
                     lb += __popc(o);
                 }
-                if (lb <= thr) {
+                mn = lb < mn ? lb : mn;
+            }
+            if (mn <= thr) {
+#pragma unroll
+                for (int p = 0; p < XP; ++p) {
                     int acc = 0;
 #pragma unroll
                     for (int w = 0; w < NW; ++w) acc += __popc(x[p][w] ^ y[w]);

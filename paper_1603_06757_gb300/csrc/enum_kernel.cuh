@@ -52,7 +52,7 @@ static __device__ __noinline__ unsigned long long candidate_key(const EnumParams
     const unsigned long long h2 = B.lane_half ? lm : wm;
     const unsigned long long full = h1 | (h2 << P.k1);
     const unsigned long long rank = lexrank64(full, P.k, P.g, DeviceBinom{});
-    atomicMin(&P.slot->U, (unsigned int)weight);
+    atomicMin(P.U, (unsigned int)weight);
     return ((unsigned long long)weight << kKeyRankBits) | rank;
 }
 
@@ -86,7 +86,7 @@ __global__ void __launch_bounds__(kCtaThreads) enum_unit_kernel(const __grid_con
     const int warp = threadIdx.x >> 5;
     uint32_t *wbuf = s_walk + warp * YL * NW;
     UnitSlot *slot = P.slot;
-    int thr = (int)(*(volatile unsigned int *)&slot->U) - P.base;  // candidates: reduced weight <= thr
+    int thr = (int)(*(volatile unsigned int *)P.U) - P.base;  // candidates: reduced weight <= thr
     unsigned long long best = kNoKey;
     unsigned long long cnt = 0;
 
@@ -107,7 +107,7 @@ __global__ void __launch_bounds__(kCtaThreads) enum_unit_kernel(const __grid_con
         const uint32_t *walk_rows = s_rows + (B.lane_half ? 0 : P.k1) * NW;
 
         {  // newest U from the other warps
-            const int gU = (int)(*(volatile unsigned int *)&slot->U) - P.base;
+            const int gU = (int)(*(volatile unsigned int *)P.U) - P.base;
             thr = gU < thr ? gU : thr;
         }
 

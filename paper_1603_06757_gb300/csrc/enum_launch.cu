@@ -100,12 +100,13 @@ static const std::vector<double> &lower_bound_cdf(int nwords, int n_bits, int gs
 
 // Expected SM clocks per codeword: POPC retire at 16 per SM-clock, issue at 128 per
 // SM-clock (4 schedulers x 32 lanes).  Exact variant: nwords XOR + nwords POPC +
-// ~nwords adds/min.  Group variant: nwords fused XOR/OR (LOP3) + one POPC and one add
-// per group + compare/branch, plus the exact count when any of the 32 lanes of the
-// warp passes the bound (the branch is taken warp-wide).
+// ~nwords adds/min.  Group variant: nwords fused XOR/OR (LOP3) + one POPC and one
+// add/min per group; a walk step (32 lanes x XP entries) whose minimum bound reaches
+// the threshold also pays the exact count of all its entries.
 int choose_filter_group(int nwords, int n_bits, int thr) {
     const double exact = std::fmax(nwords / 16.0, 3.0 * nwords / 128.0);
     if (thr >= n_bits) return 0;
+    const double step_cw = 32.0 * lane_entries_per_thread(nwords);
     double best_cost = exact;
     int best = 0;
     for (int gs = 2; gs <= 4; ++gs) {
@@ -116,9 +117,9 @@ int choose_filter_group(int nwords, int n_bits, int thr) {
             const std::vector<double> &cdf = lower_bound_cdf(nwords, n_bits, gs);
             p = cdf[(size_t)(thr < (int)cdf.size() ? thr : (int)cdf.size() - 1)];
         }
-        const double pw = 1.0 - std::pow(1.0 - p, 32.0);
-        const double popc = ng + pw * nwords;
-        const double instr = nwords + 2.0 * ng + 2.0 + pw * (3.0 * nwords + 4.0);
+        const double pstep = 1.0 - std::pow(1.0 - p, step_cw);
+        const double popc = ng + pstep * nwords;
+        const double instr = nwords + 2.0 * ng + pstep * (3.0 * nwords + 3.0);
         const double cost = std::fmax(popc / 16.0, instr / 128.0);
         if (cost < best_cost * 0.98) {
             best_cost = cost;

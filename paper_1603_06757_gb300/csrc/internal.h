@@ -23,7 +23,7 @@ constexpr uint64_t kNoKey = ~0ull;
 
 // Device-side result slot of one (g, j) unit.
 struct UnitSlot {
-    unsigned int U;              // candidate threshold: codewords of weight <= U count
+    unsigned int U;              // threshold word for launches that own their slot
     unsigned int pad0;
     unsigned long long key;      // least (weight << 54 | rank) among candidates, or kNoKey
     unsigned long long count;    // combinations enumerated
@@ -48,7 +48,8 @@ struct ProductBlock {
 // Parameters of one enumerator launch (one unit).
 struct EnumParams {
     const uint32_t *rows;        // k reduced rows of nwords 32-bit words each (row-major)
-    UnitSlot *slot;
+    unsigned int *U;             // candidate threshold (weight <= *U), shared by the units of a wave
+    UnitSlot *slot;              // this unit's key, count and work counter
     unsigned long long *hist;    // n_bits+1 bins (histogram mode only)
     int k, k1, k2, g;            // rows, half sizes (k1 = ceil(k/2)), level
     int nwords;                  // 32-bit words per reduced row

@@ -96,6 +96,7 @@ __global__ void __launch_bounds__(kProbeThreads) probe_step4_group(int iters, un
     __syncthreads();
     const long long t0 = clock64();
     for (int it = 0; it < iters; ++it) {
+        int mn = 1 << 30;
 #pragma unroll
         for (int p = 0; p < 16; ++p) {
             int lb;
@@ -104,7 +105,12 @@ __global__ void __launch_bounds__(kProbeThreads) probe_step4_group(int iters, un
             } else {
                 lb = __popc((x[p][0] ^ y0) | (x[p][1] ^ y1)) + __popc((x[p][2] ^ y2) | (x[p][3] ^ y3));
             }
-            if (lb <= thr) hits += __popc(x[p][0] ^ y0) + __popc(x[p][1] ^ y1) + __popc(x[p][2] ^ y2);
+            mn = lb < mn ? lb : mn;
+        }
+        if (mn <= thr) {
+#pragma unroll
+            for (int p = 0; p < 16; ++p)
+                hits += __popc(x[p][0] ^ y0) + __popc(x[p][1] ^ y1) + __popc(x[p][2] ^ y2) + __popc(x[p][3] ^ y3);
         }
         y0 += 0x9e3779b9u; y1 ^= y0; y2 += y1; y3 ^= y2;
     }

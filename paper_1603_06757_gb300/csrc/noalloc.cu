@@ -114,6 +114,7 @@ extern "C" int mdist_enumerate_unit_noalloc(const uint32_t *rows, int k, int nwo
     NoAllocScratch *s = reinterpret_cast<NoAllocScratch *>(scratch);
     cudaStream_t stream = (cudaStream_t)cuda_stream;
     p.rows = rows;
+    p.U = &s->slot.U;
     p.slot = &s->slot;
     p.hist = want_hist ? s->hist : nullptr;
     p.nwords = nwords;

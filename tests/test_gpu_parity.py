@@ -247,3 +247,14 @@ def test_filter_variants_identical(api, fg, n, k, seed):
         got = c.min_distance()
     assert got["total_combos"] <= ORACLE_BUDGET
     _assert_same_run(got, oracle.min_distance(G, n))
+
+
+@pytest.mark.parametrize("hint", [2, 4, 7, 30])
+@pytest.mark.parametrize("per_matrix", [False, True])
+def test_wave_hint_does_not_change_results(api, hint, per_matrix):
+    # levels launched ahead as one wave (hint too small, about right, far too large)
+    for n, k, seed in [(120, 36, 3), (96, 24, 5), (150, 36, 14)]:
+        G = synth.random_systematic(n, k, seed)
+        with api.Code(G, n, check_per_matrix=per_matrix, wstar_hint=hint) as c:
+            got = c.min_distance()
+        _assert_same_run(got, oracle.min_distance(G, n, check_per_matrix=per_matrix))
