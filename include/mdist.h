@@ -71,7 +71,8 @@ typedef struct {
                                 1 = exact weight of every codeword, 2..4 = first a lower
                                 bound (popcount of the OR of each group of that many
                                 32-bit words), exact weight only where the bound does not
-                                already exceed the threshold.  Results are identical. */
+                                already exceed the threshold, 5 = groups of 4, then of 2,
+                                then exact.  Results are identical. */
     long long timeout_cycles;/* bound for device-side waits (batched / serving); 0 = default */
     mdist_alloc_fn dev_alloc;/* optional device allocator */
     mdist_free_fn dev_free;
@@ -209,6 +210,42 @@ int mdist_batch_info(const mdist_batch *b, int *ncodes, int *graph_launches, int
                      double *seconds);
 
 void mdist_batch_free(mdist_batch *b);
+
+/* ---- serving loop ----------------------------------------------------------------- */
+
+/* Continuous batching of code requests on one GPU.  A serving thread runs rounds of the
+ * batched engine over a table of `max_slots` device slots.  Between rounds it retires
+ * finished requests and admits queued ones, first come first served, while a slot is
+ * free and the device rows pool (rows_pool_bytes) has room for the request's Gamma
+ * rows; admitted requests join the next round next to those already in flight.  Gamma
+ * rows and the per-request Alg. 1 state stay on the device until the request finishes.
+ * A request forms at most 8 information sets (fewer if opts->max_sets is smaller); its
+ * result equals mdist_min_distance's with the same max_sets.  All calls are thread-
+ * safe.  The server uses its own CUDA stream. */
+typedef struct mdist_server mdist_server;
+
+int mdist_server_create(const mdist_options *opts, int max_slots, size_t rows_pool_bytes, mdist_server **out);
+
+/* Queue a request (G copied, information sets computed on the calling thread).
+ * wstar_hint as in mdist_batch_add.  *request_id identifies it.  MDIST_ENOMEM if its
+ * rows can never fit the pool. */
+int mdist_server_submit(mdist_server *srv, const uint64_t *G, int n, int k, int words_per_row, int wstar_hint,
+                        long long *request_id);
+
+/* Result of a finished request (then forgotten): as mdist_result, plus the latency
+ * from submission to completion in seconds.  Waits up to wait_ms; MDIST_EAGAIN if the
+ * request is still queued or in flight. */
+int mdist_server_poll(mdist_server *srv, long long request_id, int wait_ms, int *d, uint64_t *witness,
+                      uint64_t *message, mdist_key *key, mdist_stats *stats, double *latency_s);
+
+/* Counters: requests admitted and completed, rounds run, requests queued and in
+ * flight, summed CUDA-event time of the rounds (ms).  Returns the server's sticky
+ * error, if any. */
+int mdist_server_info(mdist_server *srv, long long *admitted, long long *completed, long long *rounds, int *queued,
+                      int *in_flight, double *gpu_ms);
+
+/* Stop the serving thread (requests still queued or in flight are dropped) and free. */
+void mdist_server_free(mdist_server *srv);
 
 /* ---- work predictor (sizing only) ----------------------------------------------- */
 

@@ -120,6 +120,16 @@ SIGNATURES = {
     "mdist_batch_info": (ctypes.c_int, [ctypes.c_void_p, PI, PI, PI, ctypes.POINTER(ctypes.c_double),
                                         ctypes.POINTER(ctypes.c_double)]),
     "mdist_batch_free": (None, [ctypes.c_void_p]),
+    "mdist_server_create": (ctypes.c_int, [ctypes.POINTER(Options), ctypes.c_int, ctypes.c_size_t,
+                                           ctypes.POINTER(ctypes.c_void_p)]),
+    "mdist_server_submit": (ctypes.c_int, [ctypes.c_void_p, P64, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                           ctypes.c_int, ctypes.POINTER(ctypes.c_longlong)]),
+    "mdist_server_poll": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_longlong, ctypes.c_int, PI, P64, P64,
+                                         ctypes.POINTER(Key), ctypes.POINTER(Stats), ctypes.POINTER(ctypes.c_double)]),
+    "mdist_server_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_longlong),
+                                         ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong), PI, PI,
+                                         ctypes.POINTER(ctypes.c_double)]),
+    "mdist_server_free": (None, [ctypes.c_void_p]),
     "mdist_features": (ctypes.c_int, [P64, ctypes.c_int, ctypes.c_int, ctypes.c_int, PF]),
     "mdist_gv_estimate": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, PI, PI, PI]),
     "mdist_mlp_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_uint64,

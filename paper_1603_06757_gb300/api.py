@@ -234,6 +234,84 @@ def device_info() -> dict:
     return {"sm_count": sm.value, "max_sm_clock_khz": clk.value, "cc": (ma.value, mi.value)}
 
 
+class Server:
+    """Continuous-batching serving loop (mdist_server_*)."""
+
+    def __init__(self, *, max_slots: int = 1024, rows_pool_bytes: int = 64 << 20, check_per_matrix: bool = False,
+                 max_sets: int = 0, blocks_per_sm: int = 0, torch_alloc: bool = True):
+        torch = _torch()
+        self._lib = L.lib()
+        self._alloc = _TorchAllocator(torch, torch.cuda.current_device()) if torch_alloc else None
+        opts = L.Options()
+        opts.check_per_matrix = 1 if check_per_matrix else 0
+        opts.max_sets = int(max_sets)
+        opts.blocks_per_sm = int(blocks_per_sm)
+        if self._alloc is not None:
+            opts.dev_alloc = self._alloc.alloc_cb
+            opts.dev_free = self._alloc.free_cb
+        self._opts = opts
+        h = ctypes.c_void_p()
+        L.check(self._lib.mdist_server_create(ctypes.byref(opts), int(max_slots), int(rows_pool_bytes),
+                                              ctypes.byref(h)), "mdist_server_create")
+        self._h = h
+        self._W = {}
+
+    def submit(self, G, n: int, wstar_hint: int = 0) -> int:
+        G = as_packed(G, n)
+        k, W = G.shape
+        rid = ctypes.c_longlong()
+        L.check(self._lib.mdist_server_submit(self._h, _p64(G), int(n), k, W, int(wstar_hint), ctypes.byref(rid)),
+                "mdist_server_submit")
+        self._W[rid.value] = W
+        return rid.value
+
+    def poll(self, rid: int, wait_ms: int = 0):
+        """Result dict (with 'latency_s') or None if not finished yet."""
+        W = self._W[rid]
+        d = ctypes.c_int()
+        wit = np.zeros(W, dtype=np.uint64)
+        msg = np.zeros(1, dtype=np.uint64)
+        key = L.Key()
+        st = L.Stats()
+        lat = ctypes.c_double()
+        rc = self._lib.mdist_server_poll(self._h, int(rid), int(wait_ms), ctypes.byref(d), _p64(wit), _p64(msg),
+                                         ctypes.byref(key), ctypes.byref(st), ctypes.byref(lat))
+        if rc == L.EAGAIN:
+            return None
+        L.check(rc, "mdist_server_poll")
+        self._W.pop(rid, None)
+        out = _result_dict(d.value, wit, msg, key, st)
+        out["latency_s"] = lat.value
+        return out
+
+    def info(self) -> dict:
+        a, c, r = ctypes.c_longlong(), ctypes.c_longlong(), ctypes.c_longlong()
+        q, f = ctypes.c_int(), ctypes.c_int()
+        ms = ctypes.c_double()
+        rc = self._lib.mdist_server_info(self._h, ctypes.byref(a), ctypes.byref(c), ctypes.byref(r), ctypes.byref(q),
+                                         ctypes.byref(f), ctypes.byref(ms))
+        L.check(rc, "mdist_server_info")
+        return {"admitted": a.value, "completed": c.value, "rounds": r.value, "queued": q.value,
+                "in_flight": f.value, "gpu_ms": ms.value}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.mdist_server_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
 def partition_host(G, n: int, max_sets: int = 0) -> dict:
     """The information sets mdist_prepare would form, computed on the host only."""
     G = as_packed(G, n)

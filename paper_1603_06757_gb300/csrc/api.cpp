@@ -212,7 +212,7 @@ int mdist_prepare(const uint64_t *G, int n, int k, int words_per_row, const mdis
     mdist_code *c = new (std::nothrow) mdist_code();
     if (!c) return MDIST_ENOMEM;
     if (opts) c->opt = *opts;
-    if (c->opt.filter_group < 0 || c->opt.filter_group > 4) { delete c; return MDIST_EINVAL; }
+    if (c->opt.filter_group < 0 || c->opt.filter_group > 5) { delete c; return MDIST_EINVAL; }
     if (c->opt.max_sets <= 0 || c->opt.max_sets > MDIST_MAX_SETS) c->opt.max_sets = MDIST_MAX_SETS;
     c->n = n;
     c->k = k;
@@ -353,7 +353,9 @@ static int run_wave(mdist_code *c, int g_hi, int max_units, int *units_done) {
         }
     }
     const int n_units = (int)list.size();
-    const int U_thr = s.have_key ? s.key.weight : s.U;  // ties are candidates within a wave
+    // every unit of the wave follows the key's unit in (g, j) order, so only lighter
+    // codewords can replace the key; weights found inside the wave keep their ties
+    const int U_thr = s.have_key ? s.key.weight - 1 : s.U;
     for (int u = 0; u < n_units; ++u) {
         c->h_wave[u].U = 0;
         c->h_wave[u].pad0 = 0;

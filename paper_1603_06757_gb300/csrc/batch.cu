@@ -90,7 +90,8 @@ __global__ void batch_prep(BatchDev D) {
     }
     C.item0 = item0;
     C.nitems = n_items;
-    D.codeU[c] = (unsigned int)(C.have_key ? C.key_w : C.U);
+    // units of this round all follow the key's unit: only lighter codewords can replace it
+    D.codeU[c] = (unsigned int)(C.have_key ? C.key_w - 1 : C.U);
     int it = item0;
     for (int g = g0; g < g1; ++g) {
         for (int j = 0; j < C.m; ++j, ++it) {
@@ -256,6 +257,7 @@ __global__ void __launch_bounds__(kCtaThreads) batch_enum(const __grid_constant_
             case 2: walk_tile<NW, XP, 2, false>(x, wbuf, walk_len, nvalid, thr, nullptr, base, cand); break;
             case 3: walk_tile<NW, XP, 3, false>(x, wbuf, walk_len, nvalid, thr, nullptr, base, cand); break;
             case 4: walk_tile<NW, XP, 4, false>(x, wbuf, walk_len, nvalid, thr, nullptr, base, cand); break;
+            case 5: walk_tile<NW, XP, 5, false>(x, wbuf, walk_len, nvalid, thr, nullptr, base, cand); break;
             default: walk_tile<NW, XP, 0, false>(x, wbuf, walk_len, nvalid, thr, nullptr, base, cand); break;
         }
         if (lane == 0) {
@@ -303,6 +305,32 @@ static void batch_launch_nw(int nw, const BatchDev &D, int grid, cudaStream_t st
 #undef C
         default: break;
     }
+}
+
+// Host helpers shared with the serving loop (server.cu).
+cudaError_t batch_bucket_grids(const bool present[kBatchBuckets], int sm_count, int blocks_per_sm,
+                               int grid[kBatchBuckets]) {
+    for (int nb = 0; nb < kBatchBuckets; ++nb) {
+        grid[nb] = 0;
+        if (!present[nb]) continue;
+        int occ = 0;
+        const cudaError_t e = batch_prepare_nw(nb + 1, &occ);
+        if (e != cudaSuccess) return e;
+        if (occ < 1) return cudaErrorInvalidConfiguration;
+        const int per_sm = blocks_per_sm > 0 && blocks_per_sm < occ ? blocks_per_sm : occ;
+        grid[nb] = sm_count * per_sm;
+    }
+    return cudaSuccess;
+}
+
+void batch_launch_round(const BatchDev &D, const bool present[kBatchBuckets], const int grid[kBatchBuckets],
+                        cudaStream_t st) {
+    const int tb = 128, cb = (D.ncodes + tb - 1) / tb;
+    batch_round_begin<<<1, 32, 0, st>>>(D);
+    batch_prep<<<cb, tb, 0, st>>>(D);
+    for (int nb = 0; nb < kBatchBuckets; ++nb)
+        if (present[nb]) batch_launch_nw(nb + 1, D, grid[nb], st);
+    batch_update<<<cb, tb, 0, st>>>(D);
 }
 
 }  // namespace mdist
@@ -540,21 +568,14 @@ int mdist_batch_run(mdist_batch *b, int rounds_per_graph) {
     D.item_cap = (int)cap;
     // ---- grids per bucket ----
     int grid[kBatchBuckets] = {};
-    for (int nb = 0; nb < kBatchBuckets; ++nb) {
-        if (!present[nb]) continue;
-        int occ = 0;
-        if (batch_prepare_nw(nb + 1, &occ) != cudaSuccess || occ < 1) {
-            if (own) cudaStreamDestroy(own);
-            bfree_all(b);
-            return MDIST_ECUDA;
-        }
-        const int per_sm = b->opt.blocks_per_sm > 0 && b->opt.blocks_per_sm < occ ? b->opt.blocks_per_sm : occ;
-        grid[nb] = b->sm_count * per_sm;
+    if (batch_bucket_grids(present, b->sm_count, b->opt.blocks_per_sm, grid) != cudaSuccess) {
+        if (own) cudaStreamDestroy(own);
+        bfree_all(b);
+        return MDIST_ECUDA;
     }
     // ---- capture the rounds into one graph ----
     const int R = rounds_per_graph > 0 ? rounds_per_graph : std::max(4, std::min(16, max_spec + 2));
     b->rounds_per_graph = R;
-    const int tb = 128, cb = (C + tb - 1) / tb;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
@@ -563,13 +584,7 @@ int mdist_batch_run(mdist_batch *b, int rounds_per_graph) {
         bfree_all(b);
         return MDIST_ECUDA;
     }
-    for (int r = 0; r < R; ++r) {
-        batch_round_begin<<<1, 32, 0, st>>>(D);
-        batch_prep<<<cb, tb, 0, st>>>(D);
-        for (int nb = 0; nb < kBatchBuckets; ++nb)
-            if (present[nb]) batch_launch_nw(nb + 1, D, grid[nb], st);
-        batch_update<<<cb, tb, 0, st>>>(D);
-    }
+    for (int r = 0; r < R; ++r) batch_launch_round(D, present, grid, st);
     if (cudaStreamEndCapture(st, &graph) != cudaSuccess || cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) {
         if (graph) cudaGraphDestroy(graph);
         cudaGetLastError();

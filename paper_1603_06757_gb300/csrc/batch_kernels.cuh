@@ -84,4 +84,11 @@ struct BatchDev {                // what the kernels share (passed by value)
     int item_cap;
 };
 
+// Grid of the enumerator of each present bucket (SMs x CTAs per SM).
+cudaError_t batch_bucket_grids(const bool present[kBatchBuckets], int sm_count, int blocks_per_sm,
+                               int grid[kBatchBuckets]);
+// One round: clear counters, prepare items, enumerate every present bucket, fold.
+void batch_launch_round(const BatchDev &D, const bool present[kBatchBuckets], const int grid[kBatchBuckets],
+                        cudaStream_t st);
+
 }  // namespace mdist

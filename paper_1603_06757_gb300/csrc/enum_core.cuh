@@ -73,6 +73,21 @@ __device__ __forceinline__ void stage_walk(uint32_t *__restrict__ wbuf, const ui
     }
 }
 
+// Lower bound of the weight of x ^ y: sum over groups of G consecutive words of the
+// popcount of the OR of the group's XORed words.
+template <int NW, int G>
+__device__ __forceinline__ int or_bound(const uint32_t (&x)[NW], const uint32_t (&y)[NW]) {
+    int lb = 0;
+#pragma unroll
+    for (int q = 0; q < NW; q += G) {
+        uint32_t o = 0;
+#pragma unroll
+        for (int w = q; w < q + G && w < NW; ++w) o |= x[w] ^ y[w];
+        lb += __popc(o);
+    }
+    return lb;
+}
+
 // The walk over one tile.  GS = 0: exact weight of every codeword (XOR, POPC per
 // word, sum, running min, one compare per step).  GS = 2, 3, 4: a lower bound first,
 // the popcount of the OR of each group of GS XORed words (weight >= bound), and the
@@ -107,21 +122,24 @@ __device__ __forceinline__ void walk_tile(const uint32_t (&x)[XP][NW], const uin
                 }
             }
         } else {
-            // lower bound first (weight >= sum over groups of GS words of the popcount of
-            // their OR), minimum over the lane's entries, one branch per step; the exact
-            // weights are computed only in steps where some bound reaches the threshold
+            // lower bound first (weight >= sum over groups of G1 words of the popcount of
+            // their OR), minimum over the lane's entries, one branch per step; GS = 5
+            // takes groups of 4 first and, in the steps that pass, groups of 2; the exact
+            // weights are computed only in steps where the last bound reaches the threshold
+            constexpr int G1 = GS == 5 ? 4 : GS;
             int mn = INT_MAX;
 #pragma unroll
             for (int p = 0; p < XP; ++p) {
-                int lb = 0;
-#pragma unroll
-                for (int q = 0; q < NW; q += GS) {
-                    uint32_t o = 0;
-#pragma unroll
-                    for (int w = q; w < q + GS && w < NW; ++w) o |= x[p][w] ^ y[w];
-                    lb += __popc(o);
-                }
+                const int lb = or_bound<NW, G1>(x[p], y);
                 mn = lb < mn ? lb : mn;
+            }
+            if (GS == 5 && mn <= thr) {
+                mn = INT_MAX;
+#pragma unroll
+                for (int p = 0; p < XP; ++p) {
+                    const int lb = or_bound<NW, 2>(x[p], y);
+                    mn = lb < mn ? lb : mn;
+                }
             }
             if (mn <= thr) {
 #pragma unroll

@@ -184,7 +184,8 @@ cudaError_t launch_variant(const EnumParams &p, int sm_count, int blocks_per_sm,
     return cudaGetLastError();
 }
 
-// group: 0 = exact count for every codeword; 2, 3, 4 = OR-group lower bound first
+// group: 0 = exact count for every codeword; 2, 3, 4 = OR-group lower bound first;
+// 5 = groups of 4, then groups of 2, then exact
 template <int NW>
 cudaError_t launch_nw(const EnumParams &p, int group, bool hist_mode, int sm_count, int blocks_per_sm,
                       cudaStream_t stream) {
@@ -194,6 +195,7 @@ cudaError_t launch_nw(const EnumParams &p, int group, bool hist_mode, int sm_cou
         case 2: return launch_variant<NW, 2, false>(p, sm_count, blocks_per_sm, stream);
         case 3: return launch_variant<NW, 3, false>(p, sm_count, blocks_per_sm, stream);
         case 4: return launch_variant<NW, 4, false>(p, sm_count, blocks_per_sm, stream);
+        case 5: return launch_variant<NW, 5, false>(p, sm_count, blocks_per_sm, stream);
         default: return cudaErrorInvalidValue;
     }
 }

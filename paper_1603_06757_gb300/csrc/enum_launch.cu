@@ -107,23 +107,35 @@ int choose_filter_group(int nwords, int n_bits, int thr) {
     const double exact = std::fmax(nwords / 16.0, 3.0 * nwords / 128.0);
     if (thr >= n_bits) return 0;
     const double step_cw = 32.0 * lane_entries_per_thread(nwords);
+    auto pstep = [&](int gs) {
+        if (thr < 0) return 0.0;
+        const std::vector<double> &cdf = lower_bound_cdf(nwords, n_bits, gs);
+        const double p = cdf[(size_t)(thr < (int)cdf.size() ? thr : (int)cdf.size() - 1)];
+        return 1.0 - std::pow(1.0 - p, step_cw);
+    };
     double best_cost = exact;
     int best = 0;
     for (int gs = 2; gs <= 4; ++gs) {
         if (gs > nwords) break;
         const int ng = (nwords + gs - 1) / gs;
-        double p = 0.0;
-        if (thr >= 0) {
-            const std::vector<double> &cdf = lower_bound_cdf(nwords, n_bits, gs);
-            p = cdf[(size_t)(thr < (int)cdf.size() ? thr : (int)cdf.size() - 1)];
-        }
-        const double pstep = 1.0 - std::pow(1.0 - p, step_cw);
-        const double popc = ng + pstep * nwords;
-        const double instr = nwords + 2.0 * ng + pstep * (3.0 * nwords + 3.0);
+        const double ps = pstep(gs);
+        const double popc = ng + ps * nwords;
+        const double instr = nwords + 2.0 * ng + ps * (3.0 * nwords + 3.0);
         const double cost = std::fmax(popc / 16.0, instr / 128.0);
         if (cost < best_cost * 0.98) {
             best_cost = cost;
             best = gs;
+        }
+    }
+    if (nwords >= 4) {  // two levels: groups of 4, then groups of 2 where the first passes
+        const int ng4 = (nwords + 3) / 4, ng2 = (nwords + 1) / 2;
+        const double p4 = pstep(4), p2 = pstep(2);
+        const double popc = ng4 + p4 * ng2 + p2 * nwords;
+        const double instr = nwords + 2.0 * ng4 + p4 * (nwords + 2.0 * ng2 + 2.0) + p2 * (3.0 * nwords + 3.0);
+        const double cost = std::fmax(popc / 16.0, instr / 128.0);
+        if (cost < best_cost * 0.98) {
+            best_cost = cost;
+            best = 5;
         }
     }
     return best;

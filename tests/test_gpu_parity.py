@@ -238,10 +238,10 @@ def test_side_stream(api):
 VARIANT_CASES = [(120, 36, 3), (150, 36, 14), (180, 36, 13), (300, 30, 2), (500, 25, 6), (96, 24, 5)]
 
 
-@pytest.mark.parametrize("fg", [1, 2, 3, 4])
+@pytest.mark.parametrize("fg", [1, 2, 3, 4, 5])
 @pytest.mark.parametrize("n,k,seed", VARIANT_CASES)
 def test_filter_variants_identical(api, fg, n, k, seed):
-    # every enumerator variant (exact, OR-groups of 2, 3, 4 words) gives the same run
+    # every enumerator variant (exact, OR-groups of 2, 3, 4 words, 4 then 2) gives the same run
     G = synth.random_systematic(n, k, seed)
     with api.Code(G, n, filter_group=fg) as c:
         got = c.min_distance()

@@ -255,8 +255,10 @@ def test_filter_choice(lib):
     assert _choice(lib, 4, 128, 128) == 0
     # one word: nothing to group
     assert _choice(lib, 1, 20, 3) == 0
-    # the last levels of [192,64] (reduced weight <= 24 of 128 bits): a one-POPC bound
-    assert _choice(lib, 4, 128, 24) in (2, 4)
+    # the last levels of [192,64] (reduced weight <= 24 of 128 bits): groups of 4, then 2
+    assert _choice(lib, 4, 128, 24) == 5
+    assert _choice(lib, 4, 128, 28) == 2
+    assert _choice(lib, 4, 128, 12) == 4
     # threshold near the mean of a random codeword: the bound rarely rejects -> exact
     assert _choice(lib, 4, 128, 62) == 0
     # [300,50]-like rows (250 bits, threshold ~67): pairs of words
