@@ -24,6 +24,8 @@ import sys
 import threading
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
@@ -325,6 +327,213 @@ def run_profile_unit(args):
     return 0
 
 
+# ----------------------------------------------------------------------------------
+# batched codes and the predictor (config: 4096 random codes, k in [24, 56], n in [2k, 3k])
+# ----------------------------------------------------------------------------------
+
+def batch_codes(count, seed, seed_base, cap, k_lo=24, k_hi=56, nmul_hi=3):
+    """Codes of the batched workload whose Gilbert-Varshamov work estimate is <= cap:
+    list of (n, k, G, ranks)."""
+    import synth
+    from paper_1603_06757_gb300 import api, predict
+
+    out = []
+    for s in synth.batch_specs(count, k_lo, k_hi, 2, nmul_hi, seed=seed, seed_base=seed_base):
+        G = synth.random_systematic(s.n, s.k, s.seed)
+        ranks = [int(r) for r in api.partition_host(G, s.n)["ranks"]]
+        _, w = predict.gv_estimate(s.n, s.k, ranks)
+        work = sum(len(ranks) * math.comb(s.k, g) for g in range(1, w + 1))
+        if work <= cap:
+            out.append((s.n, s.k, G, ranks))
+    return out
+
+
+def run_plain(codes, hints=None):
+    """One code after the other through mdist_prepare + mdist_min_distance."""
+    import torch
+
+    from paper_1603_06757_gb300 import api
+
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    res = []
+    for i, (n, k, G, _) in enumerate(codes):
+        with api.Code(G, n, wstar_hint=hints[i] if hints else 0) as c:
+            res.append(c.min_distance())
+    torch.cuda.synchronize()
+    return len(codes) / (time.perf_counter() - t0), res
+
+
+def run_batched(codes, hints=None):
+    """All codes in one batched run (rounds captured in one CUDA graph)."""
+    import torch
+
+    from paper_1603_06757_gb300 import api
+
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    with api.Batch() as b:
+        for i, (n, k, G, _) in enumerate(codes):
+            b.add(G, n, wstar_hint=hints[i] if hints else 0)
+        b.run()
+        res = [b.result(i) for i in range(len(codes))]
+        info = b.info()
+    torch.cuda.synchronize()
+    return len(codes) / (time.perf_counter() - t0), res, info
+
+
+def train_predictor(train_codes, steps=3000):
+    """MLP on features -> (d / n, w* / k), labels from the batched engine's own runs."""
+    from paper_1603_06757_gb300 import predict
+
+    _, res, _ = run_batched(train_codes)
+    codes = [(G, n) for (n, k, G, _) in train_codes]
+    labels = [(r["d"], r["g_final"]) for r in res]
+    mlp, curve = predict.train_predictor(codes, labels, steps=steps)
+    return mlp, curve
+
+
+def predictor_report(mlp, test_codes, test_res):
+    from paper_1603_06757_gb300 import predict
+
+    shapes = [(n, k, ranks) for (n, k, G, ranks) in test_codes]
+    feats = np.stack([predict.features(G, n) for (n, k, G, _) in test_codes])
+    truth = [(r["g_final"], r["d"]) for r in test_res]
+    p_mlp = predict.Predictor(mlp).predict(feats, shapes)
+    p_gv = predict.Predictor(None).predict(feats, shapes)
+    return p_mlp, p_gv, {"mlp": predict.errors(p_mlp, truth), "gv": predict.errors(p_gv, truth)}
+
+
+def run_batch_bench(args):
+    import torch
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    torch.cuda.set_device(0)
+    cap = args.batch_cap
+    test = batch_codes(args.batch_codes, 2024, 1000, cap)
+    train = batch_codes(args.batch_train, 77, 500000, cap)
+    mlp, curve = train_predictor(train)
+    # warm-up of every path
+    run_batched(test[:64])
+    run_plain(test[:16])
+    cps_batch, res_b, info_b = run_batched(test)
+    p_mlp, p_gv, errs = predictor_report(mlp, test, res_b)
+    h_mlp = [w for (w, d) in p_mlp]
+    h_gv = [w for (w, d) in p_gv]
+    cps_batch_mlp, res_bm, info_bm = run_batched(test, h_mlp)
+    cps_batch_gv, _, info_bg = run_batched(test, h_gv)
+    cps_plain, res_p = run_plain(test)
+    cps_plain_mlp, _ = run_plain(test, h_mlp)
+    cps_plain_gv, _ = run_plain(test, h_gv)
+    same = all(a["d"] == b["d"] and a["key"] == b["key"] and np.array_equal(a["counts"], b["counts"])
+               for a, b in zip(res_b, res_p)) and all(a["key"] == b["key"] for a, b in zip(res_b, res_bm))
+    cw = sum(r["total_combos"] for r in res_b)
+    line = {
+        "metric": "codes/s, batched vs plain (one code per prepare/run)", "unit": "codes/s",
+        "value": cps_batch_mlp, "higher_is_better": True, "n_gpus": 1, "data": "synthetic",
+        "config": {"workload": f"{args.batch_codes} random codes, k ~ U[24,56], n ~ U[2k,3k], seeds 1000+i; "
+                               f"kept: GV work estimate <= {cap:.0e} codewords",
+                   "codes": len(test), "codewords": cw, "train_codes": len(train)},
+        "codes_per_s": {"plain": cps_plain, "plain_gv_hint": cps_plain_gv, "plain_mlp_hint": cps_plain_mlp,
+                        "batched": cps_batch, "batched_gv_hint": cps_batch_gv, "batched_mlp_hint": cps_batch_mlp},
+        "rounds": {"batched": info_b["rounds"], "batched_mlp_hint": info_bm["rounds"],
+                   "batched_gv_hint": info_bg["rounds"]},
+        "predictor": errs, "train_loss_last": float(curve[-50:].mean()),
+        "results_identical": bool(same),
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def serve_requests(count, seed, cap):
+    """Request stream: k ~ U[20,64], n ~ U[2k,4k]; a draw whose GV work estimate exceeds
+    cap is redrawn from the same stream (rejection sampling)."""
+    import synth
+    from paper_1603_06757_gb300 import api, predict
+
+    rng = synth.SplitMix64(seed)
+    out, rejected = [], 0
+    while len(out) < count:
+        k = rng.uniform_int(20, 64)
+        n = rng.uniform_int(2 * k, 4 * k)
+        cs = rng.next()
+        G = synth.random_systematic(n, k, cs)
+        ranks = [int(r) for r in api.partition_host(G, n, max_sets=8)["ranks"]]
+        _, w = predict.gv_estimate(n, k, ranks)
+        if sum(len(ranks) * math.comb(k, g) for g in range(1, w + 1)) > cap:
+            rejected += 1
+            continue
+        out.append((n, k, G, ranks))
+    return out, rejected
+
+
+def run_serve_bench(args):
+    import threading as th
+
+    import torch
+
+    import __graft_entry__
+    import synth
+
+    __graft_entry__.build()
+    torch.cuda.set_device(0)
+    from paper_1603_06757_gb300 import api, predict
+
+    reqs, rejected = serve_requests(args.serve_requests, 4242, args.serve_cap)
+    train = batch_codes(args.batch_train, 77, 500000, args.batch_cap, k_lo=20, k_hi=64, nmul_hi=4)
+    mlp, _ = train_predictor(train)
+    shapes = [(n, k, ranks) for (n, k, G, ranks) in reqs]
+    feats = np.stack([predict.features(G, n) for (n, k, G, _) in reqs])
+    hints = [w for (w, d) in predict.Predictor(mlp).predict(feats, shapes)]
+    # capacity: the whole stream as one batch
+    cps_batch, _, _ = run_batched([(n, k, G, r) for (n, k, G, r) in reqs], hints)
+    rate = args.serve_load * cps_batch
+    arrivals = synth.poisson_arrivals(len(reqs), rate, seed=99)
+    with api.Server(max_slots=args.serve_slots, rows_pool_bytes=64 << 20) as srv:
+        ids = [None] * len(reqs)
+        t0 = time.perf_counter()
+
+        def feeder():
+            for i, (n, k, G, _) in enumerate(reqs):
+                dt = arrivals[i] - (time.perf_counter() - t0)
+                if dt > 0:
+                    time.sleep(dt)
+                ids[i] = srv.submit(G, n, wstar_hint=hints[i])
+
+        f = th.Thread(target=feeder)
+        f.start()
+        lat = {}
+        while len(lat) < len(reqs):
+            for i in range(len(reqs)):
+                if i not in lat and ids[i] is not None:
+                    r = srv.poll(ids[i], wait_ms=0)
+                    if r is not None:
+                        lat[i] = r["latency_s"]
+            time.sleep(0.002)
+        f.join()
+        wall = time.perf_counter() - t0
+        info = srv.info()
+    lats = np.array([lat[i] for i in range(len(reqs))])
+    sample = reqs[: min(len(reqs), args.serve_plain_sample)]
+    cps_plain, _ = run_plain(sample)
+    line = {
+        "metric": "served codes/s and latency vs plain per-code launches", "unit": "codes/s",
+        "value": len(reqs) / wall, "higher_is_better": True, "n_gpus": 1, "data": "synthetic",
+        "config": {"workload": f"Poisson stream of {len(reqs)} requests, k ~ U[20,64], n ~ U[2k,4k]; draws with "
+                               f"GV work estimate > {args.serve_cap:.0e} redrawn ({rejected} redrawn)",
+                   "arrival_rate_per_s": rate, "load": args.serve_load, "slots": args.serve_slots},
+        "latency_s": {"p50": float(np.percentile(lats, 50)), "p99": float(np.percentile(lats, 99)),
+                      "mean": float(lats.mean()), "max": float(lats.max())},
+        "codes_per_s": {"served": len(reqs) / wall, "batched_capacity": cps_batch,
+                        "plain": cps_plain, "plain_sample": len(sample)},
+        "rounds": info["rounds"], "gpu_ms": info["gpu_ms"],
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -335,11 +544,24 @@ def main():
     ap.add_argument("--cpu-levels", type=int, default=8)
     ap.add_argument("--ref-levels", type=int, default=7)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--mode", choices=["single", "batch", "serve"], default="single")
+    ap.add_argument("--batch-codes", type=int, default=4096)
+    ap.add_argument("--batch-train", type=int, default=1500)
+    ap.add_argument("--batch-cap", type=float, default=1e10)
+    ap.add_argument("--serve-requests", type=int, default=20000)
+    ap.add_argument("--serve-cap", type=float, default=1e11)
+    ap.add_argument("--serve-load", type=float, default=0.7)
+    ap.add_argument("--serve-slots", type=int, default=1024)
+    ap.add_argument("--serve-plain-sample", type=int, default=500)
     ap.add_argument("--profile-unit", type=int, default=0, help="run one unit of this level (profiling)")
     ap.add_argument("--profile-d", type=int, default=0, help="d of the workload if known (skips the full run)")
     args = ap.parse_args()
     if args.profile_unit:
         return run_profile_unit(args)
+    if args.mode == "batch":
+        return run_batch_bench(args)
+    if args.mode == "serve":
+        return run_serve_bench(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

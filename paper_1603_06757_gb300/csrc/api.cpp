@@ -124,7 +124,7 @@ int run_unit(mdist_code *c, int g, int j, int U_thr, bool hist_mode, bool *found
         const int fg = c->opt.filter_group;
         group = fg == 0 ? mdist::choose_filter_group(dr.nwords, dr.n_bits, (U_thr < 0 ? 0 : U_thr) - p.base)
                         : (fg == 1 ? 0 : fg);
-        if (group > dr.nwords) group = 0;
+        if (!mdist::filter_group_valid(group, dr.nwords)) group = 0;
     }
     c->st.last_group = group;
     if (mdist::launch_enum_unit(p, dr.nwords, group, hist_mode, c->sm_count, c->opt.blocks_per_sm, c->stream) !=
@@ -389,7 +389,7 @@ static int run_wave(mdist_code *c, int g_hi, int max_units, int *units_done) {
         q.base = dr.full_rank ? g : 0;
         const int fg = c->opt.filter_group;
         int group = fg == 0 ? mdist::choose_filter_group(dr.nwords, dr.n_bits, U_thr - q.base) : (fg == 1 ? 0 : fg);
-        if (group > dr.nwords) group = 0;
+        if (!mdist::filter_group_valid(group, dr.nwords)) group = 0;
         if (mdist::launch_enum_unit(q, dr.nwords, group, false, c->sm_count, c->opt.blocks_per_sm, c->stream) !=
             cudaSuccess)
             return MDIST_ECUDA;

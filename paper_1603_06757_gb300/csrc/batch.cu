@@ -170,15 +170,16 @@ __global__ void batch_update(BatchDev D) {
 
 // Persistent enumerator of one bucket (row width NW) for one round.
 template <int NW>
-__global__ void __launch_bounds__(kCtaThreads) batch_enum(const __grid_constant__ BatchDev D, int bucket) {
+__global__ void __launch_bounds__(kCtaThreads, MDIST_ENUM_MIN_BLOCKS) batch_enum(const __grid_constant__ BatchDev D, int bucket) {
     constexpr int XP = lane_entries_per_thread(NW);
     constexpr int YL = walk_len_for(NW);
     constexpr int PER = YL / 32;
+    constexpr int SW = walk_stride(NW);
     extern __shared__ __align__(16) uint32_t smem[];
-    uint32_t *s_bn = smem;                                     // 33 x 33
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    uint32_t *wrows = s_bn + kBn * kBn + warp * (kMaxK * NW + YL * NW);  // this warp's rows
-    uint32_t *wbuf = wrows + kMaxK * NW;                                 // and walk buffer
+    uint32_t *wbuf = smem + warp * YL * SW;                                // this warp's walk buffer
+    uint32_t *wrows = smem + kWarpsPerCta * YL * SW + warp * kMaxK * NW;    // and rows
+    uint32_t *s_bn = smem + kWarpsPerCta * (YL * SW + kMaxK * NW);          // 33 x 33
     for (int i = threadIdx.x; i < kBn * kBn; i += blockDim.x) s_bn[i] = (uint32_t)c_binom_b.v[i / kBn][i % kBn];
     __syncthreads();
     const unsigned long long packed = D.bucket_packed[bucket];
@@ -271,7 +272,8 @@ __global__ void __launch_bounds__(kCtaThreads) batch_enum(const __grid_constant_
 
 template <int NW>
 size_t batch_smem_bytes() {
-    return sizeof(uint32_t) * ((size_t)kBn * kBn + (size_t)kWarpsPerCta * (kMaxK * NW + walk_len_for(NW) * NW));
+    return sizeof(uint32_t) *
+           ((size_t)kBn * kBn + (size_t)kWarpsPerCta * (kMaxK * NW + walk_len_for(NW) * walk_stride(NW)));
 }
 
 template <int NW>

@@ -49,8 +49,9 @@ __device__ __forceinline__ void build_lane_entries(uint32_t (&x)[XP][NW], const 
     }
 }
 
-// wbuf[s] = sum of the rows of walk-side subset w_first + s, s < walk_len; lane l
-// builds entries [l * per, (l + 1) * per).
+// wbuf[s] = sum of the rows of walk-side subset w_first + s, s < walk_len, entries
+// walk_stride(NW) words apart (16-byte aligned); lane l builds entries
+// [l * per, (l + 1) * per).
 template <int NW>
 __device__ __forceinline__ void stage_walk(uint32_t *__restrict__ wbuf, const uint32_t *__restrict__ bn,
                                            const uint32_t *__restrict__ rows, int kh, int t,
@@ -61,15 +62,16 @@ __device__ __forceinline__ void stage_walk(uint32_t *__restrict__ wbuf, const ui
     uint32_t y[NW];
 #pragma unroll
     for (int w = 0; w < NW; ++w) y[w] = 0;
+    constexpr int SW = walk_stride(NW);
     xor_rows<NW>(y, rows, wm);
 #pragma unroll
-    for (int w = 0; w < NW; ++w) wbuf[s0 * NW + w] = y[w];
+    for (int w = 0; w < NW; ++w) wbuf[s0 * SW + w] = y[w];
     for (int q = 1; q < per && s0 + q < walk_len; ++q) {
         const uint32_t nm = next_colex(wm);
         xor_rows<NW>(y, rows, wm ^ nm);
         wm = nm;
 #pragma unroll
-        for (int w = 0; w < NW; ++w) wbuf[(s0 + q) * NW + w] = y[w];
+        for (int w = 0; w < NW; ++w) wbuf[(s0 + q) * SW + w] = y[w];
     }
 }
 
@@ -98,10 +100,20 @@ template <int NW, int XP, int GS, bool HIST, class Cand>
 __device__ __forceinline__ void walk_tile(const uint32_t (&x)[XP][NW], const uint32_t *__restrict__ wbuf,
                                           int walk_len, int nvalid, int &thr, unsigned int *s_hist, int base,
                                           Cand &&cand) {
+    constexpr int SW = walk_stride(NW);
     for (int s = 0; s < walk_len; ++s) {
         uint32_t y[NW];
+        {  // one broadcast 128-bit shared load per 4 words
+            const uint4 *v = reinterpret_cast<const uint4 *>(wbuf + s * SW);
 #pragma unroll
-        for (int w = 0; w < NW; ++w) y[w] = wbuf[s * NW + w];
+            for (int q = 0; q < SW / 4; ++q) {
+                const uint4 t = v[q];
+                if (4 * q + 0 < NW) y[4 * q + 0] = t.x;
+                if (4 * q + 1 < NW) y[4 * q + 1] = t.y;
+                if (4 * q + 2 < NW) y[4 * q + 2] = t.z;
+                if (4 * q + 3 < NW) y[4 * q + 3] = t.w;
+            }
+        }
         if (GS == 0) {
             int mn = INT_MAX;
 #pragma unroll

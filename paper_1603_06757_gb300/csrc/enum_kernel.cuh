@@ -41,7 +41,7 @@ struct DeviceBinom {
 
 // Side path for a codeword at or below the threshold: rebuild its combination,
 // compute the key, publish the weight.  Kept out of line so the hot loop stays small.
-static __device__ __noinline__ unsigned long long candidate_key(const EnumParams &P, const ProductBlock &B,
+static __device__ __forceinline__ unsigned long long candidate_key(const EnumParams &P, const ProductBlock &B,
                                                          const uint32_t *bn, uint32_t lane_rank, uint32_t walk_rank,
                                                          int weight) {
     const int lane_kh = B.lane_half ? P.k2 : P.k1;
@@ -63,15 +63,16 @@ struct EnumCfg {
 };
 
 template <int NW, int GS, bool HIST>
-__global__ void __launch_bounds__(kCtaThreads) enum_unit_kernel(const __grid_constant__ EnumParams P) {
+__global__ void __launch_bounds__(kCtaThreads, MDIST_ENUM_MIN_BLOCKS) enum_unit_kernel(const __grid_constant__ EnumParams P) {
     constexpr int XP = EnumCfg<NW>::XP;
     constexpr int YL = EnumCfg<NW>::YL;
     constexpr int PER = YL / 32;
+    constexpr int SW = walk_stride(NW);
     extern __shared__ __align__(16) uint32_t smem[];
-    uint32_t *s_rows = smem;                             // k x NW
+    uint32_t *s_walk = smem;                             // warps x YL x SW (16-byte entries)
+    uint32_t *s_rows = s_walk + kWarpsPerCta * YL * SW;  // k x NW
     uint32_t *s_bn = s_rows + P.k * NW;                  // 33 x 33
-    uint32_t *s_walk = s_bn + kBn * kBn;                 // warps x YL x NW
-    unsigned int *s_hist = s_walk + kWarpsPerCta * YL * NW;  // histogram mode: n+1 bins
+    unsigned int *s_hist = s_bn + kBn * kBn;             // histogram mode: n+1 bins
 
     for (int i = threadIdx.x; i < P.k * NW; i += blockDim.x) s_rows[i] = P.rows[i];
     for (int i = threadIdx.x; i < kBn * kBn; i += blockDim.x) {
@@ -84,7 +85,7 @@ __global__ void __launch_bounds__(kCtaThreads) enum_unit_kernel(const __grid_con
 
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
-    uint32_t *wbuf = s_walk + warp * YL * NW;
+    uint32_t *wbuf = s_walk + warp * YL * SW;
     UnitSlot *slot = P.slot;
     int thr = (int)(*(volatile unsigned int *)P.U) - P.base;  // candidates: reduced weight <= thr
     unsigned long long best = kNoKey;
@@ -161,7 +162,8 @@ __global__ void __launch_bounds__(kCtaThreads) enum_unit_kernel(const __grid_con
 
 inline size_t enum_smem_bytes_nw(int k, int nw, int hist_bins) {
     const int yl = walk_len_for(nw);
-    return sizeof(uint32_t) * ((size_t)k * nw + kBn * kBn + (size_t)kWarpsPerCta * yl * nw + (size_t)hist_bins);
+    return sizeof(uint32_t) *
+           ((size_t)k * nw + kBn * kBn + (size_t)kWarpsPerCta * yl * walk_stride(nw) + (size_t)hist_bins);
 }
 
 template <int NW, int GS, bool HIST>

@@ -142,7 +142,8 @@ int choose_filter_group(int nwords, int n_bits, int thr) {
 }
 
 size_t enum_smem_bytes(int k, int nwords) {
-    return sizeof(uint32_t) * ((size_t)k * nwords + 33 * 33 + (size_t)kWarpsPerCta * walk_len_for(nwords) * nwords);
+    return sizeof(uint32_t) *
+           ((size_t)k * nwords + 33 * 33 + (size_t)kWarpsPerCta * walk_len_for(nwords) * walk_stride(nwords));
 }
 
 cudaError_t launch_enum_unit(const EnumParams &p, int nwords, int group, bool hist_mode, int sm_count,

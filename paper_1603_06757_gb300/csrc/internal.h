@@ -18,6 +18,10 @@ constexpr int kMaxWords32 = kMaxN / 32;  // 32-bit words of a reduced row
 constexpr int kMaxBlocks = 34;           // product blocks per level: i in [0, 32] (+1 spare)
 constexpr int kWarpsPerCta = 8;
 constexpr int kCtaThreads = 32 * kWarpsPerCta;
+// CTAs per SM the enumerator kernels are compiled for (register budget 65536 / (256 x this))
+#ifndef MDIST_ENUM_MIN_BLOCKS
+#define MDIST_ENUM_MIN_BLOCKS 2
+#endif
 constexpr int kKeyRankBits = 54;         // device key = weight << 54 | lexicographic rank
 constexpr uint64_t kNoKey = ~0ull;
 
@@ -71,6 +75,15 @@ cudaError_t launch_enum_unit(const EnumParams &p, int nwords, int group, bool hi
 // Filter variant for a unit: 0 (exact count for every codeword) or the OR-group size
 // 2, 3, 4 whose expected cost is least for this row width and threshold.
 int choose_filter_group(int nwords, int n_bits, int thr);
+
+// Variant codes: 0 exact; 2..4 one level of OR groups (group size <= nwords);
+// 5 groups of 4 then of 2 (nwords >= 4).
+inline bool filter_group_valid(int group, int nwords) {
+    return group == 0 || (group >= 2 && group <= 4 && group <= nwords) || (group == 5 && nwords >= 4);
+}
+
+// Stride in 32-bit words of a staged walk entry: padded to whole 16-byte vectors.
+__host__ __device__ constexpr int walk_stride(int nwords) { return (nwords + 3) & ~3; }
 size_t enum_smem_bytes(int k, int nwords);
 
 // Host-side binomial coefficients C(a, b), a <= 64 (enum_launch.cu).

@@ -1,0 +1,70 @@
+"""The learned predictor, trained by the library's own kernels on labels from the
+method's own runs, against the analytic Gilbert-Varshamov fallback on held-out codes;
+and the predictions used as hints never change a result."""
+
+import numpy as np
+import pytest
+
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    assert torch.cuda.is_available()
+    from paper_1603_06757_gb300 import api, predict
+
+    return api, predict
+
+
+def _codes(count, seed, seed_base):
+    specs = synth.batch_specs(count, 16, 40, 2, 3, seed=seed, seed_base=seed_base)
+    return [(s.n, s.k, synth.random_systematic(s.n, s.k, s.seed)) for s in specs]
+
+
+def _labels(api, codes):
+    with api.Batch() as b:
+        for n, k, G in codes:
+            b.add(G, n)
+        b.run()
+        return [b.result(i) for i in range(len(codes))]
+
+
+def test_trained_mlp_beats_gv_and_hints_keep_results(env):
+    api, predict = env
+    train = _codes(700, 11, 700000)
+    test = _codes(200, 12, 800000)
+    train_res = _labels(api, train)
+    mlp, curve = predict.train_predictor([(G, n) for n, k, G in train],
+                                         [(r["d"], r["g_final"]) for r in train_res], steps=3000)
+    assert np.all(np.isfinite(curve)) and curve[-100:].mean() < 0.25 * curve[:20].mean()
+    test_res = _labels(api, test)
+    shapes = [(n, k, r["ranks"]) for (n, k, G), r in zip(test, test_res)]
+    feats = np.stack([predict.features(G, n) for n, k, G in test])
+    truth = [(r["g_final"], r["d"]) for r in test_res]
+    p_mlp = predict.Predictor(mlp).predict(feats, shapes)
+    p_gv = predict.Predictor(None).predict(feats, shapes)
+    e_mlp = predict.errors(p_mlp, truth)
+    e_gv = predict.errors(p_gv, truth)
+    print("predictor errors", e_mlp, e_gv)
+    assert e_mlp["d_mae"] < e_gv["d_mae"]
+    assert e_mlp["wstar_acc"] >= e_gv["wstar_acc"]
+    # the hints only size the first wave / round: results are unchanged
+    for (n, k, G), (w, _), want in list(zip(test, p_mlp, test_res))[:60]:
+        with api.Code(G, n, wstar_hint=w) as c:
+            got = c.min_distance()
+        assert got["d"] == want["d"] and got["key"] == want["key"]
+        assert np.array_equal(got["counts"], want["counts"])
+    with api.Batch() as b:
+        for (n, k, G), (w, _) in zip(test, p_mlp):
+            b.add(G, n, wstar_hint=w)
+        b.run()
+        for i, want in enumerate(test_res):
+            got = b.result(i)
+            assert got["key"] == want["key"] and np.array_equal(got["counts"], want["counts"])
