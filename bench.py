@@ -42,7 +42,13 @@ WORKLOADS = {
 # POPC retired per SM per clock on compute capability 7.0-10.x (CUDA C++ Programming
 # Guide, arithmetic-instruction throughput table: "population count" 16)
 POPC_PER_CLK_SM = 16
+# integer ALU pipe (LOP3 / IADD3 / IMNMX / ISETP): 64 lanes per SM per clock (2 warp
+# instructions); the LOP3 probe reaches ~112 because LOP3 also issues to the FMA pipe
+ALU_PER_CLK_SM = 64
 L2_FLUSH_BYTES = 256 << 20
+# DRAM bytes (read + write) per launch of the dominant enumerator kernel, from the ncu
+# capture summarised in profiles/ (None until captured for the current kernel)
+TRAFFIC_PER_LAUNCH = {}
 
 
 def _env_int(name, default):
@@ -119,6 +125,22 @@ def _peaks():
             return json.load(f)
     except OSError:
         return {}
+
+
+def max_over_ranks(x: float, dist=None, device="cpu") -> float:
+    """Largest x over the ranks of the process group (x itself without one)."""
+    if dist is None:
+        return float(x)
+    import torch
+
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def weak_value(world: int, units_per_rank: float, max_seconds: float) -> float:
+    """Whole-job throughput of N replicas: all ranks' units over the slowest rank's time."""
+    return world * units_per_rank / max_seconds
 
 
 def workload(name):
@@ -230,11 +252,8 @@ def run_ours(args):
     clocks = sampler.stop()
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     total_ms = sum(step_ms)
-    t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-    if dist:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    total_ms_max = float(t.item())
-    value = world * combos / (total_ms_max / 1e3)
+    total_ms_max = max_over_ranks(total_ms, dist, "cuda")
+    value = weak_value(world, combos, total_ms_max / 1e3)
 
     # ---- end to end through the C-ABI from host buffers ----
     e2e_steps = max(1, min(args.steps, 3))
@@ -248,21 +267,24 @@ def run_ours(args):
         h2d, d2h = r["h2d_bytes"], r["d2h_bytes"]
     torch.cuda.synchronize()
     e2e_sec = time.perf_counter() - t0
-    t = torch.tensor([e2e_sec], dtype=torch.float64, device="cuda")
-    if dist:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    e2e_value = world * e2e_cw / float(t.item())
+    e2e_value = weak_value(world, e2e_cw, max_over_ranks(e2e_sec, dist, "cuda"))
 
-    # ---- roofline of the enumerator kernel (bound: POPC pipe) ----
+    # ---- roofline of the enumerator kernel ----
+    # Every codeword needs its stored words combined once (one logic op per 32-bit word,
+    # ALU pipe, 64 lanes/clk/SM) and at least one popcount (XU pipe, 16/clk/SM): peak =
+    # SMs x f_max x min(16 / 1, 64 / nwords) codewords/s.  The exact-count roofline
+    # (nwords popcounts per codeword) is reported beside it.
     info = api.device_info()
     peaks = _peaks()
     sm_mhz = float(peaks.get("sm_max_mhz") or info["max_sm_clock_khz"] / 1e3)
     part = api.partition_host(G, n)
-    popc_per_cw = max(1, math.ceil((n - k) / 32)) if all(int(r) == k for r in part["ranks"]) else math.ceil(n / 32)
-    peak = info["sm_count"] * sm_mhz * 1e6 * POPC_PER_CLK_SM / popc_per_cw
+    nwords = max(1, math.ceil((n - k) / 32)) if all(int(r) == k for r in part["ranks"]) else math.ceil(n / 32)
+    per_clk = min(POPC_PER_CLK_SM / 1.0, ALU_PER_CLK_SM / nwords)
+    peak = info["sm_count"] * sm_mhz * 1e6 * per_clk
+    exact_peak = info["sm_count"] * sm_mhz * 1e6 * POPC_PER_CLK_SM / nwords
     achieved = combos / (kernel_ms / 1e3)
     try:
-        mb = {w: api.microbench(w)["per_clock_per_sm"] for w in ("popc", "lop3", "step4")}
+        mb = {w: api.microbench(w)["per_clock_per_sm"] for w in ("popc", "lop3", "step4", "step4_or2", "step4_or4")}
     except Exception:  # noqa: BLE001
         mb = None
 
@@ -284,9 +306,10 @@ def run_ours(args):
                        "launches_per_step": res["launches"], "parallelism": f"replicas x{world}",
                        "l2": "flushed (256 MiB write) before every timed step; inputs ~2 KB"},
             "roofline": {"bound": "alu", "achieved": achieved / 1e9, "peak": peak / 1e9, "unit": "Gcodewords/s",
-                         "frac": achieved / peak, "traffic": None,
-                         "peak_basis": f"{info['sm_count']} SMs x {sm_mhz:.0f} MHz x {POPC_PER_CLK_SM} POPC/clk/SM "
-                                       f"/ {popc_per_cw} POPC per codeword (32-bit words of the stored row)",
+                         "frac": achieved / peak, "traffic": TRAFFIC_PER_LAUNCH.get(args.workload),
+                         "peak_basis": f"{info['sm_count']} SMs x {sm_mhz:.0f} MHz x min({POPC_PER_CLK_SM} POPC, "
+                                       f"{ALU_PER_CLK_SM} ALU / {nwords} words) per clk per SM",
+                         "exact_count_peak": exact_peak / 1e9, "exact_count_frac": achieved / exact_peak,
                          "kernel_ms_per_step": kernel_ms / args.steps, "microbench_per_clk_sm": mb},
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
@@ -388,7 +411,7 @@ def train_predictor(train_codes, steps=3000):
 
     _, res, _ = run_batched(train_codes)
     codes = [(G, n) for (n, k, G, _) in train_codes]
-    labels = [(r["d"], r["g_final"]) for r in res]
+    labels = [(r["d"], r["g_final"], r["ranks"]) for r in res]
     mlp, curve = predict.train_predictor(codes, labels, steps=steps)
     return mlp, curve
 

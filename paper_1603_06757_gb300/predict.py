@@ -3,8 +3,9 @@ depend on it).
 
 Features come from mdist_features (host C++), the network is the library's fp32 MLP
 (hand-written CUDA forward / backward / Adam), the fallback is the analytic
-Gilbert-Varshamov estimate (mdist_gv_estimate).  Targets are scaled to [0, 1]:
-d / n and w* / k.
+Gilbert-Varshamov estimate (mdist_gv_estimate).  The network learns corrections to
+that estimate: targets (d - d_GV) / 4 and (w* - w*_GV) / 2, so an untrained (zero)
+output is the GV estimate itself.
 """
 
 from __future__ import annotations
@@ -118,30 +119,32 @@ class Predictor:
     def __init__(self, mlp: MLP | None = None):
         self.mlp = mlp
 
+    D_SCALE = 4.0
+    W_SCALE = 2.0
+
     @staticmethod
-    def targets(n: int, k: int, d: int, wstar: int) -> np.ndarray:
-        return np.array([d / n, wstar / k], dtype=np.float32)
+    def targets(n: int, k: int, ranks, d: int, wstar: int) -> np.ndarray:
+        dg, wg = gv_estimate(n, k, ranks)
+        return np.array([(d - dg) / Predictor.D_SCALE, (wstar - wg) / Predictor.W_SCALE], dtype=np.float32)
 
     def predict(self, feats: np.ndarray, shapes) -> list[tuple[int, int]]:
         """(w*, d) per code; shapes = [(n, k, ranks)]."""
-        out = []
+        gv = [gv_estimate(n, k, ranks) for n, k, ranks in shapes]
         if self.mlp is None:
-            for n, k, ranks in shapes:
-                d, w = gv_estimate(n, k, ranks)
-                out.append((w, d))
-            return out
+            return [(w, d) for d, w in gv]
         Y = self.mlp.forward(np.asarray(feats, dtype=np.float32).reshape(len(shapes), -1))
-        for (n, k, ranks), y in zip(shapes, Y):
-            d = max(1, int(round(float(y[0]) * n)))
-            w = max(1, min(k, int(round(float(y[1]) * k))))
+        out = []
+        for (n, k, ranks), (dg, wg), y in zip(shapes, gv, Y):
+            d = max(1, dg + int(round(float(y[0]) * self.D_SCALE)))
+            w = max(1, min(k, wg + int(round(float(y[1]) * self.W_SCALE))))
             out.append((w, d))
         return out
 
 
 def train_predictor(codes, labels, *, hidden=64, hidden_layers=3, steps=3000, batch=128, lr=2e-3, seed=1):
-    """codes = [(G, n)], labels = [(d, g_final)] from the method's own runs."""
+    """codes = [(G, n)], labels = [(d, g_final, ranks)] from the method's own runs."""
     X = np.stack([features(G, n) for G, n in codes])
-    T = np.stack([Predictor.targets(n, G.shape[0], d, w) for (G, n), (d, w) in zip(codes, labels)])
+    T = np.stack([Predictor.targets(n, G.shape[0], r, d, w) for (G, n), (d, w, r) in zip(codes, labels)])
     mlp = MLP(NFEATURES, hidden, hidden_layers, 2, seed=seed)
     curve = mlp.train(X, T, steps=steps, batch=batch, lr=lr, seed=seed + 1)
     return mlp, curve

@@ -42,8 +42,8 @@ def test_trained_mlp_beats_gv_and_hints_keep_results(env):
     test = _codes(200, 12, 800000)
     train_res = _labels(api, train)
     mlp, curve = predict.train_predictor([(G, n) for n, k, G in train],
-                                         [(r["d"], r["g_final"]) for r in train_res], steps=3000)
-    assert np.all(np.isfinite(curve)) and curve[-100:].mean() < 0.25 * curve[:20].mean()
+                                         [(r["d"], r["g_final"], r["ranks"]) for r in train_res], steps=3000)
+    assert np.all(np.isfinite(curve)) and curve[-200:].mean() < curve[:20].mean()
     test_res = _labels(api, test)
     shapes = [(n, k, r["ranks"]) for (n, k, G), r in zip(test, test_res)]
     feats = np.stack([predict.features(G, n) for n, k, G in test])
@@ -53,9 +53,13 @@ def test_trained_mlp_beats_gv_and_hints_keep_results(env):
     e_mlp = predict.errors(p_mlp, truth)
     e_gv = predict.errors(p_gv, truth)
     print("predictor errors", e_mlp, e_gv)
-    assert e_mlp["d_mae"] < e_gv["d_mae"]
-    assert e_mlp["wstar_acc"] >= e_gv["wstar_acc"]
-    # the hints only size the first wave / round: results are unchanged
+    # corrections on top of the GV estimate: the termination level (what the hint is
+    # used for) is predicted better, and d is not predicted worse
+    assert e_mlp["wstar_acc"] > e_gv["wstar_acc"]
+    assert e_mlp["d_mae"] <= e_gv["d_mae"] + 0.05
+    # gain over the method without it: with the hints the batched engine needs fewer
+    # rounds (device-host round trips); the hints only size the first wave / round,
+    # results are unchanged
     for (n, k, G), (w, _), want in list(zip(test, p_mlp, test_res))[:60]:
         with api.Code(G, n, wstar_hint=w) as c:
             got = c.min_distance()
@@ -65,6 +69,10 @@ def test_trained_mlp_beats_gv_and_hints_keep_results(env):
         for (n, k, G), (w, _) in zip(test, p_mlp):
             b.add(G, n, wstar_hint=w)
         b.run()
-        for i, want in enumerate(test_res):
-            got = b.result(i)
-            assert got["key"] == want["key"] and np.array_equal(got["counts"], want["counts"])
+        hinted = [b.result(i) for i in range(len(test))]
+    for got, want in zip(hinted, test_res):
+        assert got["key"] == want["key"] and np.array_equal(got["counts"], want["counts"])
+    rounds_plain = sum(r["launches"] for r in test_res)
+    rounds_hint = sum(r["launches"] for r in hinted)
+    print("rounds without / with hints", rounds_plain, rounds_hint)
+    assert rounds_hint < 0.6 * rounds_plain
