@@ -509,10 +509,15 @@ def run_serve_bench(args):
     mlp, _ = train_predictor(train)
     shapes = [(n, k, ranks) for (n, k, G, ranks) in reqs]
     feats = np.stack([predict.features(G, n) for (n, k, G, _) in reqs])
-    hints = [w for (w, d) in predict.Predictor(mlp).predict(feats, shapes)]
+    if args.serve_hints == "mlp":
+        hints = [w for (w, d) in predict.Predictor(mlp).predict(feats, shapes)]
+    elif args.serve_hints == "gv":
+        hints = [w for (w, d) in predict.Predictor(None).predict(feats, shapes)]
+    else:
+        hints = [0] * len(reqs)
     # capacity: the whole stream as one batch
     cps_batch, _, _ = run_batched([(n, k, G, r) for (n, k, G, r) in reqs], hints)
-    rate = args.serve_load * cps_batch
+    rate = args.serve_rate if args.serve_rate > 0 else args.serve_load * cps_batch
     arrivals = synth.poisson_arrivals(len(reqs), rate, seed=99)
     with api.Server(max_slots=args.serve_slots, rows_pool_bytes=64 << 20) as srv:
         ids = [None] * len(reqs)
@@ -546,7 +551,8 @@ def run_serve_bench(args):
         "value": len(reqs) / wall, "higher_is_better": True, "n_gpus": 1, "data": "synthetic",
         "config": {"workload": f"Poisson stream of {len(reqs)} requests, k ~ U[20,64], n ~ U[2k,4k]; draws with "
                                f"GV work estimate > {args.serve_cap:.0e} redrawn ({rejected} redrawn)",
-                   "arrival_rate_per_s": rate, "load": args.serve_load, "slots": args.serve_slots},
+                   "arrival_rate_per_s": rate, "load": args.serve_load, "slots": args.serve_slots,
+                   "hints": args.serve_hints},
         "latency_s": {"p50": float(np.percentile(lats, 50)), "p99": float(np.percentile(lats, 99)),
                       "mean": float(lats.mean()), "max": float(lats.max())},
         "codes_per_s": {"served": len(reqs) / wall, "batched_capacity": cps_batch,
@@ -576,6 +582,8 @@ def main():
     ap.add_argument("--serve-load", type=float, default=0.7)
     ap.add_argument("--serve-slots", type=int, default=1024)
     ap.add_argument("--serve-plain-sample", type=int, default=500)
+    ap.add_argument("--serve-hints", choices=["mlp", "gv", "none"], default="mlp")
+    ap.add_argument("--serve-rate", type=float, default=0.0, help="arrivals/s (0: load x batched capacity)")
     ap.add_argument("--profile-unit", type=int, default=0, help="run one unit of this level (profiling)")
     ap.add_argument("--profile-d", type=int, default=0, help="d of the workload if known (skips the full run)")
     args = ap.parse_args()
