@@ -48,7 +48,7 @@ ALU_PER_CLK_SM = 64
 L2_FLUSH_BYTES = 256 << 20
 # DRAM bytes (read + write) per launch of the dominant enumerator kernel, from the ncu
 # capture summarised in profiles/ (None until captured for the current kernel)
-TRAFFIC_PER_LAUNCH = {}
+TRAFFIC_PER_LAUNCH = {"192x64": 555264}  # enum_unit_kernel<4,5,0>, level 11 (profiles/enum_unit_192x64_g11_v5.md)
 
 
 def _env_int(name, default):

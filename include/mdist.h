@@ -324,6 +324,12 @@ int mdist_microbench(int which, int iters, double *ops_per_clock_per_sm, double 
 int mdist_enumerate_unit_noalloc(const uint32_t *rows, int k, int nwords, int n_bits, int full_rank, int g, int U,
                                  int want_hist, unsigned long long *out, void *cuda_stream);
 
+/* Tensor-core check: D = A * B^T for A 128 x K and B N x K of E4M3 bytes (row-major,
+ * host), K and N multiples of 32 up to 256, computed by tcgen05 kind::f8f6f4 with f32
+ * accumulation in TMEM on one CTA; D 128 x N f32 (host).  Allocates its device buffers
+ * for the call.  MDIST_ETIMEOUT if the MMA's completion wait ran out. */
+int mdist_tc_probe(const uint8_t *A, const uint8_t *B, int N, int K, float *D);
+
 /* ---- host-only entry points (no CUDA call; usable without a GPU) ---------------- */
 
 /* The information-set partition of mdist_prepare alone (same reading of §2, same

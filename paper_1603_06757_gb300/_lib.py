@@ -145,6 +145,7 @@ SIGNATURES = {
     "mdist_enumerate_unit_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                                     ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                                     ctypes.c_void_p, ctypes.c_void_p]),
+    "mdist_tc_probe": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int, PF]),
     "mdist_partition_host": (ctypes.c_int, [P64, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, PI, PI,
                                             PI32, P64, P64]),
     "mdist_debug_set_rows": (ctypes.c_int, [P64, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, PI, PI, PI,
