@@ -80,7 +80,10 @@ typedef struct {
     int wstar_hint;          /* > 1: predicted termination level; mdist_run then launches
                                 levels 1 .. wstar_hint-1 as one wave (one host
                                 synchronisation).  Sizing only: results never depend on it. */
-    int reserved1;
+    int tensor_cores;        /* product blocks on the tensor cores (tcgen05 Gram-matrix
+                                enumerator, stored rows of at most 7 words): 0 = blocks
+                                whose two sides hold >= 128 subsets each, 1 = none, 2 =
+                                every block.  Results are identical. */
 } mdist_options;
 
 /* Witness key: the least (weight, g, j, rank) over the enumerated units (a total

@@ -42,7 +42,7 @@ class Options(ctypes.Structure):
         ("dev_free", FREE_FN),
         ("alloc_ctx", ctypes.c_void_p),
         ("wstar_hint", ctypes.c_int),
-        ("reserved1", ctypes.c_int),
+        ("tensor_cores", ctypes.c_int),
     ]
 
 

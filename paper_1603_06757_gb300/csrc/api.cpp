@@ -111,7 +111,7 @@ int run_unit(mdist_code *c, int g, int j, int U_thr, bool hist_mode, bool *found
     p.n_bits = dr.n_bits;
     p.base = dr.full_rank ? g : 0;
     c->h_slot->U = (unsigned)(U_thr < 0 ? 0 : U_thr);
-    c->h_slot->pad0 = 0;
+    c->h_slot->status = 0;
     c->h_slot->key = mdist::kNoKey;
     c->h_slot->count = 0;
     c->h_slot->tile_next = 0;
@@ -127,8 +127,8 @@ int run_unit(mdist_code *c, int g, int j, int U_thr, bool hist_mode, bool *found
         if (!mdist::filter_group_valid(group, dr.nwords)) group = 0;
     }
     c->st.last_group = group;
-    if (mdist::launch_enum_unit(p, dr.nwords, group, hist_mode, c->sm_count, c->opt.blocks_per_sm, c->stream) !=
-        cudaSuccess)
+    if (mdist::launch_unit_split(p, dr.nwords, group, hist_mode, c->sm_count, c->opt.blocks_per_sm,
+                                 c->opt.tensor_cores, c->stream) != cudaSuccess)
         return MDIST_ECUDA;
     if (cudaEventRecord(c->ev1, c->stream) != cudaSuccess) return MDIST_ECUDA;
     if (cudaMemcpyAsync(c->h_slot, c->d_slot, sizeof(UnitSlot), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess)
@@ -138,6 +138,7 @@ int run_unit(mdist_code *c, int g, int j, int U_thr, bool hist_mode, bool *found
     float ms = 0.f;
     if (cudaEventElapsedTime(&ms, c->ev0, c->ev1) == cudaSuccess) c->st.kernel_ms += ms;
     c->st.launches += 1;
+    if (c->h_slot->status) return MDIST_ETIMEOUT;
     const unsigned long long key = c->h_slot->key;
     *found = key != mdist::kNoKey;
     *w_out = *found ? (int)(key >> mdist::kKeyRankBits) : INT_MAX;
@@ -212,7 +213,10 @@ int mdist_prepare(const uint64_t *G, int n, int k, int words_per_row, const mdis
     mdist_code *c = new (std::nothrow) mdist_code();
     if (!c) return MDIST_ENOMEM;
     if (opts) c->opt = *opts;
-    if (c->opt.filter_group < 0 || c->opt.filter_group > 5) { delete c; return MDIST_EINVAL; }
+    if (c->opt.filter_group < 0 || c->opt.filter_group > 5 || c->opt.tensor_cores < 0 || c->opt.tensor_cores > 2) {
+        delete c;
+        return MDIST_EINVAL;
+    }
     if (c->opt.max_sets <= 0 || c->opt.max_sets > MDIST_MAX_SETS) c->opt.max_sets = MDIST_MAX_SETS;
     c->n = n;
     c->k = k;
@@ -358,14 +362,14 @@ static int run_wave(mdist_code *c, int g_hi, int max_units, int *units_done) {
     const int U_thr = s.have_key ? s.key.weight - 1 : s.U;
     for (int u = 0; u < n_units; ++u) {
         c->h_wave[u].U = 0;
-        c->h_wave[u].pad0 = 0;
+        c->h_wave[u].status = 0;
         c->h_wave[u].key = mdist::kNoKey;
         c->h_wave[u].count = 0;
         c->h_wave[u].tile_next = 0;
     }
     UnitSlot &thr_word = c->h_wave[c->wave_cap];
     thr_word.U = (unsigned)(U_thr < 0 ? 0 : U_thr);
-    thr_word.pad0 = 0;
+    thr_word.status = 0;
     thr_word.key = thr_word.count = thr_word.tile_next = 0;
     unsigned int *d_U = &c->d_wave[c->wave_cap].U;
     if (cudaMemcpyAsync(c->d_wave, c->h_wave, sizeof(UnitSlot) * (size_t)n_units, cudaMemcpyHostToDevice, c->stream) !=
@@ -390,8 +394,8 @@ static int run_wave(mdist_code *c, int g_hi, int max_units, int *units_done) {
         const int fg = c->opt.filter_group;
         int group = fg == 0 ? mdist::choose_filter_group(dr.nwords, dr.n_bits, U_thr - q.base) : (fg == 1 ? 0 : fg);
         if (!mdist::filter_group_valid(group, dr.nwords)) group = 0;
-        if (mdist::launch_enum_unit(q, dr.nwords, group, false, c->sm_count, c->opt.blocks_per_sm, c->stream) !=
-            cudaSuccess)
+        if (mdist::launch_unit_split(q, dr.nwords, group, false, c->sm_count, c->opt.blocks_per_sm,
+                                     c->opt.tensor_cores, c->stream) != cudaSuccess)
             return MDIST_ECUDA;
     }
     if (cudaEventRecord(c->ev1, c->stream) != cudaSuccess) return MDIST_ECUDA;
@@ -403,6 +407,8 @@ static int run_wave(mdist_code *c, int g_hi, int max_units, int *units_done) {
     float ms = 0.f;
     if (cudaEventElapsedTime(&ms, c->ev0, c->ev1) == cudaSuccess) s.kernel_ms += ms;
     s.launches += n_units;
+    for (int u = 0; u < n_units; ++u)
+        if (c->h_wave[u].status) return MDIST_ETIMEOUT;
     // fold in (g, j) order
     for (int u = 0; u < n_units && !s.finished; ++u) {
         const int g = list[(size_t)u].g, j = list[(size_t)u].j;

@@ -146,6 +146,45 @@ size_t enum_smem_bytes(int k, int nwords) {
            ((size_t)k * nwords + 33 * 33 + (size_t)kWarpsPerCta * walk_len_for(nwords) * walk_stride(nwords));
 }
 
+// One unit: its large product blocks on the tensor cores (tc_mode 0: blocks whose
+// sides both hold >= kGramMinSide entries; 2: every block; 1: none), the others on the
+// ALU kernel.  Both launches share the threshold word, key, count and status of `p`.
+cudaError_t launch_unit_split(const EnumParams &p, int nwords, int group, bool hist_mode, int sm_count,
+                              int blocks_per_sm, int tc_mode, cudaStream_t stream) {
+    bool tc[kMaxBlocks] = {};
+    int ntc = 0;
+    if (!hist_mode && tc_mode != 1 && gram_eligible(nwords)) {
+        for (int b = 0; b < p.nblocks; ++b) {
+            const ProductBlock &B = p.blocks[b];
+            const unsigned long long small = B.lane_n < B.walk_n ? B.lane_n : B.walk_n;
+            if (tc_mode == 2 || small >= (unsigned long long)kGramMinSide) {
+                tc[b] = true;
+                ++ntc;
+            }
+        }
+    }
+    if (ntc) {
+        const cudaError_t e =
+            launch_gram_unit(p, tc, p.U, p.slot, reinterpret_cast<int *>(&p.slot->status), sm_count, stream);
+        if (e != cudaSuccess) return e;
+    }
+    if (ntc == p.nblocks) return cudaSuccess;
+    EnumParams q = p;
+    const unsigned long long lane_chunk = 32ull * (unsigned long long)lane_entries_per_thread(nwords);
+    int nb = 0;
+    unsigned long long tiles = 0;
+    for (int b = 0; b < p.nblocks; ++b) {
+        if (tc[b]) continue;
+        ProductBlock B = p.blocks[b];
+        B.tile_begin = tiles;
+        tiles += ((B.lane_n + lane_chunk - 1) / lane_chunk) * B.walk_chunks;
+        q.blocks[nb++] = B;
+    }
+    q.nblocks = nb;
+    q.total_tiles = tiles;
+    return launch_enum_unit(q, nwords, group, hist_mode, sm_count, blocks_per_sm, stream);
+}
+
 cudaError_t launch_enum_unit(const EnumParams &p, int nwords, int group, bool hist_mode, int sm_count,
                              int blocks_per_sm, cudaStream_t stream) {
     switch (nwords) {

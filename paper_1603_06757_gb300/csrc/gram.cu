@@ -1,0 +1,429 @@
+// gram.cu -- the level enumerator on the tensor cores (tcgen05) for the large product
+// blocks of a unit.
+//
+// Within a product block every codeword is x ^ y with x from one side (an i-subset sum
+// of one half of the rows) and y from the other, and
+//     wt(x ^ y) = wt(x) + wt(y) - 2 <x, y>,
+// so the weights of a whole 128 x 256 tile of codewords form a Gram matrix: a dense
+// contraction over the n_bits columns.  Operand rows are bit-expanded to E4M3 bytes
+// (x: 1.0 per set bit; y: -2.0 per set bit) and carry six extra columns after the bits
+// that add wt(x) and wt(y) - thr - 1 as base-8 digits (every value exact in E4M3), so
+// one kind::f8f6f4 MMA chain with f32 accumulation gives, exactly,
+//     acc = wt(x ^ y) - thr - 1      (thr = largest reduced weight still a candidate),
+// and a codeword is a candidate iff acc < 0: the epilogue ORs the sign bits of the
+// accumulators it reads from TMEM and only a set sign bit sends a lane to the side path,
+// which recomputes the weight from the bit-packed rows before touching the key.
+//
+// Persistent grid, one CTA per SM, 288 threads in three roles:
+//   warps 0-3  epilogue  (TMEM lanes 32w..32w+31 = rows of the accumulator tile),
+//   warps 4-7  builders  (operand rows: unrank the subset, XOR its rows, expand),
+//   warp  8    MMA issue (one lane) and TMEM allocation.
+// A work unit is (product block, 128-row A tile, up to kTilesPerUnit 256-row B tiles);
+// every role walks the same static sequence of work units (CTA c takes c, c + grid,
+// ...).  Operand B has two shared-memory stages, the accumulator two TMEM buffers
+// (2 x 256 columns); all hand-offs are mbarriers, every wait is bounded and a timeout
+// sets the status word and ends the kernel after its MMAs have drained.
+#include <cstdint>
+
+#include "combinatorics.cuh"
+#include "enum_core.cuh"
+#include "internal.h"
+#include "tc_common.cuh"
+
+namespace mdist {
+
+static __constant__ BinomTable64 c_binom_g = make_binom_table64();
+
+struct DevBinomG {
+    __device__ __forceinline__ unsigned long long operator()(int a, int b) const { return c_binom_g.v[a][b]; }
+};
+
+namespace {
+
+constexpr int kGM = 128;               // accumulator rows (A tile)
+constexpr int kGN = 256;               // accumulator columns (B tile)
+constexpr int kTilesPerUnit = 16;      // B tiles per work unit
+constexpr int kGramThreads = 288;
+constexpr uint8_t kE4M3One = 0x38;     // 1.0
+constexpr uint8_t kE4M3MinusTwo = 0xC0;  // -2.0
+
+__host__ __device__ constexpr int gram_ka(int nw) { return 32 * nw + 32; }  // bytes per operand row
+
+// E4M3 code of an integer 0..15 (exact)
+__device__ __forceinline__ uint32_t e4m3_small(uint32_t v) {
+    if (v == 0) return 0;
+    const int e = 31 - __clz(v);                 // 2^e <= v < 2^(e+1)
+    const uint32_t mant = ((v << 3) >> e) & 7u;  // 3 fraction bits (exact for v < 16)
+    return ((uint32_t)(e + 7) << 3) | mant;
+}
+
+// base-8 digits of |v| (v in [-1023, 1023]) as E4M3 bytes with the sign of v:
+// |v| = 64 d0 + 8 d1 + d2, d0 <= 15
+__device__ __forceinline__ uint32_t digits3(int v) {
+    const uint32_t s = v < 0 ? 0x80u : 0u;
+    const uint32_t a = (uint32_t)(v < 0 ? -v : v);
+    const uint32_t d0 = a >> 6, d1 = (a >> 3) & 7u, d2 = a & 7u;
+    auto enc = [&](uint32_t d) { return d ? (e4m3_small(d) | s) : 0u; };
+    return enc(d0) | (enc(d1) << 8) | (enc(d2) << 16);
+}
+
+// bytes 64, 8, 1 (E4M3) in the low three bytes
+constexpr uint32_t kScale3 = 0x68u | (0x50u << 8) | (0x38u << 16);
+
+struct GramBlock {
+    unsigned int a_half;         // half of the rows the A side's subsets come from
+    unsigned int a_t, b_t;       // subset sizes
+    unsigned int pad;
+    unsigned long long a_n, b_n; // entries per side
+    unsigned long long a_tiles, b_units, b_tiles;
+    unsigned long long wu_begin;
+};
+
+struct GramParams {
+    const uint32_t *rows;        // k x nwords
+    unsigned int *U;
+    UnitSlot *slot;
+    int *status;
+    int k, k1, k2, g, nwords, n_bits, base;
+    int nblocks;
+    unsigned long long total_wu;
+    long long max_wait;
+    GramBlock blocks[kMaxBlocks];
+};
+
+__device__ __forceinline__ void decode_wu(const GramParams &P, unsigned long long wu, int &b,
+                                          unsigned long long &a_tile, unsigned long long &bt0,
+                                          unsigned long long &bt1) {
+    b = 0;
+    while (b + 1 < P.nblocks && wu >= P.blocks[b + 1].wu_begin) ++b;
+    const GramBlock &B = P.blocks[b];
+    const unsigned long long w = wu - B.wu_begin;
+    a_tile = w / B.b_units;
+    const unsigned long long bu = w - a_tile * B.b_units;
+    bt0 = bu * kTilesPerUnit;
+    bt1 = bt0 + kTilesPerUnit < B.b_tiles ? bt0 + kTilesPerUnit : B.b_tiles;
+}
+
+// Bit-expanded operand row r of a tile (K-major, no-swizzle layout): the NW words of
+// the subset sum, 1.0 / -2.0 per set bit, then the six augmented columns, then zeros.
+template <int NW>
+__device__ __forceinline__ void write_row(uint8_t *tile, int r, const uint32_t (&x)[NW], uint32_t one,
+                                          uint32_t aug_lo, uint32_t aug_hi) {
+    constexpr int KA = gram_ka(NW);
+#pragma unroll
+    for (int w = 0; w < NW; ++w) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {  // 16 bits -> 16 bytes
+            uint32_t q[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const uint32_t nib = (x[w] >> (16 * h + 4 * j)) & 0xFu;
+                q[j] = ((nib * 0x00204081u) & 0x01010101u) * one;
+            }
+            *reinterpret_cast<uint4 *>(tile + kmajor_offset((uint32_t)r, (uint32_t)(32 * w + 16 * h), KA)) =
+                make_uint4(q[0], q[1], q[2], q[3]);
+        }
+    }
+    // columns 32NW .. 32NW+15: three digit bytes, three scale bytes, zeros
+    *reinterpret_cast<uint4 *>(tile + kmajor_offset((uint32_t)r, (uint32_t)(32 * NW), KA)) =
+        make_uint4(aug_lo | ((aug_hi & 0xFFu) << 24), aug_hi >> 8, 0u, 0u);
+    *reinterpret_cast<uint4 *>(tile + kmajor_offset((uint32_t)r, (uint32_t)(32 * NW + 16), KA)) =
+        make_uint4(0u, 0u, 0u, 0u);
+}
+
+template <int NW>
+__device__ __forceinline__ void subset_sum(const uint32_t *rows, const uint32_t *bn, int kh, int t, uint32_t rank,
+                                           uint32_t (&x)[NW], uint32_t &mask) {
+    mask = unrank_colex(bn, kh, t, rank);
+#pragma unroll
+    for (int w = 0; w < NW; ++w) x[w] = 0;
+    xor_rows<NW>(x, rows, mask);
+}
+
+template <int NW>
+__global__ void __launch_bounds__(kGramThreads, 1) gram_kernel(const __grid_constant__ GramParams P) {
+    constexpr int KA = gram_ka(NW);
+    constexpr int KSTEPS = KA / 32;
+    constexpr int A_BYTES = kGM * KA, B_BYTES = kGN * KA;
+    extern __shared__ __align__(1024) uint8_t sm[];
+    uint8_t *sA = sm;
+    uint8_t *sB0 = sm + A_BYTES;
+    // barriers: 0 a_full, 1 a_empty, 2-3 b_full, 4-5 b_empty, 6-7 acc_full, 8-9 acc_empty, 10 drain
+    uint64_t *bars = reinterpret_cast<uint64_t *>(sm + A_BYTES + 2 * B_BYTES);
+    uint32_t *s_tmem = reinterpret_cast<uint32_t *>(bars + 12);
+    volatile int *s_abort = reinterpret_cast<volatile int *>(s_tmem + 1);
+    uint32_t *s_rows = reinterpret_cast<uint32_t *>(bars + 16);
+    uint32_t *s_bn = s_rows + P.k * NW;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    auto bar = [&](int i) { return smem_addr(bars + i); };
+
+    for (int i = tid; i < P.k * NW; i += blockDim.x) s_rows[i] = P.rows[i];
+    for (int i = tid; i < kBn * kBn; i += blockDim.x) s_bn[i] = (uint32_t)c_binom_g.v[i / kBn][i % kBn];
+    if (warp == 8) tmem_alloc(smem_addr(s_tmem), 512);
+    if (tid == 0) {
+        mbar_init(bar(0), 128);
+        mbar_init(bar(1), 1);
+        mbar_init(bar(2), 128);
+        mbar_init(bar(3), 128);
+        mbar_init(bar(4), 1);
+        mbar_init(bar(5), 1);
+        mbar_init(bar(6), 1);
+        mbar_init(bar(7), 1);
+        mbar_init(bar(8), 128);
+        mbar_init(bar(9), 128);
+        mbar_init(bar(10), 1);
+        *s_abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *s_tmem;
+    auto fail = [&]() {
+        *s_abort = 1;
+        atomicExch(P.status, 1);
+    };
+
+    if (warp >= 4 && warp < 8) {
+        // ---------------- builders ----------------
+        const int r = tid - 128;  // A row r; B rows r and r + 128
+        unsigned long long t = 0, u = 0;
+        for (unsigned long long wu = blockIdx.x; wu < P.total_wu && !*s_abort; wu += gridDim.x, ++u) {
+            int b;
+            unsigned long long a_tile, bt0, bt1;
+            decode_wu(P, wu, b, a_tile, bt0, bt1);
+            const GramBlock &B = P.blocks[b];
+            const int a_kh = B.a_half ? P.k2 : P.k1, b_kh = B.a_half ? P.k1 : P.k2;
+            const uint32_t *a_rows = s_rows + (B.a_half ? P.k1 : 0) * NW;
+            const uint32_t *b_rows = s_rows + (B.a_half ? 0 : P.k1) * NW;
+            if (!mbar_wait(bar(1), (uint32_t)((u & 1) ^ 1), P.max_wait)) { fail(); break; }
+            {
+                const unsigned long long e = a_tile * kGM + (unsigned long long)r;
+                uint32_t x[NW], mask;
+                if (e < B.a_n) {
+                    subset_sum<NW>(a_rows, s_bn, a_kh, (int)B.a_t, (uint32_t)e, x, mask);
+                    int wx = 0;
+#pragma unroll
+                    for (int w = 0; w < NW; ++w) wx += __popc(x[w]);
+                    write_row<NW>(sA, r, x, kE4M3One, digits3(wx), kScale3);
+                } else {  // padding row: zero bits, weight 1023 (never a candidate)
+#pragma unroll
+                    for (int w = 0; w < NW; ++w) x[w] = 0;
+                    write_row<NW>(sA, r, x, kE4M3One, digits3(1023), kScale3);
+                }
+            }
+            fence_async_smem();
+            mbar_arrive(bar(0));
+            for (unsigned long long bt = bt0; bt < bt1; ++bt, ++t) {
+                const int s = (int)(t & 1);
+                if (!mbar_wait(bar(4 + s), (uint32_t)(((t >> 1) & 1) ^ 1), P.max_wait)) { fail(); break; }
+                uint8_t *sB = sB0 + s * B_BYTES;
+                const int thr = (int)(*(volatile unsigned int *)P.U) - P.base;
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int rr = r + 128 * h;
+                    const unsigned long long e = bt * kGN + (unsigned long long)rr;
+                    uint32_t y[NW], mask;
+                    int v = 1023;  // padding column: never a candidate
+                    if (e < B.b_n) {
+                        subset_sum<NW>(b_rows, s_bn, b_kh, (int)B.b_t, (uint32_t)e, y, mask);
+                        int wy = 0;
+#pragma unroll
+                        for (int w = 0; w < NW; ++w) wy += __popc(y[w]);
+                        v = wy - thr - 1;
+                        v = v < -1023 ? -1023 : (v > 1023 ? 1023 : v);
+                    } else {
+#pragma unroll
+                        for (int w = 0; w < NW; ++w) y[w] = 0;
+                    }
+                    write_row<NW>(sB, rr, y, kE4M3MinusTwo, kScale3, digits3(v));
+                }
+                fence_async_smem();
+                mbar_arrive(bar(2 + s));
+            }
+        }
+    } else if (warp == 8) {
+        // ---------------- MMA issue ----------------
+        if (lane == 0) {
+            const uint32_t idesc = idesc_f8f6f4_e4m3_f32(kGM, kGN);
+            const uint32_t sbo = (uint32_t)(KA / 16) * 128u;
+            unsigned long long t = 0, u = 0;
+            for (unsigned long long wu = blockIdx.x; wu < P.total_wu && !*s_abort; wu += gridDim.x, ++u) {
+                int b;
+                unsigned long long a_tile, bt0, bt1;
+                decode_wu(P, wu, b, a_tile, bt0, bt1);
+                if (!mbar_wait(bar(0), (uint32_t)(u & 1), P.max_wait)) { fail(); break; }
+                bool ok = true;
+                for (unsigned long long bt = bt0; bt < bt1; ++bt, ++t) {
+                    const int s = (int)(t & 1), ab = (int)(t & 1);
+                    if (!mbar_wait(bar(2 + s), (uint32_t)((t >> 1) & 1), P.max_wait) ||
+                        !mbar_wait(bar(8 + ab), (uint32_t)(((t >> 1) & 1) ^ 1), P.max_wait)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t a0 = smem_addr(sA), b0 = smem_addr(sB0 + s * B_BYTES);
+                    const uint32_t d = tmem + (uint32_t)(ab * kGN);
+#pragma unroll
+                    for (int ks = 0; ks < KSTEPS; ++ks)
+                        mma_f8f6f4(d, smem_desc(a0 + ks * 256, 128, sbo), smem_desc(b0 + ks * 256, 128, sbo), idesc,
+                                   ks > 0 ? 1u : 0u);
+                    mma_commit(bar(4 + s));   // operand stage free again
+                    mma_commit(bar(6 + ab));  // accumulator ready
+                }
+                mma_commit(bar(1));  // A tile free again
+                if (!ok) { fail(); break; }
+            }
+            mma_commit(bar(10));
+            if (!mbar_wait(bar(10), 0, P.max_wait)) fail();  // every MMA has completed
+        }
+    } else {
+        // ---------------- epilogue (warps 0-3) ----------------
+        const int row = tid;  // TMEM lane
+        unsigned long long t = 0, cnt = 0;
+        for (unsigned long long wu = blockIdx.x; wu < P.total_wu && !*s_abort; wu += gridDim.x) {
+            int b;
+            unsigned long long a_tile, bt0, bt1;
+            decode_wu(P, wu, b, a_tile, bt0, bt1);
+            const GramBlock &B = P.blocks[b];
+            const unsigned long long a_e = a_tile * kGM + (unsigned long long)row;
+            const bool a_valid = a_e < B.a_n;
+            const unsigned long long a_valid_rows = B.a_n - a_tile * kGM < (unsigned long long)kGM
+                                                        ? B.a_n - a_tile * kGM
+                                                        : (unsigned long long)kGM;
+            for (unsigned long long bt = bt0; bt < bt1; ++bt, ++t) {
+                const int ab = (int)(t & 1);
+                if (!mbar_wait(bar(6 + ab), (uint32_t)((t >> 1) & 1), P.max_wait)) {
+                    fail();
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t base = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(ab * kGN);
+#pragma unroll 1
+                for (int c = 0; c < kGN / 32; ++c) {
+                    float v[32];
+                    tmem_ld32(base + (uint32_t)(c * 32), v);
+                    uint32_t o = 0;
+#pragma unroll
+                    for (int i = 0; i < 32; ++i) o |= __float_as_uint(v[i]);
+                    if ((o & 0x80000000u) && a_valid) {
+                        // side path: which columns are negative, then the exact weight from
+                        // the bit-packed rows, then the key
+                        uint32_t neg = 0;
+#pragma unroll
+                        for (int i = 0; i < 32; ++i) neg |= (__float_as_uint(v[i]) >> 31) << i;
+                        const int a_kh = B.a_half ? P.k2 : P.k1, b_kh = B.a_half ? P.k1 : P.k2;
+                        const uint32_t *a_rows = s_rows + (B.a_half ? P.k1 : 0) * NW;
+                        const uint32_t *b_rows = s_rows + (B.a_half ? 0 : P.k1) * NW;
+                        uint32_t x[NW], am;
+                        subset_sum<NW>(a_rows, s_bn, a_kh, (int)B.a_t, (uint32_t)a_e, x, am);
+                        while (neg) {
+                            const int i = __ffs(neg) - 1;
+                            neg &= neg - 1;
+                            const unsigned long long b_e = bt * kGN + (unsigned long long)(c * 32 + i);
+                            if (b_e >= B.b_n) continue;
+                            uint32_t y[NW], bm;
+                            subset_sum<NW>(b_rows, s_bn, b_kh, (int)B.b_t, (uint32_t)b_e, y, bm);
+                            int w = 0;
+#pragma unroll
+                            for (int q = 0; q < NW; ++q) w += __popc(x[q] ^ y[q]);
+                            const int weight = w + P.base;
+                            if (weight > (int)(*(volatile unsigned int *)P.U)) continue;
+                            const unsigned long long h1 = B.a_half ? bm : am, h2 = B.a_half ? am : bm;
+                            const unsigned long long rank = lexrank64(h1 | (h2 << P.k1), P.k, P.g, DevBinomG{});
+                            atomicMin(P.U, (unsigned int)weight);
+                            atomicMin(&P.slot->key, ((unsigned long long)weight << kKeyRankBits) | rank);
+                        }
+                    }
+                }
+                tc_fence_before();
+                mbar_arrive(bar(8 + ab));
+                if (row == 0) {
+                    const unsigned long long b_left = B.b_n - bt * kGN;
+                    cnt += a_valid_rows * (b_left < (unsigned long long)kGN ? b_left : (unsigned long long)kGN);
+                }
+            }
+        }
+        if (row == 0 && cnt) atomicAdd(&P.slot->count, cnt);
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 8) tmem_dealloc(tmem, 512);
+}
+
+// at least 120 KB so that two CTAs never share an SM (each allocates all 512 TMEM columns)
+template <int NW>
+size_t gram_smem_bytes(int k) {
+    constexpr int KA = gram_ka(NW);
+    const size_t need = (size_t)kGM * KA + 2 * (size_t)kGN * KA + 16 * sizeof(uint64_t) +
+                        sizeof(uint32_t) * ((size_t)k * NW + kBn * kBn);
+    return need < (size_t)(120 << 10) ? (size_t)(120 << 10) : need;
+}
+
+template <int NW>
+cudaError_t gram_launch_nw(const GramParams &p, int sm_count, cudaStream_t stream) {
+    const size_t smem = gram_smem_bytes<NW>(p.k);
+    cudaError_t e = cudaFuncSetAttribute(gram_kernel<NW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    unsigned long long grid = (unsigned long long)sm_count;
+    if (p.total_wu < grid) grid = p.total_wu;
+    if (grid < 1) return cudaSuccess;
+    gram_kernel<NW><<<(unsigned int)grid, kGramThreads, smem, stream>>>(p);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+// Blocks whose sides both hold at least kGramMinSide entries go to the tensor cores.
+bool gram_eligible(int nwords) { return nwords >= 1 && nwords <= kGramMaxWords; }
+
+cudaError_t launch_gram_unit(const EnumParams &ep, const bool *tc_block, unsigned int *U, UnitSlot *slot,
+                             int *status, int sm_count, cudaStream_t stream) {
+    GramParams p{};
+    p.rows = ep.rows;
+    p.U = U;
+    p.slot = slot;
+    p.status = status;
+    p.k = ep.k;
+    p.k1 = ep.k1;
+    p.k2 = ep.k2;
+    p.g = ep.g;
+    p.nwords = ep.nwords;
+    p.n_bits = ep.n_bits;
+    p.base = ep.base;
+    p.max_wait = 200000000ll;
+    int nb = 0;
+    unsigned long long wu = 0;
+    for (int b = 0; b < ep.nblocks; ++b) {
+        if (!tc_block[b]) continue;
+        const ProductBlock &E = ep.blocks[b];
+        GramBlock &G = p.blocks[nb++];
+        G.a_half = E.lane_half;
+        G.a_t = E.lane_t;
+        G.b_t = E.walk_t;
+        G.pad = 0;
+        G.a_n = E.lane_n;
+        G.b_n = E.walk_n;
+        G.a_tiles = (E.lane_n + kGM - 1) / kGM;
+        G.b_tiles = (E.walk_n + kGN - 1) / kGN;
+        G.b_units = (G.b_tiles + kTilesPerUnit - 1) / kTilesPerUnit;
+        G.wu_begin = wu;
+        wu += G.a_tiles * G.b_units;
+    }
+    p.nblocks = nb;
+    p.total_wu = wu;
+    if (nb == 0) return cudaSuccess;
+    switch (ep.nwords) {
+        case 1: return gram_launch_nw<1>(p, sm_count, stream);
+        case 2: return gram_launch_nw<2>(p, sm_count, stream);
+        case 3: return gram_launch_nw<3>(p, sm_count, stream);
+        case 4: return gram_launch_nw<4>(p, sm_count, stream);
+        case 5: return gram_launch_nw<5>(p, sm_count, stream);
+        case 6: return gram_launch_nw<6>(p, sm_count, stream);
+        case 7: return gram_launch_nw<7>(p, sm_count, stream);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace mdist

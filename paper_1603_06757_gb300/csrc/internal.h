@@ -28,7 +28,7 @@ constexpr uint64_t kNoKey = ~0ull;
 // Device-side result slot of one (g, j) unit.
 struct UnitSlot {
     unsigned int U;              // threshold word for launches that own their slot
-    unsigned int pad0;
+    unsigned int status;         // nonzero: a bounded device wait ran out
     unsigned long long key;      // least (weight << 54 | rank) among candidates, or kNoKey
     unsigned long long count;    // combinations enumerated
     unsigned long long tile_next;// work counter of the persistent grid
@@ -71,6 +71,17 @@ __host__ __device__ constexpr int walk_len_for(int nwords) { return nwords <= 8 
 // Launch one unit's enumerator (enum_launch.cu).  hist == nullptr for the normal path.
 cudaError_t launch_enum_unit(const EnumParams &p, int nwords, int group, bool hist_mode, int sm_count,
                              int blocks_per_sm, cudaStream_t stream);
+
+// Tensor-core (tcgen05) enumerator for the large product blocks of a unit (gram.cu).
+// A block goes there when both of its sides hold at least kGramMinSide entries and the
+// stored rows are at most kGramMaxWords words.  `tc_block[b]` selects blocks of `ep`.
+constexpr int kGramMinSide = 128;
+constexpr int kGramMaxWords = 7;
+bool gram_eligible(int nwords);
+cudaError_t launch_gram_unit(const EnumParams &ep, const bool *tc_block, unsigned int *U, UnitSlot *slot,
+                             int *status, int sm_count, cudaStream_t stream);
+cudaError_t launch_unit_split(const EnumParams &p, int nwords, int group, bool hist_mode, int sm_count,
+                              int blocks_per_sm, int tc_mode, cudaStream_t stream);
 
 // Filter variant for a unit: 0 (exact count for every codeword) or the OR-group size
 // 2, 3, 4 whose expected cost is least for this row width and threshold.

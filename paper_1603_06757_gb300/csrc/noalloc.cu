@@ -42,7 +42,7 @@ __global__ void noalloc_init(unsigned int U, int bins) {
     NoAllocScratch *s = reinterpret_cast<NoAllocScratch *>(g_noalloc_scratch);
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         s->slot.U = U;
-        s->slot.pad0 = 0;
+        s->slot.status = 0;
         s->slot.key = kNoKey;
         s->slot.count = 0;
         s->slot.tile_next = 0;
