@@ -216,7 +216,7 @@ def run_ours(args):
 
     n, k, seed, G = workload(args.workload)
     stream = torch.cuda.current_stream()
-    code = api.Code(G, n)
+    code = api.Code(G, n, tensor_cores=args.tensor_cores)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
 
     def step():
@@ -336,7 +336,7 @@ def run_profile_unit(args):
 
     n, k, seed, G = workload(args.workload)
     g = args.profile_unit
-    with api.Code(G, n) as code:
+    with api.Code(G, n, tensor_cores=args.tensor_cores) as code:
         d = code.min_distance()["d"] if args.profile_d <= 0 else args.profile_d
         out = []
         for _ in range(2):
@@ -346,6 +346,7 @@ def run_profile_unit(args):
             torch.cuda.synchronize()
             out.append(time.perf_counter() - t0)
     print(json.dumps({"workload": args.workload, "g": g, "j": 0, "U": d - 1, "combos": combos[0],
+                      "tensor_cores": args.tensor_cores,
                       "seconds": out, "codewords_per_s": combos[0] / out[-1]}), flush=True)
     return 0
 
@@ -584,6 +585,8 @@ def main():
     ap.add_argument("--serve-plain-sample", type=int, default=500)
     ap.add_argument("--serve-hints", choices=["mlp", "gv", "none"], default="mlp")
     ap.add_argument("--serve-rate", type=float, default=0.0, help="arrivals/s (0: load x batched capacity)")
+    ap.add_argument("--tensor-cores", type=int, choices=[0, 1, 2], default=0,
+                    help="0: large product blocks on the tcgen05 enumerator, 1: ALU enumerator only, 2: all blocks")
     ap.add_argument("--profile-unit", type=int, default=0, help="run one unit of this level (profiling)")
     ap.add_argument("--profile-d", type=int, default=0, help="d of the workload if known (skips the full run)")
     args = ap.parse_args()

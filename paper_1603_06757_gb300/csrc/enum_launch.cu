@@ -146,26 +146,23 @@ size_t enum_smem_bytes(int k, int nwords) {
            ((size_t)k * nwords + 33 * 33 + (size_t)kWarpsPerCta * walk_len_for(nwords) * walk_stride(nwords));
 }
 
-// One unit: its large product blocks on the tensor cores (tc_mode 0: blocks whose
-// sides both hold >= kGramMinSide entries; 2: every block; 1: none), the others on the
-// ALU kernel.  Both launches share the threshold word, key, count and status of `p`.
+// One unit: the product blocks that come with subset-sum tables on the tensor cores,
+// the others on the ALU kernel.  Both launches share the threshold word, key, count and
+// status of `p`.
 cudaError_t launch_unit_split(const EnumParams &p, int nwords, int group, bool hist_mode, int sm_count,
-                              int blocks_per_sm, int tc_mode, cudaStream_t stream) {
+                              int blocks_per_sm, const uint32_t *const *lane_tab, const uint32_t *const *walk_tab,
+                              cudaStream_t stream) {
     bool tc[kMaxBlocks] = {};
     int ntc = 0;
-    if (!hist_mode && tc_mode != 1 && gram_eligible(nwords)) {
-        for (int b = 0; b < p.nblocks; ++b) {
-            const ProductBlock &B = p.blocks[b];
-            const unsigned long long small = B.lane_n < B.walk_n ? B.lane_n : B.walk_n;
-            if (tc_mode == 2 || small >= (unsigned long long)kGramMinSide) {
+    if (!hist_mode && lane_tab && walk_tab)
+        for (int b = 0; b < p.nblocks; ++b)
+            if (lane_tab[b] && walk_tab[b]) {
                 tc[b] = true;
                 ++ntc;
             }
-        }
-    }
     if (ntc) {
-        const cudaError_t e =
-            launch_gram_unit(p, tc, p.U, p.slot, reinterpret_cast<int *>(&p.slot->status), sm_count, stream);
+        const cudaError_t e = launch_gram_unit(p, lane_tab, walk_tab, p.U, p.slot,
+                                               reinterpret_cast<int *>(&p.slot->status), sm_count, stream);
         if (e != cudaSuccess) return e;
     }
     if (ntc == p.nblocks) return cudaSuccess;

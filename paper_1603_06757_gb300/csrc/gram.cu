@@ -14,10 +14,11 @@
 // accumulators it reads from TMEM and only a set sign bit sends a lane to the side path,
 // which recomputes the weight from the bit-packed rows before touching the key.
 //
-// Persistent grid, one CTA per SM, 288 threads in three roles:
-//   warps 0-3  epilogue  (TMEM lanes 32w..32w+31 = rows of the accumulator tile),
-//   warps 4-7  builders  (operand rows: unrank the subset, XOR its rows, expand),
-//   warp  8    MMA issue (one lane) and TMEM allocation.
+// Persistent grid, one CTA per SM, 416 threads in three roles:
+//   warps 0-3   epilogue  (TMEM lanes 32w..32w+31 = rows of the accumulator tile),
+//   warps 4-11  builders  (operand rows: load the subset sum from the per-half table of
+//               subset sums, expand it to bytes, add the augmented columns),
+//   warp  12    MMA issue (one lane) and TMEM allocation.
 // A work unit is (product block, 128-row A tile, up to kTilesPerUnit 256-row B tiles);
 // every role walks the same static sequence of work units (CTA c takes c, c + grid,
 // ...).  Operand B has two shared-memory stages, the accumulator two TMEM buffers
@@ -43,7 +44,7 @@ namespace {
 constexpr int kGM = 128;               // accumulator rows (A tile)
 constexpr int kGN = 256;               // accumulator columns (B tile)
 constexpr int kTilesPerUnit = 16;      // B tiles per work unit
-constexpr int kGramThreads = 288;
+constexpr int kGramThreads = 416;  // 4 epilogue warps, 8 builder warps, 1 MMA warp
 constexpr uint8_t kE4M3One = 0x38;     // 1.0
 constexpr uint8_t kE4M3MinusTwo = 0xC0;  // -2.0
 
@@ -77,6 +78,8 @@ struct GramBlock {
     unsigned long long a_n, b_n; // entries per side
     unsigned long long a_tiles, b_units, b_tiles;
     unsigned long long wu_begin;
+    const uint32_t *a_tab;       // a_n x nwords: subset sums of the A side, colex order
+    const uint32_t *b_tab;       // b_n x nwords
 };
 
 struct GramParams {
@@ -159,12 +162,12 @@ __global__ void __launch_bounds__(kGramThreads, 1) gram_kernel(const __grid_cons
 
     for (int i = tid; i < P.k * NW; i += blockDim.x) s_rows[i] = P.rows[i];
     for (int i = tid; i < kBn * kBn; i += blockDim.x) s_bn[i] = (uint32_t)c_binom_g.v[i / kBn][i % kBn];
-    if (warp == 8) tmem_alloc(smem_addr(s_tmem), 512);
+    if (warp == 12) tmem_alloc(smem_addr(s_tmem), 512);
     if (tid == 0) {
-        mbar_init(bar(0), 128);
+        mbar_init(bar(0), 256);
         mbar_init(bar(1), 1);
-        mbar_init(bar(2), 128);
-        mbar_init(bar(3), 128);
+        mbar_init(bar(2), 256);
+        mbar_init(bar(3), 256);
         mbar_init(bar(4), 1);
         mbar_init(bar(5), 1);
         mbar_init(bar(6), 1);
@@ -184,27 +187,26 @@ __global__ void __launch_bounds__(kGramThreads, 1) gram_kernel(const __grid_cons
         atomicExch(P.status, 1);
     };
 
-    if (warp >= 4 && warp < 8) {
+    if (warp >= 4 && warp < 12) {
         // ---------------- builders ----------------
-        const int r = tid - 128;  // A row r; B rows r and r + 128
+        const int r = tid - 128;  // B row r; A row r when r < 128
         unsigned long long t = 0, u = 0;
         for (unsigned long long wu = blockIdx.x; wu < P.total_wu && !*s_abort; wu += gridDim.x, ++u) {
             int b;
             unsigned long long a_tile, bt0, bt1;
             decode_wu(P, wu, b, a_tile, bt0, bt1);
             const GramBlock &B = P.blocks[b];
-            const int a_kh = B.a_half ? P.k2 : P.k1, b_kh = B.a_half ? P.k1 : P.k2;
-            const uint32_t *a_rows = s_rows + (B.a_half ? P.k1 : 0) * NW;
-            const uint32_t *b_rows = s_rows + (B.a_half ? 0 : P.k1) * NW;
             if (!mbar_wait(bar(1), (uint32_t)((u & 1) ^ 1), P.max_wait)) { fail(); break; }
-            {
+            if (r < kGM) {
                 const unsigned long long e = a_tile * kGM + (unsigned long long)r;
-                uint32_t x[NW], mask;
+                uint32_t x[NW];
                 if (e < B.a_n) {
-                    subset_sum<NW>(a_rows, s_bn, a_kh, (int)B.a_t, (uint32_t)e, x, mask);
                     int wx = 0;
 #pragma unroll
-                    for (int w = 0; w < NW; ++w) wx += __popc(x[w]);
+                    for (int w = 0; w < NW; ++w) {
+                        x[w] = B.a_tab[e * NW + w];
+                        wx += __popc(x[w]);
+                    }
                     write_row<NW>(sA, r, x, kE4M3One, digits3(wx), kScale3);
                 } else {  // padding row: zero bits, weight 1023 (never a candidate)
 #pragma unroll
@@ -219,30 +221,28 @@ __global__ void __launch_bounds__(kGramThreads, 1) gram_kernel(const __grid_cons
                 if (!mbar_wait(bar(4 + s), (uint32_t)(((t >> 1) & 1) ^ 1), P.max_wait)) { fail(); break; }
                 uint8_t *sB = sB0 + s * B_BYTES;
                 const int thr = (int)(*(volatile unsigned int *)P.U) - P.base;
+                const unsigned long long e = bt * kGN + (unsigned long long)r;
+                uint32_t y[NW];
+                int v = 1023;  // padding column: never a candidate
+                if (e < B.b_n) {
+                    int wy = 0;
 #pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const int rr = r + 128 * h;
-                    const unsigned long long e = bt * kGN + (unsigned long long)rr;
-                    uint32_t y[NW], mask;
-                    int v = 1023;  // padding column: never a candidate
-                    if (e < B.b_n) {
-                        subset_sum<NW>(b_rows, s_bn, b_kh, (int)B.b_t, (uint32_t)e, y, mask);
-                        int wy = 0;
-#pragma unroll
-                        for (int w = 0; w < NW; ++w) wy += __popc(y[w]);
-                        v = wy - thr - 1;
-                        v = v < -1023 ? -1023 : (v > 1023 ? 1023 : v);
-                    } else {
-#pragma unroll
-                        for (int w = 0; w < NW; ++w) y[w] = 0;
+                    for (int w = 0; w < NW; ++w) {
+                        y[w] = B.b_tab[e * NW + w];
+                        wy += __popc(y[w]);
                     }
-                    write_row<NW>(sB, rr, y, kE4M3MinusTwo, kScale3, digits3(v));
+                    v = wy - thr - 1;
+                    v = v < -1023 ? -1023 : (v > 1023 ? 1023 : v);
+                } else {
+#pragma unroll
+                    for (int w = 0; w < NW; ++w) y[w] = 0;
                 }
+                write_row<NW>(sB, r, y, kE4M3MinusTwo, kScale3, digits3(v));
                 fence_async_smem();
                 mbar_arrive(bar(2 + s));
             }
         }
-    } else if (warp == 8) {
+    } else if (warp == 12) {
         // ---------------- MMA issue ----------------
         if (lane == 0) {
             const uint32_t idesc = idesc_f8f6f4_e4m3_f32(kGM, kGN);
@@ -313,22 +313,21 @@ __global__ void __launch_bounds__(kGramThreads, 1) gram_kernel(const __grid_cons
 #pragma unroll
                         for (int i = 0; i < 32; ++i) neg |= (__float_as_uint(v[i]) >> 31) << i;
                         const int a_kh = B.a_half ? P.k2 : P.k1, b_kh = B.a_half ? P.k1 : P.k2;
-                        const uint32_t *a_rows = s_rows + (B.a_half ? P.k1 : 0) * NW;
-                        const uint32_t *b_rows = s_rows + (B.a_half ? 0 : P.k1) * NW;
-                        uint32_t x[NW], am;
-                        subset_sum<NW>(a_rows, s_bn, a_kh, (int)B.a_t, (uint32_t)a_e, x, am);
+                        uint32_t x[NW];
+#pragma unroll
+                        for (int q = 0; q < NW; ++q) x[q] = B.a_tab[a_e * NW + q];
                         while (neg) {
                             const int i = __ffs(neg) - 1;
                             neg &= neg - 1;
                             const unsigned long long b_e = bt * kGN + (unsigned long long)(c * 32 + i);
                             if (b_e >= B.b_n) continue;
-                            uint32_t y[NW], bm;
-                            subset_sum<NW>(b_rows, s_bn, b_kh, (int)B.b_t, (uint32_t)b_e, y, bm);
                             int w = 0;
 #pragma unroll
-                            for (int q = 0; q < NW; ++q) w += __popc(x[q] ^ y[q]);
+                            for (int q = 0; q < NW; ++q) w += __popc(x[q] ^ B.b_tab[b_e * NW + q]);
                             const int weight = w + P.base;
                             if (weight > (int)(*(volatile unsigned int *)P.U)) continue;
+                            const uint32_t am = unrank_colex(s_bn, a_kh, (int)B.a_t, (uint32_t)a_e);
+                            const uint32_t bm = unrank_colex(s_bn, b_kh, (int)B.b_t, (uint32_t)b_e);
                             const unsigned long long h1 = B.a_half ? bm : am, h2 = B.a_half ? am : bm;
                             const unsigned long long rank = lexrank64(h1 | (h2 << P.k1), P.k, P.g, DevBinomG{});
                             atomicMin(P.U, (unsigned int)weight);
@@ -349,7 +348,7 @@ __global__ void __launch_bounds__(kGramThreads, 1) gram_kernel(const __grid_cons
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    if (warp == 8) tmem_dealloc(tmem, 512);
+    if (warp == 12) tmem_dealloc(tmem, 512);
 }
 
 // at least 120 KB so that two CTAs never share an SM (each allocates all 512 TMEM columns)
@@ -373,13 +372,55 @@ cudaError_t gram_launch_nw(const GramParams &p, int sm_count, cudaStream_t strea
     return cudaGetLastError();
 }
 
+// out[e * NW ..] = sum of the rows of the t-subset of {0..kh-1} with colex rank e
+template <int NW>
+__global__ void subset_table_kernel(const uint32_t *rows, int kh, int t, unsigned long long count, uint32_t *out) {
+    __shared__ uint32_t s_bn[kBn * kBn];
+    __shared__ uint32_t s_rows[32 * NW];
+    for (int i = threadIdx.x; i < kBn * kBn; i += blockDim.x) s_bn[i] = (uint32_t)c_binom_g.v[i / kBn][i % kBn];
+    for (int i = threadIdx.x; i < kh * NW; i += blockDim.x) s_rows[i] = rows[i];
+    __syncthreads();
+    for (unsigned long long e = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; e < count;
+         e += (unsigned long long)gridDim.x * blockDim.x) {
+        uint32_t x[NW], mask;
+        subset_sum<NW>(s_rows, s_bn, kh, t, (uint32_t)e, x, mask);
+#pragma unroll
+        for (int w = 0; w < NW; ++w) out[e * NW + w] = x[w];
+    }
+}
+
+template <int NW>
+cudaError_t table_launch_nw(const uint32_t *rows, int kh, int t, unsigned long long count, uint32_t *out,
+                            int sm_count, cudaStream_t stream) {
+    unsigned long long grid = (count + 255) / 256;
+    const unsigned long long cap = (unsigned long long)sm_count * 8;
+    if (grid > cap) grid = cap;
+    if (grid < 1) grid = 1;
+    subset_table_kernel<NW><<<(unsigned int)grid, 256, 0, stream>>>(rows, kh, t, count, out);
+    return cudaGetLastError();
+}
+
 }  // namespace
+
+cudaError_t launch_subset_table(const uint32_t *rows, int nwords, int kh, int t, unsigned long long count,
+                                uint32_t *out, int sm_count, cudaStream_t stream) {
+    switch (nwords) {
+        case 1: return table_launch_nw<1>(rows, kh, t, count, out, sm_count, stream);
+        case 2: return table_launch_nw<2>(rows, kh, t, count, out, sm_count, stream);
+        case 3: return table_launch_nw<3>(rows, kh, t, count, out, sm_count, stream);
+        case 4: return table_launch_nw<4>(rows, kh, t, count, out, sm_count, stream);
+        case 5: return table_launch_nw<5>(rows, kh, t, count, out, sm_count, stream);
+        case 6: return table_launch_nw<6>(rows, kh, t, count, out, sm_count, stream);
+        case 7: return table_launch_nw<7>(rows, kh, t, count, out, sm_count, stream);
+        default: return cudaErrorInvalidValue;
+    }
+}
 
 // Blocks whose sides both hold at least kGramMinSide entries go to the tensor cores.
 bool gram_eligible(int nwords) { return nwords >= 1 && nwords <= kGramMaxWords; }
 
-cudaError_t launch_gram_unit(const EnumParams &ep, const bool *tc_block, unsigned int *U, UnitSlot *slot,
-                             int *status, int sm_count, cudaStream_t stream) {
+cudaError_t launch_gram_unit(const EnumParams &ep, const uint32_t *const *lane_tab, const uint32_t *const *walk_tab,
+                             unsigned int *U, UnitSlot *slot, int *status, int sm_count, cudaStream_t stream) {
     GramParams p{};
     p.rows = ep.rows;
     p.U = U;
@@ -396,9 +437,11 @@ cudaError_t launch_gram_unit(const EnumParams &ep, const bool *tc_block, unsigne
     int nb = 0;
     unsigned long long wu = 0;
     for (int b = 0; b < ep.nblocks; ++b) {
-        if (!tc_block[b]) continue;
+        if (!lane_tab[b] || !walk_tab[b]) continue;
         const ProductBlock &E = ep.blocks[b];
         GramBlock &G = p.blocks[nb++];
+        G.a_tab = lane_tab[b];
+        G.b_tab = walk_tab[b];
         G.a_half = E.lane_half;
         G.a_t = E.lane_t;
         G.b_t = E.walk_t;

@@ -78,10 +78,17 @@ cudaError_t launch_enum_unit(const EnumParams &p, int nwords, int group, bool hi
 constexpr int kGramMinSide = 128;
 constexpr int kGramMaxWords = 7;
 bool gram_eligible(int nwords);
-cudaError_t launch_gram_unit(const EnumParams &ep, const bool *tc_block, unsigned int *U, UnitSlot *slot,
-                             int *status, int sm_count, cudaStream_t stream);
+// lane_tab[b] / walk_tab[b]: device tables of the subset sums of block b's two sides
+// (colex order, nwords words each), or null for a block left to the ALU kernel.
+cudaError_t launch_gram_unit(const EnumParams &ep, const uint32_t *const *lane_tab, const uint32_t *const *walk_tab,
+                             unsigned int *U, UnitSlot *slot, int *status, int sm_count, cudaStream_t stream);
+// out[e * nwords ..] = sum of the rows of the t-subset of rows[0..kh) with colex rank e
+cudaError_t launch_subset_table(const uint32_t *rows, int nwords, int kh, int t, unsigned long long count,
+                                uint32_t *out, int sm_count, cudaStream_t stream);
+// A unit: blocks with both tables on the tensor cores, the others on the ALU kernel.
 cudaError_t launch_unit_split(const EnumParams &p, int nwords, int group, bool hist_mode, int sm_count,
-                              int blocks_per_sm, int tc_mode, cudaStream_t stream);
+                              int blocks_per_sm, const uint32_t *const *lane_tab, const uint32_t *const *walk_tab,
+                              cudaStream_t stream);
 
 // Filter variant for a unit: 0 (exact count for every codeword) or the OR-group size
 // 2, 3, 4 whose expected cost is least for this row width and threshold.
