@@ -61,7 +61,7 @@ struct mdist_code {
     UnitSlot *d_wave = nullptr;          // [wave_cap] per-unit slots + 1 threshold word after them
     UnitSlot *h_wave = nullptr;          // pinned copy
     // subset-sum tables for the tensor-core enumerator, key (j << 16 | half << 8 | t)
-    std::map<uint32_t, uint32_t *> tabs;
+    std::map<uint32_t, void *> tabs;
     size_t tab_bytes = 0;
     RunState st;
 };
@@ -103,26 +103,40 @@ void reset_state(mdist_code *c) {
 
 // Device bytes a code may hold in subset-sum tables; blocks whose tables would not fit
 // stay on the ALU enumerator.
-constexpr size_t kTableBudget = 8ull << 30;
+constexpr size_t kTableBudget = 16ull << 30;
 
-// Table of the sums of the t-subsets of half `half` of set j's rows (colex order), built
-// on first use and kept for later levels; null when over budget.
-int subset_table(mdist_code *c, int j, int half, int t, unsigned long long count, const uint32_t **out) {
+// Table of the sums of the t-subsets of half `half` of set j's rows (colex order) and,
+// with `expanded`, its expansion to tensor-core operand tiles; built on first use and
+// kept for later levels; null when over budget.
+int subset_table(mdist_code *c, int j, int half, int t, unsigned long long count, bool expanded, const void **out) {
     *out = nullptr;
-    const uint32_t key = ((uint32_t)j << 16) | ((uint32_t)half << 8) | (uint32_t)t;
+    const uint32_t key = ((uint32_t)j << 16) | ((uint32_t)half << 8) | (uint32_t)t | (expanded ? 1u << 31 : 0u);
     auto it = c->tabs.find(key);
     if (it != c->tabs.end()) {
         *out = it->second;
         return MDIST_OK;
     }
     const DeviceRows &dr = c->rows[(size_t)j];
-    const size_t bytes = (size_t)count * (size_t)dr.nwords * sizeof(uint32_t);
+    const void *packed = nullptr;
+    if (expanded) {
+        const int rc = subset_table(c, j, half, t, count, false, &packed);
+        if (rc != MDIST_OK || !packed) return rc;
+    }
+    const size_t bytes = expanded ? mdist::gram_expanded_bytes(dr.nwords, count)
+                                  : (size_t)count * (size_t)dr.nwords * sizeof(uint32_t);
     if (c->tab_bytes + bytes > kTableBudget) return MDIST_OK;
-    uint32_t *d = (uint32_t *)dev_alloc(c, bytes);
+    void *d = dev_alloc(c, bytes);
     if (!d) return MDIST_OK;
-    const int k1 = (c->k + 1) / 2, kh = half ? c->k - k1 : k1;
-    const uint32_t *rows = c->d_rows[(size_t)j] + (half ? (size_t)k1 * (size_t)dr.nwords : 0);
-    if (mdist::launch_subset_table(rows, dr.nwords, kh, t, count, d, c->sm_count, c->stream) != cudaSuccess) {
+    cudaError_t e;
+    if (expanded) {
+        e = mdist::launch_expand_table((const uint32_t *)packed, dr.nwords, count, (uint8_t *)d, c->sm_count,
+                                       c->stream);
+    } else {
+        const int k1 = (c->k + 1) / 2, kh = half ? c->k - k1 : k1;
+        const uint32_t *rows = c->d_rows[(size_t)j] + (half ? (size_t)k1 * (size_t)dr.nwords : 0);
+        e = mdist::launch_subset_table(rows, dr.nwords, kh, t, count, (uint32_t *)d, c->sm_count, c->stream);
+    }
+    if (e != cudaSuccess) {
         dev_release(c, d);
         return MDIST_ECUDA;
     }
@@ -134,21 +148,24 @@ int subset_table(mdist_code *c, int j, int half, int t, unsigned long long count
 
 // Tables of the product blocks of unit p (set j) that go to the tensor cores
 // (tensor_cores 0: blocks whose sides both hold >= kGramMinSide entries; 2: every block;
-// 1: none); lane[b] = walk[b] = null for a block left to the ALU enumerator.
-int gram_tables(mdist_code *c, int j, const EnumParams &p, const uint32_t **lane, const uint32_t **walk) {
-    for (int b = 0; b < mdist::kMaxBlocks; ++b) lane[b] = walk[b] = nullptr;
+// 1: none); all null for a block left to the ALU enumerator.
+int gram_tables(mdist_code *c, int j, const EnumParams &p, mdist::GramTables *tabs) {
+    for (int b = 0; b < mdist::kMaxBlocks; ++b) tabs[b] = mdist::GramTables{};
     if (c->opt.tensor_cores == 1 || !mdist::gram_eligible(p.nwords)) return MDIST_OK;
     for (int b = 0; b < p.nblocks; ++b) {
         const mdist::ProductBlock &B = p.blocks[b];
         const unsigned long long small = B.lane_n < B.walk_n ? B.lane_n : B.walk_n;
         if (c->opt.tensor_cores == 0 && small < (unsigned long long)mdist::kGramMinSide) continue;
-        const uint32_t *a = nullptr, *w = nullptr;
-        int rc = subset_table(c, j, (int)B.lane_half, (int)B.lane_t, B.lane_n, &a);
-        if (rc == MDIST_OK && a) rc = subset_table(c, j, 1 - (int)B.lane_half, (int)B.walk_t, B.walk_n, &w);
+        const void *a = nullptr, *w = nullptr, *wx = nullptr;
+        const int walk_half = 1 - (int)B.lane_half;
+        int rc = subset_table(c, j, (int)B.lane_half, (int)B.lane_t, B.lane_n, false, &a);
+        if (rc == MDIST_OK && a) rc = subset_table(c, j, walk_half, (int)B.walk_t, B.walk_n, false, &w);
+        if (rc == MDIST_OK && w) rc = subset_table(c, j, walk_half, (int)B.walk_t, B.walk_n, true, &wx);
         if (rc != MDIST_OK) return rc;
-        if (a && w) {
-            lane[b] = a;
-            walk[b] = w;
+        if (a && w && wx) {
+            tabs[b].lane = (const uint32_t *)a;
+            tabs[b].walk = (const uint32_t *)w;
+            tabs[b].walk_exp = (const uint8_t *)wx;
         }
     }
     return MDIST_OK;
@@ -184,14 +201,13 @@ int run_unit(mdist_code *c, int g, int j, int U_thr, bool hist_mode, bool *found
         if (!mdist::filter_group_valid(group, dr.nwords)) group = 0;
     }
     c->st.last_group = group;
-    const uint32_t *lane_tab[mdist::kMaxBlocks], *walk_tab[mdist::kMaxBlocks];
+    mdist::GramTables tabs[mdist::kMaxBlocks];
     if (!hist_mode) {
-        const int rc = gram_tables(c, j, p, lane_tab, walk_tab);
+        const int rc = gram_tables(c, j, p, tabs);
         if (rc != MDIST_OK) return rc;
     }
     if (mdist::launch_unit_split(p, dr.nwords, group, hist_mode, c->sm_count, c->opt.blocks_per_sm,
-                                 hist_mode ? nullptr : lane_tab, hist_mode ? nullptr : walk_tab,
-                                 c->stream) != cudaSuccess)
+                                 hist_mode ? nullptr : tabs, c->stream) != cudaSuccess)
         return MDIST_ECUDA;
     if (cudaEventRecord(c->ev1, c->stream) != cudaSuccess) return MDIST_ECUDA;
     if (cudaMemcpyAsync(c->h_slot, c->d_slot, sizeof(UnitSlot), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess)
@@ -458,11 +474,11 @@ static int run_wave(mdist_code *c, int g_hi, int max_units, int *units_done) {
         const int fg = c->opt.filter_group;
         int group = fg == 0 ? mdist::choose_filter_group(dr.nwords, dr.n_bits, U_thr - q.base) : (fg == 1 ? 0 : fg);
         if (!mdist::filter_group_valid(group, dr.nwords)) group = 0;
-        const uint32_t *lane_tab[mdist::kMaxBlocks], *walk_tab[mdist::kMaxBlocks];
-        const int rc = gram_tables(c, j, q, lane_tab, walk_tab);
+        mdist::GramTables tabs[mdist::kMaxBlocks];
+        const int rc = gram_tables(c, j, q, tabs);
         if (rc != MDIST_OK) return rc;
-        if (mdist::launch_unit_split(q, dr.nwords, group, false, c->sm_count, c->opt.blocks_per_sm, lane_tab,
-                                     walk_tab, c->stream) != cudaSuccess)
+        if (mdist::launch_unit_split(q, dr.nwords, group, false, c->sm_count, c->opt.blocks_per_sm, tabs,
+                                     c->stream) != cudaSuccess)
             return MDIST_ECUDA;
     }
     if (cudaEventRecord(c->ev1, c->stream) != cudaSuccess) return MDIST_ECUDA;

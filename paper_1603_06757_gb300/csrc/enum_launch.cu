@@ -150,19 +150,18 @@ size_t enum_smem_bytes(int k, int nwords) {
 // the others on the ALU kernel.  Both launches share the threshold word, key, count and
 // status of `p`.
 cudaError_t launch_unit_split(const EnumParams &p, int nwords, int group, bool hist_mode, int sm_count,
-                              int blocks_per_sm, const uint32_t *const *lane_tab, const uint32_t *const *walk_tab,
-                              cudaStream_t stream) {
+                              int blocks_per_sm, const GramTables *tabs, cudaStream_t stream) {
     bool tc[kMaxBlocks] = {};
     int ntc = 0;
-    if (!hist_mode && lane_tab && walk_tab)
+    if (!hist_mode && tabs)
         for (int b = 0; b < p.nblocks; ++b)
-            if (lane_tab[b] && walk_tab[b]) {
+            if (tabs[b].lane && tabs[b].walk && tabs[b].walk_exp) {
                 tc[b] = true;
                 ++ntc;
             }
     if (ntc) {
-        const cudaError_t e = launch_gram_unit(p, lane_tab, walk_tab, p.U, p.slot,
-                                               reinterpret_cast<int *>(&p.slot->status), sm_count, stream);
+        const cudaError_t e = launch_gram_unit(p, tabs, p.U, p.slot, reinterpret_cast<int *>(&p.slot->status),
+                                               sm_count, stream);
         if (e != cudaSuccess) return e;
     }
     if (ntc == p.nblocks) return cudaSuccess;

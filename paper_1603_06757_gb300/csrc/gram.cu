@@ -7,23 +7,32 @@
 // so the weights of a whole 128 x 256 tile of codewords form a Gram matrix: a dense
 // contraction over the n_bits columns.  Operand rows are bit-expanded to E4M3 bytes
 // (x: 1.0 per set bit; y: -2.0 per set bit) and carry six extra columns after the bits
-// that add wt(x) and wt(y) - thr - 1 as base-8 digits (every value exact in E4M3), so
+// that add wt(x) - thr - 1 and wt(y) as base-8 digits (every value exact in E4M3), so
 // one kind::f8f6f4 MMA chain with f32 accumulation gives, exactly,
 //     acc = wt(x ^ y) - thr - 1      (thr = largest reduced weight still a candidate),
 // and a codeword is a candidate iff acc < 0: the epilogue ORs the sign bits of the
 // accumulators it reads from TMEM and only a set sign bit sends a lane to the side path,
 // which recomputes the weight from the bit-packed rows before touching the key.
 //
-// Persistent grid, one CTA per SM, 416 threads in three roles:
-//   warps 0-3   epilogue  (TMEM lanes 32w..32w+31 = rows of the accumulator tile),
-//   warps 4-11  builders  (operand rows: load the subset sum from the per-half table of
-//               subset sums, expand it to bytes, add the augmented columns),
-//   warp  12    MMA issue (one lane) and TMEM allocation.
+// The threshold sits on the A side, so a B operand tile does not depend on it: the B
+// side of a block is expanded once, tile by tile in the shared-memory layout, into a
+// device table, and a tile reaches shared memory as one bulk copy.  A tiles are built
+// per work unit from the bit-packed subset sums with the threshold of that moment (a
+// threshold read late is only larger, never smaller, than the current one: more
+// candidates, all rechecked exactly).
+//
+// Persistent grid, one CTA per SM, 320 threads in four roles:
+//   warps 0-3  epilogue   (TMEM lanes 32w..32w+31 = rows of the accumulator tile),
+//   warps 4-7  A builders (one A row each: load the subset sum, expand, augment),
+//   warp  8    B producer (one lane: bulk copies of B tiles),
+//   warp  9    MMA issue  (one lane) and TMEM allocation.
 // A work unit is (product block, 128-row A tile, up to kTilesPerUnit 256-row B tiles);
-// every role walks the same static sequence of work units (CTA c takes c, c + grid,
-// ...).  Operand B has two shared-memory stages, the accumulator two TMEM buffers
-// (2 x 256 columns); all hand-offs are mbarriers, every wait is bounded and a timeout
-// sets the status word and ends the kernel after its MMAs have drained.
+// the units of a block are ordered A tile first, so the CTAs running at the same time
+// share their B tiles in L2.  Every role walks the same static sequence of work units
+// (CTA c takes c, c + grid, ...).  A has two shared-memory stages, B up to four, the
+// accumulator two TMEM buffers (2 x 256 columns); all hand-offs are mbarriers, every
+// wait is bounded and a timeout sets the status word and ends the kernel after its
+// copies and MMAs have drained.
 #include <cstdint>
 
 #include "combinatorics.cuh"
@@ -44,11 +53,19 @@ namespace {
 constexpr int kGM = 128;               // accumulator rows (A tile)
 constexpr int kGN = 256;               // accumulator columns (B tile)
 constexpr int kTilesPerUnit = 16;      // B tiles per work unit
-constexpr int kGramThreads = 416;  // 4 epilogue warps, 8 builder warps, 1 MMA warp
+constexpr int kGramThreads = 320;      // 4 epilogue warps, 4 builder warps, producer warp, MMA warp
 constexpr uint8_t kE4M3One = 0x38;     // 1.0
 constexpr uint8_t kE4M3MinusTwo = 0xC0;  // -2.0
+constexpr int kSmemOperandBudget = 200 << 10;
 
 __host__ __device__ constexpr int gram_ka(int nw) { return 32 * nw + 32; }  // bytes per operand row
+
+// B stages that fit beside the two A stages
+__host__ __device__ constexpr int gram_b_stages(int nw) {
+    return (kSmemOperandBudget - 2 * kGM * gram_ka(nw)) / (kGN * gram_ka(nw)) < 4
+               ? (kSmemOperandBudget - 2 * kGM * gram_ka(nw)) / (kGN * gram_ka(nw))
+               : 4;
+}
 
 // E4M3 code of an integer 0..15 (exact)
 __device__ __forceinline__ uint32_t e4m3_small(uint32_t v) {
@@ -80,10 +97,10 @@ struct GramBlock {
     unsigned long long wu_begin;
     const uint32_t *a_tab;       // a_n x nwords: subset sums of the A side, colex order
     const uint32_t *b_tab;       // b_n x nwords
+    const uint8_t *b_exp;        // b_tiles x (kGN x KA) bytes: expanded B tiles (layout of write_row)
 };
 
 struct GramParams {
-    const uint32_t *rows;        // k x nwords
     unsigned int *U;
     UnitSlot *slot;
     int *status;
@@ -94,6 +111,7 @@ struct GramParams {
     GramBlock blocks[kMaxBlocks];
 };
 
+// work unit -> (block, A tile, B tile range); within a block the A tile runs fastest
 __device__ __forceinline__ void decode_wu(const GramParams &P, unsigned long long wu, int &b,
                                           unsigned long long &a_tile, unsigned long long &bt0,
                                           unsigned long long &bt1) {
@@ -101,8 +119,8 @@ __device__ __forceinline__ void decode_wu(const GramParams &P, unsigned long lon
     while (b + 1 < P.nblocks && wu >= P.blocks[b + 1].wu_begin) ++b;
     const GramBlock &B = P.blocks[b];
     const unsigned long long w = wu - B.wu_begin;
-    a_tile = w / B.b_units;
-    const unsigned long long bu = w - a_tile * B.b_units;
+    const unsigned long long bu = w / B.a_tiles;
+    a_tile = w - bu * B.a_tiles;
     bt0 = bu * kTilesPerUnit;
     bt1 = bt0 + kTilesPerUnit < B.b_tiles ? bt0 + kTilesPerUnit : B.b_tiles;
 }
@@ -147,34 +165,36 @@ template <int NW>
 __global__ void __launch_bounds__(kGramThreads, 1) gram_kernel(const __grid_constant__ GramParams P) {
     constexpr int KA = gram_ka(NW);
     constexpr int KSTEPS = KA / 32;
+    constexpr int S = gram_b_stages(NW);
     constexpr int A_BYTES = kGM * KA, B_BYTES = kGN * KA;
+    static_assert(S >= 2, "two B stages at least");
     extern __shared__ __align__(1024) uint8_t sm[];
-    uint8_t *sA = sm;
-    uint8_t *sB0 = sm + A_BYTES;
-    // barriers: 0 a_full, 1 a_empty, 2-3 b_full, 4-5 b_empty, 6-7 acc_full, 8-9 acc_empty, 10 drain
-    uint64_t *bars = reinterpret_cast<uint64_t *>(sm + A_BYTES + 2 * B_BYTES);
-    uint32_t *s_tmem = reinterpret_cast<uint32_t *>(bars + 12);
+    uint8_t *sA0 = sm;
+    uint8_t *sB0 = sm + 2 * A_BYTES;
+    // barriers: 0-1 a_full, 2-3 a_empty, 4-5 acc_full, 6-7 acc_empty, 8 drain,
+    //           9 .. 9+S-1 b_full, 9+S .. 9+2S-1 b_empty
+    uint64_t *bars = reinterpret_cast<uint64_t *>(sm + 2 * A_BYTES + S * B_BYTES);
+    uint32_t *s_tmem = reinterpret_cast<uint32_t *>(bars + 20);
     volatile int *s_abort = reinterpret_cast<volatile int *>(s_tmem + 1);
-    uint32_t *s_rows = reinterpret_cast<uint32_t *>(bars + 16);
-    uint32_t *s_bn = s_rows + P.k * NW;
+    uint32_t *s_bn = reinterpret_cast<uint32_t *>(bars + 24);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     auto bar = [&](int i) { return smem_addr(bars + i); };
+    constexpr int A_FULL = 0, A_EMPTY = 2, ACC_FULL = 4, ACC_EMPTY = 6, DRAIN = 8, B_FULL = 9, B_EMPTY = 9 + S;
 
-    for (int i = tid; i < P.k * NW; i += blockDim.x) s_rows[i] = P.rows[i];
     for (int i = tid; i < kBn * kBn; i += blockDim.x) s_bn[i] = (uint32_t)c_binom_g.v[i / kBn][i % kBn];
-    if (warp == 12) tmem_alloc(smem_addr(s_tmem), 512);
+    if (warp == 9) tmem_alloc(smem_addr(s_tmem), 512);
     if (tid == 0) {
-        mbar_init(bar(0), 256);
-        mbar_init(bar(1), 1);
-        mbar_init(bar(2), 256);
-        mbar_init(bar(3), 256);
-        mbar_init(bar(4), 1);
-        mbar_init(bar(5), 1);
-        mbar_init(bar(6), 1);
-        mbar_init(bar(7), 1);
-        mbar_init(bar(8), 128);
-        mbar_init(bar(9), 128);
-        mbar_init(bar(10), 1);
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(bar(A_FULL + i), 128);
+            mbar_init(bar(A_EMPTY + i), 1);
+            mbar_init(bar(ACC_FULL + i), 1);
+            mbar_init(bar(ACC_EMPTY + i), 128);
+        }
+        mbar_init(bar(DRAIN), 1);
+        for (int i = 0; i < S; ++i) {
+            mbar_init(bar(B_FULL + i), 1);
+            mbar_init(bar(B_EMPTY + i), 1);
+        }
         *s_abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -187,62 +207,66 @@ __global__ void __launch_bounds__(kGramThreads, 1) gram_kernel(const __grid_cons
         atomicExch(P.status, 1);
     };
 
-    if (warp >= 4 && warp < 12) {
-        // ---------------- builders ----------------
-        const int r = tid - 128;  // B row r; A row r when r < 128
-        unsigned long long t = 0, u = 0;
+    if (warp >= 4 && warp < 8) {
+        // ---------------- A builders ----------------
+        const int r = tid - 128;
+        unsigned long long u = 0;
         for (unsigned long long wu = blockIdx.x; wu < P.total_wu && !*s_abort; wu += gridDim.x, ++u) {
             int b;
             unsigned long long a_tile, bt0, bt1;
             decode_wu(P, wu, b, a_tile, bt0, bt1);
             const GramBlock &B = P.blocks[b];
-            if (!mbar_wait(bar(1), (uint32_t)((u & 1) ^ 1), P.max_wait)) { fail(); break; }
-            if (r < kGM) {
-                const unsigned long long e = a_tile * kGM + (unsigned long long)r;
-                uint32_t x[NW];
-                if (e < B.a_n) {
-                    int wx = 0;
+            const int st = (int)(u & 1);
+            const unsigned long long e = a_tile * kGM + (unsigned long long)r;
+            uint32_t x[NW];
+            int v = 1023;  // padding row: zero bits, never a candidate
+            if (e < B.a_n) {
+                int wx = 0;
 #pragma unroll
-                    for (int w = 0; w < NW; ++w) {
-                        x[w] = B.a_tab[e * NW + w];
-                        wx += __popc(x[w]);
-                    }
-                    write_row<NW>(sA, r, x, kE4M3One, digits3(wx), kScale3);
-                } else {  // padding row: zero bits, weight 1023 (never a candidate)
-#pragma unroll
-                    for (int w = 0; w < NW; ++w) x[w] = 0;
-                    write_row<NW>(sA, r, x, kE4M3One, digits3(1023), kScale3);
+                for (int w = 0; w < NW; ++w) {
+                    x[w] = B.a_tab[e * NW + w];
+                    wx += __popc(x[w]);
                 }
+                v = wx - ((int)(*(volatile unsigned int *)P.U) - P.base) - 1;
+                v = v < -1023 ? -1023 : (v > 1023 ? 1023 : v);
+            } else {
+#pragma unroll
+                for (int w = 0; w < NW; ++w) x[w] = 0;
             }
+            if (!mbar_wait(bar(A_EMPTY + st), (uint32_t)(((u >> 1) & 1) ^ 1), P.max_wait)) { fail(); break; }
+            write_row<NW>(sA0 + st * A_BYTES, r, x, kE4M3One, digits3(v), kScale3);
             fence_async_smem();
-            mbar_arrive(bar(0));
-            for (unsigned long long bt = bt0; bt < bt1; ++bt, ++t) {
-                const int s = (int)(t & 1);
-                if (!mbar_wait(bar(4 + s), (uint32_t)(((t >> 1) & 1) ^ 1), P.max_wait)) { fail(); break; }
-                uint8_t *sB = sB0 + s * B_BYTES;
-                const int thr = (int)(*(volatile unsigned int *)P.U) - P.base;
-                const unsigned long long e = bt * kGN + (unsigned long long)r;
-                uint32_t y[NW];
-                int v = 1023;  // padding column: never a candidate
-                if (e < B.b_n) {
-                    int wy = 0;
-#pragma unroll
-                    for (int w = 0; w < NW; ++w) {
-                        y[w] = B.b_tab[e * NW + w];
-                        wy += __popc(y[w]);
-                    }
-                    v = wy - thr - 1;
-                    v = v < -1023 ? -1023 : (v > 1023 ? 1023 : v);
-                } else {
-#pragma unroll
-                    for (int w = 0; w < NW; ++w) y[w] = 0;
-                }
-                write_row<NW>(sB, r, y, kE4M3MinusTwo, kScale3, digits3(v));
-                fence_async_smem();
-                mbar_arrive(bar(2 + s));
-            }
+            mbar_arrive(bar(A_FULL + st));
         }
-    } else if (warp == 12) {
+    } else if (warp == 8) {
+        // ---------------- B producer ----------------
+        if (lane == 0) {
+            unsigned long long t = 0;
+            for (unsigned long long wu = blockIdx.x; wu < P.total_wu && !*s_abort; wu += gridDim.x) {
+                int b;
+                unsigned long long a_tile, bt0, bt1;
+                decode_wu(P, wu, b, a_tile, bt0, bt1);
+                const GramBlock &B = P.blocks[b];
+                bool ok = true;
+                for (unsigned long long bt = bt0; bt < bt1; ++bt, ++t) {
+                    const int s = (int)(t % S);
+                    if (!mbar_wait(bar(B_EMPTY + s), (uint32_t)(((t / S) & 1) ^ 1), P.max_wait)) {
+                        ok = false;
+                        break;
+                    }
+                    mbar_arrive_expect_tx(bar(B_FULL + s), (uint32_t)B_BYTES);
+                    bulk_copy_g2s(smem_addr(sB0 + s * B_BYTES), B.b_exp + bt * (unsigned long long)B_BYTES,
+                                  (uint32_t)B_BYTES, bar(B_FULL + s));
+                }
+                if (!ok) { fail(); break; }
+            }
+            // no copy may still be writing shared memory when the CTA ends: wait for the
+            // last copy of every stage
+            const unsigned long long first = t > (unsigned long long)S ? t - S : 0;
+            for (unsigned long long i = first; i < t; ++i)
+                if (!mbar_wait(bar(B_FULL + (int)(i % S)), (uint32_t)((i / S) & 1), P.max_wait)) fail();
+        }
+    } else if (warp == 9) {
         // ---------------- MMA issue ----------------
         if (lane == 0) {
             const uint32_t idesc = idesc_f8f6f4_e4m3_f32(kGM, kGN);
@@ -252,30 +276,31 @@ __global__ void __launch_bounds__(kGramThreads, 1) gram_kernel(const __grid_cons
                 int b;
                 unsigned long long a_tile, bt0, bt1;
                 decode_wu(P, wu, b, a_tile, bt0, bt1);
-                if (!mbar_wait(bar(0), (uint32_t)(u & 1), P.max_wait)) { fail(); break; }
+                const int st = (int)(u & 1);
+                if (!mbar_wait(bar(A_FULL + st), (uint32_t)((u >> 1) & 1), P.max_wait)) { fail(); break; }
                 bool ok = true;
                 for (unsigned long long bt = bt0; bt < bt1; ++bt, ++t) {
-                    const int s = (int)(t & 1), ab = (int)(t & 1);
-                    if (!mbar_wait(bar(2 + s), (uint32_t)((t >> 1) & 1), P.max_wait) ||
-                        !mbar_wait(bar(8 + ab), (uint32_t)(((t >> 1) & 1) ^ 1), P.max_wait)) {
+                    const int s = (int)(t % S), ab = (int)(t & 1);
+                    if (!mbar_wait(bar(B_FULL + s), (uint32_t)((t / S) & 1), P.max_wait) ||
+                        !mbar_wait(bar(ACC_EMPTY + ab), (uint32_t)(((t >> 1) & 1) ^ 1), P.max_wait)) {
                         ok = false;
                         break;
                     }
                     tc_fence_after();
-                    const uint32_t a0 = smem_addr(sA), b0 = smem_addr(sB0 + s * B_BYTES);
+                    const uint32_t a0 = smem_addr(sA0 + st * A_BYTES), b0 = smem_addr(sB0 + s * B_BYTES);
                     const uint32_t d = tmem + (uint32_t)(ab * kGN);
 #pragma unroll
                     for (int ks = 0; ks < KSTEPS; ++ks)
                         mma_f8f6f4(d, smem_desc(a0 + ks * 256, 128, sbo), smem_desc(b0 + ks * 256, 128, sbo), idesc,
                                    ks > 0 ? 1u : 0u);
-                    mma_commit(bar(4 + s));   // operand stage free again
-                    mma_commit(bar(6 + ab));  // accumulator ready
+                    mma_commit(bar(B_EMPTY + s));   // operand stage free again
+                    mma_commit(bar(ACC_FULL + ab));  // accumulator ready
                 }
-                mma_commit(bar(1));  // A tile free again
+                mma_commit(bar(A_EMPTY + st));  // A tile free again
                 if (!ok) { fail(); break; }
             }
-            mma_commit(bar(10));
-            if (!mbar_wait(bar(10), 0, P.max_wait)) fail();  // every MMA has completed
+            mma_commit(bar(DRAIN));
+            if (!mbar_wait(bar(DRAIN), 0, P.max_wait)) fail();  // every MMA has completed
         }
     } else {
         // ---------------- epilogue (warps 0-3) ----------------
@@ -293,7 +318,7 @@ __global__ void __launch_bounds__(kGramThreads, 1) gram_kernel(const __grid_cons
                                                         : (unsigned long long)kGM;
             for (unsigned long long bt = bt0; bt < bt1; ++bt, ++t) {
                 const int ab = (int)(t & 1);
-                if (!mbar_wait(bar(6 + ab), (uint32_t)((t >> 1) & 1), P.max_wait)) {
+                if (!mbar_wait(bar(ACC_FULL + ab), (uint32_t)((t >> 1) & 1), P.max_wait)) {
                     fail();
                     break;
                 }
@@ -336,7 +361,7 @@ __global__ void __launch_bounds__(kGramThreads, 1) gram_kernel(const __grid_cons
                     }
                 }
                 tc_fence_before();
-                mbar_arrive(bar(8 + ab));
+                mbar_arrive(bar(ACC_EMPTY + ab));
                 if (row == 0) {
                     const unsigned long long b_left = B.b_n - bt * kGN;
                     cnt += a_valid_rows * (b_left < (unsigned long long)kGN ? b_left : (unsigned long long)kGN);
@@ -348,21 +373,21 @@ __global__ void __launch_bounds__(kGramThreads, 1) gram_kernel(const __grid_cons
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    if (warp == 12) tmem_dealloc(tmem, 512);
+    if (warp == 9) tmem_dealloc(tmem, 512);
 }
 
 // at least 120 KB so that two CTAs never share an SM (each allocates all 512 TMEM columns)
 template <int NW>
-size_t gram_smem_bytes(int k) {
+size_t gram_smem_bytes() {
     constexpr int KA = gram_ka(NW);
-    const size_t need = (size_t)kGM * KA + 2 * (size_t)kGN * KA + 16 * sizeof(uint64_t) +
-                        sizeof(uint32_t) * ((size_t)k * NW + kBn * kBn);
+    const size_t need = 2 * (size_t)kGM * KA + (size_t)gram_b_stages(NW) * kGN * KA + 24 * sizeof(uint64_t) +
+                        sizeof(uint32_t) * (size_t)(kBn * kBn);
     return need < (size_t)(120 << 10) ? (size_t)(120 << 10) : need;
 }
 
 template <int NW>
 cudaError_t gram_launch_nw(const GramParams &p, int sm_count, cudaStream_t stream) {
-    const size_t smem = gram_smem_bytes<NW>(p.k);
+    const size_t smem = gram_smem_bytes<NW>();
     cudaError_t e = cudaFuncSetAttribute(gram_kernel<NW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     unsigned long long grid = (unsigned long long)sm_count;
@@ -389,6 +414,34 @@ __global__ void subset_table_kernel(const uint32_t *rows, int kh, int t, unsigne
     }
 }
 
+// B tiles of a packed table: row e of tile e / kGN is the expanded y (-2.0 per set bit)
+// with scales 64, 8, 1 against the A side's digits and the digits of wt(y) against the
+// A side's scales; rows past `count` are padding (zero bits, weight 1023: never a
+// candidate).
+template <int NW>
+__global__ void expand_table_kernel(const uint32_t *packed, unsigned long long count, unsigned long long rows,
+                                    uint8_t *out) {
+    constexpr int KA = gram_ka(NW);
+    for (unsigned long long e = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; e < rows;
+         e += (unsigned long long)gridDim.x * blockDim.x) {
+        uint32_t y[NW];
+        int wy = 1023;
+        if (e < count) {
+            wy = 0;
+#pragma unroll
+            for (int w = 0; w < NW; ++w) {
+                y[w] = packed[e * NW + w];
+                wy += __popc(y[w]);
+            }
+        } else {
+#pragma unroll
+            for (int w = 0; w < NW; ++w) y[w] = 0;
+        }
+        write_row<NW>(out + (e / kGN) * (unsigned long long)(kGN * KA), (int)(e % kGN), y, kE4M3MinusTwo, kScale3,
+                      digits3(wy));
+    }
+}
+
 template <int NW>
 cudaError_t table_launch_nw(const uint32_t *rows, int kh, int t, unsigned long long count, uint32_t *out,
                             int sm_count, cudaStream_t stream) {
@@ -397,6 +450,18 @@ cudaError_t table_launch_nw(const uint32_t *rows, int kh, int t, unsigned long l
     if (grid > cap) grid = cap;
     if (grid < 1) grid = 1;
     subset_table_kernel<NW><<<(unsigned int)grid, 256, 0, stream>>>(rows, kh, t, count, out);
+    return cudaGetLastError();
+}
+
+template <int NW>
+cudaError_t expand_launch_nw(const uint32_t *packed, unsigned long long count, uint8_t *out, int sm_count,
+                             cudaStream_t stream) {
+    const unsigned long long rows = (count + kGN - 1) / kGN * kGN;
+    unsigned long long grid = (rows + 255) / 256;
+    const unsigned long long cap = (unsigned long long)sm_count * 8;
+    if (grid > cap) grid = cap;
+    if (grid < 1) grid = 1;
+    expand_table_kernel<NW><<<(unsigned int)grid, 256, 0, stream>>>(packed, count, rows, out);
     return cudaGetLastError();
 }
 
@@ -416,13 +481,29 @@ cudaError_t launch_subset_table(const uint32_t *rows, int nwords, int kh, int t,
     }
 }
 
-// Blocks whose sides both hold at least kGramMinSide entries go to the tensor cores.
+size_t gram_expanded_bytes(int nwords, unsigned long long count) {
+    return (size_t)((count + kGN - 1) / kGN) * (size_t)kGN * (size_t)gram_ka(nwords);
+}
+
+cudaError_t launch_expand_table(const uint32_t *packed, int nwords, unsigned long long count, uint8_t *out,
+                                int sm_count, cudaStream_t stream) {
+    switch (nwords) {
+        case 1: return expand_launch_nw<1>(packed, count, out, sm_count, stream);
+        case 2: return expand_launch_nw<2>(packed, count, out, sm_count, stream);
+        case 3: return expand_launch_nw<3>(packed, count, out, sm_count, stream);
+        case 4: return expand_launch_nw<4>(packed, count, out, sm_count, stream);
+        case 5: return expand_launch_nw<5>(packed, count, out, sm_count, stream);
+        case 6: return expand_launch_nw<6>(packed, count, out, sm_count, stream);
+        case 7: return expand_launch_nw<7>(packed, count, out, sm_count, stream);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
 bool gram_eligible(int nwords) { return nwords >= 1 && nwords <= kGramMaxWords; }
 
-cudaError_t launch_gram_unit(const EnumParams &ep, const uint32_t *const *lane_tab, const uint32_t *const *walk_tab,
-                             unsigned int *U, UnitSlot *slot, int *status, int sm_count, cudaStream_t stream) {
+cudaError_t launch_gram_unit(const EnumParams &ep, const GramTables *tabs, unsigned int *U, UnitSlot *slot,
+                             int *status, int sm_count, cudaStream_t stream) {
     GramParams p{};
-    p.rows = ep.rows;
     p.U = U;
     p.slot = slot;
     p.status = status;
@@ -437,11 +518,13 @@ cudaError_t launch_gram_unit(const EnumParams &ep, const uint32_t *const *lane_t
     int nb = 0;
     unsigned long long wu = 0;
     for (int b = 0; b < ep.nblocks; ++b) {
-        if (!lane_tab[b] || !walk_tab[b]) continue;
+        const GramTables &T = tabs[b];
+        if (!T.lane || !T.walk || !T.walk_exp) continue;
         const ProductBlock &E = ep.blocks[b];
         GramBlock &G = p.blocks[nb++];
-        G.a_tab = lane_tab[b];
-        G.b_tab = walk_tab[b];
+        G.a_tab = T.lane;
+        G.b_tab = T.walk;
+        G.b_exp = T.walk_exp;
         G.a_half = E.lane_half;
         G.a_t = E.lane_t;
         G.b_t = E.walk_t;

@@ -78,17 +78,28 @@ cudaError_t launch_enum_unit(const EnumParams &p, int nwords, int group, bool hi
 constexpr int kGramMinSide = 128;
 constexpr int kGramMaxWords = 7;
 bool gram_eligible(int nwords);
-// lane_tab[b] / walk_tab[b]: device tables of the subset sums of block b's two sides
-// (colex order, nwords words each), or null for a block left to the ALU kernel.
-cudaError_t launch_gram_unit(const EnumParams &ep, const uint32_t *const *lane_tab, const uint32_t *const *walk_tab,
-                             unsigned int *U, UnitSlot *slot, int *status, int sm_count, cudaStream_t stream);
+// Device tables of one product block for the tensor-core enumerator: the subset sums of
+// its lane side and of its walk side (colex order, nwords words each) and the walk side
+// expanded to operand tiles (gram_expanded_bytes).  All null: the block stays on the
+// ALU kernel.
+struct GramTables {
+    const uint32_t *lane = nullptr;
+    const uint32_t *walk = nullptr;
+    const uint8_t *walk_exp = nullptr;
+};
+cudaError_t launch_gram_unit(const EnumParams &ep, const GramTables *tabs, unsigned int *U, UnitSlot *slot,
+                             int *status, int sm_count, cudaStream_t stream);
 // out[e * nwords ..] = sum of the rows of the t-subset of rows[0..kh) with colex rank e
 cudaError_t launch_subset_table(const uint32_t *rows, int nwords, int kh, int t, unsigned long long count,
                                 uint32_t *out, int sm_count, cudaStream_t stream);
-// A unit: blocks with both tables on the tensor cores, the others on the ALU kernel.
+// bytes of the expanded operand tiles of a packed table of `count` entries
+size_t gram_expanded_bytes(int nwords, unsigned long long count);
+cudaError_t launch_expand_table(const uint32_t *packed, int nwords, unsigned long long count, uint8_t *out,
+                                int sm_count, cudaStream_t stream);
+// A unit: blocks with tables on the tensor cores, the others on the ALU kernel
+// (tabs may be null: every block on the ALU kernel).
 cudaError_t launch_unit_split(const EnumParams &p, int nwords, int group, bool hist_mode, int sm_count,
-                              int blocks_per_sm, const uint32_t *const *lane_tab, const uint32_t *const *walk_tab,
-                              cudaStream_t stream);
+                              int blocks_per_sm, const GramTables *tabs, cudaStream_t stream);
 
 // Filter variant for a unit: 0 (exact count for every codeword) or the OR-group size
 // 2, 3, 4 whose expected cost is least for this row width and threshold.

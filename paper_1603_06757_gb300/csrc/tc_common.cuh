@@ -84,6 +84,21 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mbar_smem, uint32_t parity, l
     return false;
 }
 
+// arrive on an mbarrier and raise its expected transaction bytes
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t mbar_smem, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar_smem), "r"(bytes) : "memory");
+}
+
+// bulk copy global -> this CTA's shared memory (both 16-byte aligned, bytes a multiple
+// of 16), completion counted on the mbarrier as transaction bytes
+__device__ __forceinline__ void bulk_copy_g2s(uint32_t dst_smem, const void *src, uint32_t bytes,
+                                              uint32_t mbar_smem) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     dst_smem),
+                 "l"(src), "r"(bytes), "r"(mbar_smem)
+                 : "memory");
+}
+
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
