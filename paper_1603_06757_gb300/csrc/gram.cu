@@ -21,11 +21,12 @@
 // threshold read late is only larger, never smaller, than the current one: more
 // candidates, all rechecked exactly).
 //
-// Persistent grid, one CTA per SM, 320 threads in four roles:
-//   warps 0-3  epilogue   (TMEM lanes 32w..32w+31 = rows of the accumulator tile),
-//   warps 4-7  A builders (one A row each: load the subset sum, expand, augment),
-//   warp  8    B producer (one lane: bulk copies of B tiles),
-//   warp  9    MMA issue  (one lane) and TMEM allocation.
+// Persistent grid, one CTA per SM, 448 threads in four roles:
+//   warps 0-7  epilogue   (warp w: TMEM lanes 32 (w % 4) .. + 31 = rows of the
+//              accumulator tile, columns 128 (w / 4) .. + 127),
+//   warps 8-11 A builders (one A row each: load the subset sum, expand, augment),
+//   warp  12   B producer (one lane: bulk copies of B tiles),
+//   warp  13   MMA issue  (one lane) and TMEM allocation.
 // A work unit is (product block, 128-row A tile, up to kTilesPerUnit 256-row B tiles);
 // the units of a block are ordered A tile first, so the CTAs running at the same time
 // share their B tiles in L2.  Every role walks the same static sequence of work units
@@ -53,7 +54,7 @@ namespace {
 constexpr int kGM = 128;               // accumulator rows (A tile)
 constexpr int kGN = 256;               // accumulator columns (B tile)
 constexpr int kTilesPerUnit = 16;      // B tiles per work unit
-constexpr int kGramThreads = 320;      // 4 epilogue warps, 4 builder warps, producer warp, MMA warp
+constexpr int kGramThreads = 448;      // 8 epilogue warps, 4 builder warps, producer warp, MMA warp
 constexpr uint8_t kE4M3One = 0x38;     // 1.0
 constexpr uint8_t kE4M3MinusTwo = 0xC0;  // -2.0
 constexpr int kSmemOperandBudget = 200 << 10;
@@ -182,13 +183,13 @@ __global__ void __launch_bounds__(kGramThreads, 1) gram_kernel(const __grid_cons
     constexpr int A_FULL = 0, A_EMPTY = 2, ACC_FULL = 4, ACC_EMPTY = 6, DRAIN = 8, B_FULL = 9, B_EMPTY = 9 + S;
 
     for (int i = tid; i < kBn * kBn; i += blockDim.x) s_bn[i] = (uint32_t)c_binom_g.v[i / kBn][i % kBn];
-    if (warp == 9) tmem_alloc(smem_addr(s_tmem), 512);
+    if (warp == 13) tmem_alloc(smem_addr(s_tmem), 512);
     if (tid == 0) {
         for (int i = 0; i < 2; ++i) {
             mbar_init(bar(A_FULL + i), 128);
             mbar_init(bar(A_EMPTY + i), 1);
             mbar_init(bar(ACC_FULL + i), 1);
-            mbar_init(bar(ACC_EMPTY + i), 128);
+            mbar_init(bar(ACC_EMPTY + i), 256);
         }
         mbar_init(bar(DRAIN), 1);
         for (int i = 0; i < S; ++i) {
@@ -207,9 +208,9 @@ __global__ void __launch_bounds__(kGramThreads, 1) gram_kernel(const __grid_cons
         atomicExch(P.status, 1);
     };
 
-    if (warp >= 4 && warp < 8) {
+    if (warp >= 8 && warp < 12) {
         // ---------------- A builders ----------------
-        const int r = tid - 128;
+        const int r = tid - 256;
         unsigned long long u = 0;
         for (unsigned long long wu = blockIdx.x; wu < P.total_wu && !*s_abort; wu += gridDim.x, ++u) {
             int b;
@@ -238,7 +239,7 @@ __global__ void __launch_bounds__(kGramThreads, 1) gram_kernel(const __grid_cons
             fence_async_smem();
             mbar_arrive(bar(A_FULL + st));
         }
-    } else if (warp == 8) {
+    } else if (warp == 12) {
         // ---------------- B producer ----------------
         if (lane == 0) {
             unsigned long long t = 0;
@@ -266,7 +267,7 @@ __global__ void __launch_bounds__(kGramThreads, 1) gram_kernel(const __grid_cons
             for (unsigned long long i = first; i < t; ++i)
                 if (!mbar_wait(bar(B_FULL + (int)(i % S)), (uint32_t)((i / S) & 1), P.max_wait)) fail();
         }
-    } else if (warp == 9) {
+    } else if (warp == 13) {
         // ---------------- MMA issue ----------------
         if (lane == 0) {
             const uint32_t idesc = idesc_f8f6f4_e4m3_f32(kGM, kGN);
@@ -303,8 +304,9 @@ __global__ void __launch_bounds__(kGramThreads, 1) gram_kernel(const __grid_cons
             if (!mbar_wait(bar(DRAIN), 0, P.max_wait)) fail();  // every MMA has completed
         }
     } else {
-        // ---------------- epilogue (warps 0-3) ----------------
-        const int row = tid;  // TMEM lane
+        // ---------------- epilogue (warps 0-7) ----------------
+        const int row = 32 * (warp & 3) + lane;  // TMEM lane = A row
+        const int col0 = 128 * (warp >> 2);      // first accumulator column of this warp
         unsigned long long t = 0, cnt = 0;
         for (unsigned long long wu = blockIdx.x; wu < P.total_wu && !*s_abort; wu += gridDim.x) {
             int b;
@@ -323,28 +325,37 @@ __global__ void __launch_bounds__(kGramThreads, 1) gram_kernel(const __grid_cons
                     break;
                 }
                 tc_fence_after();
-                const uint32_t base = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(ab * kGN);
+                const uint32_t base = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(ab * kGN + col0);
 #pragma unroll 1
-                for (int c = 0; c < kGN / 32; ++c) {
-                    float v[32];
-                    tmem_ld32(base + (uint32_t)(c * 32), v);
-                    uint32_t o = 0;
+                for (int c = 0; c < 128; c += 64) {
+                    uint32_t v0[32], v1[32];
+                    tmem_ld32_issue(base + (uint32_t)c, v0);
+                    tmem_ld32_issue(base + (uint32_t)(c + 32), v1);
+                    tmem_wait_ld(v0);
+                    tmem_regs_ready(v1);
+                    uint32_t o0 = 0, o1 = 0;
 #pragma unroll
-                    for (int i = 0; i < 32; ++i) o |= __float_as_uint(v[i]);
-                    if ((o & 0x80000000u) && a_valid) {
+                    for (int i = 0; i < 32; ++i) {
+                        o0 |= v0[i];
+                        o1 |= v1[i];
+                    }
+                    if (((o0 | o1) & 0x80000000u) && a_valid) {
                         // side path: which columns are negative, then the exact weight from
                         // the bit-packed rows, then the key
-                        uint32_t neg = 0;
+                        unsigned long long neg = 0;
 #pragma unroll
-                        for (int i = 0; i < 32; ++i) neg |= (__float_as_uint(v[i]) >> 31) << i;
+                        for (int i = 0; i < 32; ++i) {
+                            neg |= (unsigned long long)(v0[i] >> 31) << i;
+                            neg |= (unsigned long long)(v1[i] >> 31) << (32 + i);
+                        }
                         const int a_kh = B.a_half ? P.k2 : P.k1, b_kh = B.a_half ? P.k1 : P.k2;
                         uint32_t x[NW];
 #pragma unroll
                         for (int q = 0; q < NW; ++q) x[q] = B.a_tab[a_e * NW + q];
                         while (neg) {
-                            const int i = __ffs(neg) - 1;
+                            const int i = __ffsll((long long)neg) - 1;
                             neg &= neg - 1;
-                            const unsigned long long b_e = bt * kGN + (unsigned long long)(c * 32 + i);
+                            const unsigned long long b_e = bt * kGN + (unsigned long long)(col0 + c + i);
                             if (b_e >= B.b_n) continue;
                             int w = 0;
 #pragma unroll
@@ -362,18 +373,18 @@ __global__ void __launch_bounds__(kGramThreads, 1) gram_kernel(const __grid_cons
                 }
                 tc_fence_before();
                 mbar_arrive(bar(ACC_EMPTY + ab));
-                if (row == 0) {
+                if (tid == 0) {
                     const unsigned long long b_left = B.b_n - bt * kGN;
                     cnt += a_valid_rows * (b_left < (unsigned long long)kGN ? b_left : (unsigned long long)kGN);
                 }
             }
         }
-        if (row == 0 && cnt) atomicAdd(&P.slot->count, cnt);
+        if (tid == 0 && cnt) atomicAdd(&P.slot->count, cnt);
     }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    if (warp == 9) tmem_dealloc(tmem, 512);
+    if (warp == 13) tmem_dealloc(tmem, 512);
 }
 
 // at least 120 KB so that two CTAs never share an SM (each allocates all 512 TMEM columns)
