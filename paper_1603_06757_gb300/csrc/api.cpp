@@ -129,8 +129,8 @@ int subset_table(mdist_code *c, int j, int half, int t, unsigned long long count
     if (!d) return MDIST_OK;
     cudaError_t e;
     if (expanded) {
-        e = mdist::launch_expand_table((const uint32_t *)packed, dr.nwords, count, (uint8_t *)d, c->sm_count,
-                                       c->stream);
+        e = mdist::launch_expand_table((const uint32_t *)packed, dr.nwords, count, dr.n_bits, (uint8_t *)d,
+                                       c->sm_count, c->stream);
     } else {
         const int k1 = (c->k + 1) / 2, kh = half ? c->k - k1 : k1;
         const uint32_t *rows = c->d_rows[(size_t)j] + (half ? (size_t)k1 * (size_t)dr.nwords : 0);

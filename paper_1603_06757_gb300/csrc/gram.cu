@@ -2,38 +2,25 @@
 // blocks of a unit.
 //
 // Within a product block every codeword is x ^ y with x from one side (an i-subset sum
-// of one half of the rows) and y from the other, and
-//     wt(x ^ y) = wt(x) + wt(y) - 2 <x, y>,
-// so the weights of a whole 128 x 256 tile of codewords form a Gram matrix: a dense
-// contraction over the n_bits columns.  Operand rows are bit-expanded to E4M3 bytes
-// (x: 1.0 per set bit; y: -2.0 per set bit) and carry six extra columns after the bits
-// that add wt(x) - thr - 1 and wt(y) as base-8 digits (every value exact in E4M3), so
-// one kind::f8f6f4 MMA chain with f32 accumulation gives, exactly,
-//     acc = wt(x ^ y) - thr - 1      (thr = largest reduced weight still a candidate),
-// and a codeword is a candidate iff acc < 0: the epilogue ORs the sign bits of the
-// accumulators it reads from TMEM and only a set sign bit sends a lane to the side path,
-// which recomputes the weight from the bit-packed rows before touching the key.
+// of one half of the rows) and y from the other.  With the signs e(b) = 1 - 2b of the
+// bits,
+//     sum over the n_bits columns of e(x_c) e(y_c) = n_bits - 2 wt(x ^ y),
+// so the weights of a whole 128 x 256 tile of codewords follow from a Gram matrix: a
+// dense contraction over the n_bits columns.  Operand rows are the signs as E4M3 bytes
+// (+1.0 / -1.0; the B side has zero bytes past n_bits), one kind::f8f6f4 MMA chain
+// with f32 accumulation gives every acc = n_bits - 2 wt(x ^ y) exactly, and a codeword
+// is a candidate iff acc >= n_bits - 2 thr (thr = largest reduced weight still a
+// candidate).  The epilogue takes the maximum of the accumulators it reads from TMEM;
+// only a maximum at or above that bound sends a lane to the side path, which recomputes
+// the weight from the bit-packed rows before touching the key.  A bound read late is
+// only lower, never higher, than the current one: more candidates, all rechecked
+// exactly.
 //
-// The threshold sits on the A side, so a B operand tile does not depend on it: the B
-// side of a block is expanded once, tile by tile in the shared-memory layout, into a
-// device table, and a tile reaches shared memory as one bulk copy.  A tiles are built
-// per work unit from the bit-packed subset sums with the threshold of that moment (a
-// threshold read late is only larger, never smaller, than the current one: more
-// candidates, all rechecked exactly).
+// Neither operand depends on the threshold: the B side of a block is expanded once,
+// tile by tile in the shared-memory layout, into a device table, and a tile reaches
+// shared memory as one bulk copy; A tiles are expanded per work unit from the
+// bit-packed subset sums.
 //
-// Persistent grid, one CTA per SM, 448 threads in four roles:
-//   warps 0-7  epilogue   (warp w: TMEM lanes 32 (w % 4) .. + 31 = rows of the
-//              accumulator tile, columns 128 (w / 4) .. + 127),
-//   warps 8-11 A builders (one A row each: load the subset sum, expand, augment),
-//   warp  12   B producer (one lane: bulk copies of B tiles),
-//   warp  13   MMA issue  (one lane) and TMEM allocation.
-// A work unit is (product block, 128-row A tile, up to kTilesPerUnit 256-row B tiles);
-// the units of a block are ordered A tile first, so the CTAs running at the same time
-// share their B tiles in L2.  Every role walks the same static sequence of work units
-// (CTA c takes c, c + grid, ...).  A has two shared-memory stages, B up to four, the
-// accumulator two TMEM buffers (2 x 256 columns); all hand-offs are mbarriers, every
-// wait is bounded and a timeout sets the status word and ends the kernel after its
-// copies and MMAs have drained.
 #include <cstdint>
 
 #include "combinatorics.cuh"
@@ -54,12 +41,10 @@ namespace {
 constexpr int kGM = 128;               // accumulator rows (A tile)
 constexpr int kGN = 256;               // accumulator columns (B tile)
 constexpr int kTilesPerUnit = 16;      // B tiles per work unit
-constexpr int kGramThreads = 448;      // 8 epilogue warps, 4 builder warps, producer warp, MMA warp
-constexpr uint8_t kE4M3One = 0x38;     // 1.0
-constexpr uint8_t kE4M3MinusTwo = 0xC0;  // -2.0
+constexpr int kGramThreads = 352;      // 8 epilogue warps, builder warp, producer warp, MMA warp
 constexpr int kSmemOperandBudget = 200 << 10;
 
-__host__ __device__ constexpr int gram_ka(int nw) { return 32 * nw + 32; }  // bytes per operand row
+__host__ __device__ constexpr int gram_ka(int nw) { return 32 * nw; }  // bytes per operand row
 
 // B stages that fit beside the two A stages
 __host__ __device__ constexpr int gram_b_stages(int nw) {
@@ -67,27 +52,6 @@ __host__ __device__ constexpr int gram_b_stages(int nw) {
                ? (kSmemOperandBudget - 2 * kGM * gram_ka(nw)) / (kGN * gram_ka(nw))
                : 4;
 }
-
-// E4M3 code of an integer 0..15 (exact)
-__device__ __forceinline__ uint32_t e4m3_small(uint32_t v) {
-    if (v == 0) return 0;
-    const int e = 31 - __clz(v);                 // 2^e <= v < 2^(e+1)
-    const uint32_t mant = ((v << 3) >> e) & 7u;  // 3 fraction bits (exact for v < 16)
-    return ((uint32_t)(e + 7) << 3) | mant;
-}
-
-// base-8 digits of |v| (v in [-1023, 1023]) as E4M3 bytes with the sign of v:
-// |v| = 64 d0 + 8 d1 + d2, d0 <= 15
-__device__ __forceinline__ uint32_t digits3(int v) {
-    const uint32_t s = v < 0 ? 0x80u : 0u;
-    const uint32_t a = (uint32_t)(v < 0 ? -v : v);
-    const uint32_t d0 = a >> 6, d1 = (a >> 3) & 7u, d2 = a & 7u;
-    auto enc = [&](uint32_t d) { return d ? (e4m3_small(d) | s) : 0u; };
-    return enc(d0) | (enc(d1) << 8) | (enc(d2) << 16);
-}
-
-// bytes 64, 8, 1 (E4M3) in the low three bytes
-constexpr uint32_t kScale3 = 0x68u | (0x50u << 8) | (0x38u << 16);
 
 struct GramBlock {
     unsigned int a_half;         // half of the rows the A side's subsets come from
@@ -126,31 +90,30 @@ __device__ __forceinline__ void decode_wu(const GramParams &P, unsigned long lon
     bt1 = bt0 + kTilesPerUnit < B.b_tiles ? bt0 + kTilesPerUnit : B.b_tiles;
 }
 
-// Bit-expanded operand row r of a tile (K-major, no-swizzle layout): the NW words of
-// the subset sum, 1.0 / -2.0 per set bit, then the six augmented columns, then zeros.
+// Operand row r of a tile (K-major, no-swizzle layout): per bit of the NW words one
+// E4M3 byte, +1.0 (0x38) for a clear bit and -1.0 (0xB8) for a set bit; the bits past
+// `nbits` give zero bytes.
 template <int NW>
-__device__ __forceinline__ void write_row(uint8_t *tile, int r, const uint32_t (&x)[NW], uint32_t one,
-                                          uint32_t aug_lo, uint32_t aug_hi) {
+__device__ __forceinline__ void write_row(uint8_t *tile, int r, const uint32_t (&x)[NW], int nbits) {
     constexpr int KA = gram_ka(NW);
 #pragma unroll
     for (int w = 0; w < NW; ++w) {
+        const int vb = nbits - 32 * w;
+        const uint32_t valid = vb >= 32 ? 0xFFFFFFFFu : (vb <= 0 ? 0u : (1u << vb) - 1u);
 #pragma unroll
         for (int h = 0; h < 2; ++h) {  // 16 bits -> 16 bytes
             uint32_t q[4];
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
-                const uint32_t nib = (x[w] >> (16 * h + 4 * j)) & 0xFu;
-                q[j] = ((nib * 0x00204081u) & 0x01010101u) * one;
+                const int sh = 16 * h + 4 * j;
+                const uint32_t set = (((x[w] >> sh) & 0xFu) * 0x00204081u) & 0x01010101u;
+                const uint32_t val = ((((valid >> sh) & 0xFu) * 0x00204081u) & 0x01010101u) * 0xFFu;
+                q[j] = (0x38383838u | (set << 7)) & val;
             }
             *reinterpret_cast<uint4 *>(tile + kmajor_offset((uint32_t)r, (uint32_t)(32 * w + 16 * h), KA)) =
                 make_uint4(q[0], q[1], q[2], q[3]);
         }
     }
-    // columns 32NW .. 32NW+15: three digit bytes, three scale bytes, zeros
-    *reinterpret_cast<uint4 *>(tile + kmajor_offset((uint32_t)r, (uint32_t)(32 * NW), KA)) =
-        make_uint4(aug_lo | ((aug_hi & 0xFFu) << 24), aug_hi >> 8, 0u, 0u);
-    *reinterpret_cast<uint4 *>(tile + kmajor_offset((uint32_t)r, (uint32_t)(32 * NW + 16), KA)) =
-        make_uint4(0u, 0u, 0u, 0u);
 }
 
 template <int NW>
@@ -183,10 +146,10 @@ __global__ void __launch_bounds__(kGramThreads, 1) gram_kernel(const __grid_cons
     constexpr int A_FULL = 0, A_EMPTY = 2, ACC_FULL = 4, ACC_EMPTY = 6, DRAIN = 8, B_FULL = 9, B_EMPTY = 9 + S;
 
     for (int i = tid; i < kBn * kBn; i += blockDim.x) s_bn[i] = (uint32_t)c_binom_g.v[i / kBn][i % kBn];
-    if (warp == 13) tmem_alloc(smem_addr(s_tmem), 512);
+    if (warp == 10) tmem_alloc(smem_addr(s_tmem), 512);
     if (tid == 0) {
         for (int i = 0; i < 2; ++i) {
-            mbar_init(bar(A_FULL + i), 128);
+            mbar_init(bar(A_FULL + i), 32);
             mbar_init(bar(A_EMPTY + i), 1);
             mbar_init(bar(ACC_FULL + i), 1);
             mbar_init(bar(ACC_EMPTY + i), 256);
@@ -208,9 +171,8 @@ __global__ void __launch_bounds__(kGramThreads, 1) gram_kernel(const __grid_cons
         atomicExch(P.status, 1);
     };
 
-    if (warp >= 8 && warp < 12) {
-        // ---------------- A builders ----------------
-        const int r = tid - 256;
+    if (warp == 8) {
+        // ---------------- A builder ----------------
         unsigned long long u = 0;
         for (unsigned long long wu = blockIdx.x; wu < P.total_wu && !*s_abort; wu += gridDim.x, ++u) {
             int b;
@@ -218,28 +180,20 @@ __global__ void __launch_bounds__(kGramThreads, 1) gram_kernel(const __grid_cons
             decode_wu(P, wu, b, a_tile, bt0, bt1);
             const GramBlock &B = P.blocks[b];
             const int st = (int)(u & 1);
-            const unsigned long long e = a_tile * kGM + (unsigned long long)r;
-            uint32_t x[NW];
-            int v = 1023;  // padding row: zero bits, never a candidate
-            if (e < B.a_n) {
-                int wx = 0;
+            uint32_t x[kGM / 32][NW];
 #pragma unroll
-                for (int w = 0; w < NW; ++w) {
-                    x[w] = B.a_tab[e * NW + w];
-                    wx += __popc(x[w]);
-                }
-                v = wx - ((int)(*(volatile unsigned int *)P.U) - P.base) - 1;
-                v = v < -1023 ? -1023 : (v > 1023 ? 1023 : v);
-            } else {
+            for (int h = 0; h < kGM / 32; ++h) {
+                const unsigned long long e = a_tile * kGM + (unsigned long long)(lane + 32 * h);
 #pragma unroll
-                for (int w = 0; w < NW; ++w) x[w] = 0;
+                for (int w = 0; w < NW; ++w) x[h][w] = e < B.a_n ? B.a_tab[e * NW + w] : 0u;
             }
             if (!mbar_wait(bar(A_EMPTY + st), (uint32_t)(((u >> 1) & 1) ^ 1), P.max_wait)) { fail(); break; }
-            write_row<NW>(sA0 + st * A_BYTES, r, x, kE4M3One, digits3(v), kScale3);
+#pragma unroll
+            for (int h = 0; h < kGM / 32; ++h) write_row<NW>(sA0 + st * A_BYTES, lane + 32 * h, x[h], 32 * NW);
             fence_async_smem();
             mbar_arrive(bar(A_FULL + st));
         }
-    } else if (warp == 12) {
+    } else if (warp == 9) {
         // ---------------- B producer ----------------
         if (lane == 0) {
             unsigned long long t = 0;
@@ -267,7 +221,7 @@ __global__ void __launch_bounds__(kGramThreads, 1) gram_kernel(const __grid_cons
             for (unsigned long long i = first; i < t; ++i)
                 if (!mbar_wait(bar(B_FULL + (int)(i % S)), (uint32_t)((i / S) & 1), P.max_wait)) fail();
         }
-    } else if (warp == 13) {
+    } else if (warp == 10) {
         // ---------------- MMA issue ----------------
         if (lane == 0) {
             const uint32_t idesc = idesc_f8f6f4_e4m3_f32(kGM, kGN);
@@ -318,6 +272,8 @@ __global__ void __launch_bounds__(kGramThreads, 1) gram_kernel(const __grid_cons
             const unsigned long long a_valid_rows = B.a_n - a_tile * kGM < (unsigned long long)kGM
                                                         ? B.a_n - a_tile * kGM
                                                         : (unsigned long long)kGM;
+            // candidates: acc >= n_bits - 2 thr, with the threshold of the unit's start
+            const float bound = (float)(P.n_bits - 2 * ((int)(*(volatile unsigned int *)P.U) - P.base));
             for (unsigned long long bt = bt0; bt < bt1; ++bt, ++t) {
                 const int ab = (int)(t & 1);
                 if (!mbar_wait(bar(ACC_FULL + ab), (uint32_t)((t >> 1) & 1), P.max_wait)) {
@@ -326,40 +282,40 @@ __global__ void __launch_bounds__(kGramThreads, 1) gram_kernel(const __grid_cons
                 }
                 tc_fence_after();
                 const uint32_t base = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(ab * kGN + col0);
-#pragma unroll 1
-                for (int c = 0; c < 128; c += 64) {
-                    uint32_t v0[32], v1[32];
-                    tmem_ld32_issue(base + (uint32_t)c, v0);
-                    tmem_ld32_issue(base + (uint32_t)(c + 32), v1);
-                    tmem_wait_ld(v0);
-                    tmem_regs_ready(v1);
-                    uint32_t o0 = 0, o1 = 0;
+                uint32_t v[4][32];
+                tmem_ld32_issue(base, v[0]);
+                tmem_ld32_issue(base + 32u, v[1]);
+                tmem_ld32_issue(base + 64u, v[2]);
+                tmem_ld32_issue(base + 96u, v[3]);
+                tmem_wait_ld(v[0]);
+                tmem_regs_ready(v[1]);
+                tmem_regs_ready(v[2]);
+                tmem_regs_ready(v[3]);
+                float m = __uint_as_float(v[0][0]);
 #pragma unroll
-                    for (int i = 0; i < 32; ++i) {
-                        o0 |= v0[i];
-                        o1 |= v1[i];
-                    }
-                    if (((o0 | o1) & 0x80000000u) && a_valid) {
-                        // side path: which columns are negative, then the exact weight from
-                        // the bit-packed rows, then the key
-                        unsigned long long neg = 0;
+                for (int q = 0; q < 4; ++q)
 #pragma unroll
-                        for (int i = 0; i < 32; ++i) {
-                            neg |= (unsigned long long)(v0[i] >> 31) << i;
-                            neg |= (unsigned long long)(v1[i] >> 31) << (32 + i);
-                        }
-                        const int a_kh = B.a_half ? P.k2 : P.k1, b_kh = B.a_half ? P.k1 : P.k2;
-                        uint32_t x[NW];
+                    for (int i = 0; i < 32; ++i) m = fmaxf(m, __uint_as_float(v[q][i]));
+                if (m >= bound && a_valid) {
+                    // side path: which columns reach the bound, then the exact weight from
+                    // the bit-packed rows, then the key
+                    const int a_kh = B.a_half ? P.k2 : P.k1, b_kh = B.a_half ? P.k1 : P.k2;
+                    uint32_t x[NW];
 #pragma unroll
-                        for (int q = 0; q < NW; ++q) x[q] = B.a_tab[a_e * NW + q];
+                    for (int w = 0; w < NW; ++w) x[w] = B.a_tab[a_e * NW + w];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        uint32_t neg = 0;
+#pragma unroll
+                        for (int i = 0; i < 32; ++i) neg |= (__uint_as_float(v[q][i]) >= bound ? 1u : 0u) << i;
                         while (neg) {
-                            const int i = __ffsll((long long)neg) - 1;
+                            const int i = __ffs(neg) - 1;
                             neg &= neg - 1;
-                            const unsigned long long b_e = bt * kGN + (unsigned long long)(col0 + c + i);
+                            const unsigned long long b_e = bt * kGN + (unsigned long long)(col0 + 32 * q + i);
                             if (b_e >= B.b_n) continue;
                             int w = 0;
 #pragma unroll
-                            for (int q = 0; q < NW; ++q) w += __popc(x[q] ^ B.b_tab[b_e * NW + q]);
+                            for (int z = 0; z < NW; ++z) w += __popc(x[z] ^ B.b_tab[b_e * NW + z]);
                             const int weight = w + P.base;
                             if (weight > (int)(*(volatile unsigned int *)P.U)) continue;
                             const uint32_t am = unrank_colex(s_bn, a_kh, (int)B.a_t, (uint32_t)a_e);
@@ -384,7 +340,7 @@ __global__ void __launch_bounds__(kGramThreads, 1) gram_kernel(const __grid_cons
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    if (warp == 13) tmem_dealloc(tmem, 512);
+    if (warp == 10) tmem_dealloc(tmem, 512);
 }
 
 // at least 120 KB so that two CTAs never share an SM (each allocates all 512 TMEM columns)
@@ -425,31 +381,19 @@ __global__ void subset_table_kernel(const uint32_t *rows, int kh, int t, unsigne
     }
 }
 
-// B tiles of a packed table: row e of tile e / kGN is the expanded y (-2.0 per set bit)
-// with scales 64, 8, 1 against the A side's digits and the digits of wt(y) against the
-// A side's scales; rows past `count` are padding (zero bits, weight 1023: never a
-// candidate).
+// B tiles of a packed table: row e of tile e / kGN is the sign row of entry e (write_row
+// with the code's n_bits); rows past `count` are padding (zero bytes).
 template <int NW>
 __global__ void expand_table_kernel(const uint32_t *packed, unsigned long long count, unsigned long long rows,
-                                    uint8_t *out) {
+                                    int n_bits, uint8_t *out) {
     constexpr int KA = gram_ka(NW);
     for (unsigned long long e = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; e < rows;
          e += (unsigned long long)gridDim.x * blockDim.x) {
         uint32_t y[NW];
-        int wy = 1023;
-        if (e < count) {
-            wy = 0;
 #pragma unroll
-            for (int w = 0; w < NW; ++w) {
-                y[w] = packed[e * NW + w];
-                wy += __popc(y[w]);
-            }
-        } else {
-#pragma unroll
-            for (int w = 0; w < NW; ++w) y[w] = 0;
-        }
-        write_row<NW>(out + (e / kGN) * (unsigned long long)(kGN * KA), (int)(e % kGN), y, kE4M3MinusTwo, kScale3,
-                      digits3(wy));
+        for (int w = 0; w < NW; ++w) y[w] = e < count ? packed[e * NW + w] : 0u;
+        write_row<NW>(out + (e / kGN) * (unsigned long long)(kGN * KA), (int)(e % kGN), y,
+                      e < count ? n_bits : 0);
     }
 }
 
@@ -465,14 +409,14 @@ cudaError_t table_launch_nw(const uint32_t *rows, int kh, int t, unsigned long l
 }
 
 template <int NW>
-cudaError_t expand_launch_nw(const uint32_t *packed, unsigned long long count, uint8_t *out, int sm_count,
-                             cudaStream_t stream) {
+cudaError_t expand_launch_nw(const uint32_t *packed, unsigned long long count, int n_bits, uint8_t *out,
+                             int sm_count, cudaStream_t stream) {
     const unsigned long long rows = (count + kGN - 1) / kGN * kGN;
     unsigned long long grid = (rows + 255) / 256;
     const unsigned long long cap = (unsigned long long)sm_count * 8;
     if (grid > cap) grid = cap;
     if (grid < 1) grid = 1;
-    expand_table_kernel<NW><<<(unsigned int)grid, 256, 0, stream>>>(packed, count, rows, out);
+    expand_table_kernel<NW><<<(unsigned int)grid, 256, 0, stream>>>(packed, count, rows, n_bits, out);
     return cudaGetLastError();
 }
 
@@ -496,16 +440,16 @@ size_t gram_expanded_bytes(int nwords, unsigned long long count) {
     return (size_t)((count + kGN - 1) / kGN) * (size_t)kGN * (size_t)gram_ka(nwords);
 }
 
-cudaError_t launch_expand_table(const uint32_t *packed, int nwords, unsigned long long count, uint8_t *out,
-                                int sm_count, cudaStream_t stream) {
+cudaError_t launch_expand_table(const uint32_t *packed, int nwords, unsigned long long count, int n_bits,
+                                uint8_t *out, int sm_count, cudaStream_t stream) {
     switch (nwords) {
-        case 1: return expand_launch_nw<1>(packed, count, out, sm_count, stream);
-        case 2: return expand_launch_nw<2>(packed, count, out, sm_count, stream);
-        case 3: return expand_launch_nw<3>(packed, count, out, sm_count, stream);
-        case 4: return expand_launch_nw<4>(packed, count, out, sm_count, stream);
-        case 5: return expand_launch_nw<5>(packed, count, out, sm_count, stream);
-        case 6: return expand_launch_nw<6>(packed, count, out, sm_count, stream);
-        case 7: return expand_launch_nw<7>(packed, count, out, sm_count, stream);
+        case 1: return expand_launch_nw<1>(packed, count, n_bits, out, sm_count, stream);
+        case 2: return expand_launch_nw<2>(packed, count, n_bits, out, sm_count, stream);
+        case 3: return expand_launch_nw<3>(packed, count, n_bits, out, sm_count, stream);
+        case 4: return expand_launch_nw<4>(packed, count, n_bits, out, sm_count, stream);
+        case 5: return expand_launch_nw<5>(packed, count, n_bits, out, sm_count, stream);
+        case 6: return expand_launch_nw<6>(packed, count, n_bits, out, sm_count, stream);
+        case 7: return expand_launch_nw<7>(packed, count, n_bits, out, sm_count, stream);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -94,8 +94,8 @@ cudaError_t launch_subset_table(const uint32_t *rows, int nwords, int kh, int t,
                                 uint32_t *out, int sm_count, cudaStream_t stream);
 // bytes of the expanded operand tiles of a packed table of `count` entries
 size_t gram_expanded_bytes(int nwords, unsigned long long count);
-cudaError_t launch_expand_table(const uint32_t *packed, int nwords, unsigned long long count, uint8_t *out,
-                                int sm_count, cudaStream_t stream);
+cudaError_t launch_expand_table(const uint32_t *packed, int nwords, unsigned long long count, int n_bits,
+                                uint8_t *out, int sm_count, cudaStream_t stream);
 // A unit: blocks with tables on the tensor cores, the others on the ALU kernel
 // (tabs may be null: every block on the ALU kernel).
 cudaError_t launch_unit_split(const EnumParams &p, int nwords, int group, bool hist_mode, int sm_count,
