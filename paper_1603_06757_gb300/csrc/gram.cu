@@ -8,7 +8,8 @@
 // so the weights of a whole 128 x 256 tile of codewords follow from a Gram matrix: a
 // dense contraction over the n_bits columns.  Operand rows are the signs as E4M3 bytes
 // (+1.0 / -1.0; the B side has zero bytes past n_bits), one kind::f8f6f4 MMA chain
-// with f32 accumulation gives every acc = n_bits - 2 wt(x ^ y) exactly, and a codeword
+// with f16 accumulation gives every acc = n_bits - 2 wt(x ^ y) exactly (every partial
+// sum is an integer of magnitude <= n_bits <= 224), and a codeword
 // is a candidate iff acc >= n_bits - 2 thr (thr = largest reduced weight still a
 // candidate).  The epilogue takes the maximum of the accumulators it reads from TMEM;
 // only a maximum at or above that bound sends a lane to the side path, which recomputes
@@ -21,6 +22,8 @@
 // shared memory as one bulk copy; A tiles are expanded per work unit from the
 // bit-packed subset sums.
 //
+#include <cuda_fp16.h>
+
 #include <cstdint>
 
 #include "combinatorics.cuh"
@@ -224,7 +227,7 @@ __global__ void __launch_bounds__(kGramThreads, 1) gram_kernel(const __grid_cons
     } else if (warp == 10) {
         // ---------------- MMA issue ----------------
         if (lane == 0) {
-            const uint32_t idesc = idesc_f8f6f4_e4m3_f32(kGM, kGN);
+            const uint32_t idesc = idesc_f8f6f4_e4m3_f16(kGM, kGN);
             const uint32_t sbo = (uint32_t)(KA / 16) * 128u;
             unsigned long long t = 0, u = 0;
             for (unsigned long long wu = blockIdx.x; wu < P.total_wu && !*s_abort; wu += gridDim.x, ++u) {
@@ -282,20 +285,17 @@ __global__ void __launch_bounds__(kGramThreads, 1) gram_kernel(const __grid_cons
                 }
                 tc_fence_after();
                 const uint32_t base = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(ab * kGN + col0);
-                uint32_t v[4][32];
-                tmem_ld32_issue(base, v[0]);
-                tmem_ld32_issue(base + 32u, v[1]);
-                tmem_ld32_issue(base + 64u, v[2]);
-                tmem_ld32_issue(base + 96u, v[3]);
+                uint32_t v[2][32];  // 128 f16 accumulators, two per register
+                tmem_ld64_pack16_issue(base, v[0]);
+                tmem_ld64_pack16_issue(base + 64u, v[1]);
                 tmem_wait_ld(v[0]);
                 tmem_regs_ready(v[1]);
-                tmem_regs_ready(v[2]);
-                tmem_regs_ready(v[3]);
-                float m = __uint_as_float(v[0][0]);
+                __half2 m2 = *reinterpret_cast<const __half2 *>(&v[0][0]);
 #pragma unroll
-                for (int q = 0; q < 4; ++q)
+                for (int q = 0; q < 2; ++q)
 #pragma unroll
-                    for (int i = 0; i < 32; ++i) m = fmaxf(m, __uint_as_float(v[q][i]));
+                    for (int i = 0; i < 32; ++i) m2 = __hmax2(m2, *reinterpret_cast<const __half2 *>(&v[q][i]));
+                const float m = fmaxf(__low2float(m2), __high2float(m2));
                 if (m >= bound && a_valid) {
                     // side path: which columns reach the bound, then the exact weight from
                     // the bit-packed rows, then the key
@@ -304,14 +304,18 @@ __global__ void __launch_bounds__(kGramThreads, 1) gram_kernel(const __grid_cons
 #pragma unroll
                     for (int w = 0; w < NW; ++w) x[w] = B.a_tab[a_e * NW + w];
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        uint32_t neg = 0;
+                    for (int q = 0; q < 2; ++q) {
+                        unsigned long long neg = 0;
 #pragma unroll
-                        for (int i = 0; i < 32; ++i) neg |= (__uint_as_float(v[q][i]) >= bound ? 1u : 0u) << i;
+                        for (int i = 0; i < 32; ++i) {
+                            const __half2 h = *reinterpret_cast<const __half2 *>(&v[q][i]);
+                            neg |= (unsigned long long)(__low2float(h) >= bound ? 1u : 0u) << (2 * i);
+                            neg |= (unsigned long long)(__high2float(h) >= bound ? 1u : 0u) << (2 * i + 1);
+                        }
                         while (neg) {
-                            const int i = __ffs(neg) - 1;
+                            const int i = __ffsll((long long)neg) - 1;
                             neg &= neg - 1;
-                            const unsigned long long b_e = bt * kGN + (unsigned long long)(col0 + 32 * q + i);
+                            const unsigned long long b_e = bt * kGN + (unsigned long long)(col0 + 64 * q + i);
                             if (b_e >= B.b_n) continue;
                             int w = 0;
 #pragma unroll
