@@ -46,9 +46,12 @@ POPC_PER_CLK_SM = 16
 # instructions); the LOP3 probe reaches ~112 because LOP3 also issues to the FMA pipe
 ALU_PER_CLK_SM = 64
 L2_FLUSH_BYTES = 256 << 20
-# DRAM bytes (read + write) per launch of the dominant enumerator kernel, from the ncu
-# capture summarised in profiles/ (None until captured for the current kernel)
-TRAFFIC_PER_LAUNCH = {"192x64": 555264}  # enum_unit_kernel<4,5,0>, level 11 (profiles/enum_unit_192x64_g11_v5.md)
+# dense fp8 / bf16 tensor throughput, nominal (2.25 and 4.5 PFLOP/s per GB300)
+FP8_PER_BF16 = 2.0
+# DRAM bytes (read + write) per launch of the dominant kernel (the tensor-core
+# enumerator), from the ncu capture summarised in profiles/ (None until captured for
+# the current kernel)
+TRAFFIC_PER_LAUNCH = {}
 
 
 def _env_int(name, default):
@@ -235,6 +238,9 @@ def run_ours(args):
     kernel_ms = 0.0
     launches = 0
     combos = 0
+    tc_ms = 0.0
+    tc_launches = 0
+    tc_combos = 0
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
@@ -246,6 +252,9 @@ def run_ours(args):
         kernel_ms += res["kernel_ms"]
         launches += res["launches"]
         combos += res["total_combos"]
+        tc_ms += res["tc_ms"]
+        tc_launches += res["tc_launches"]
+        tc_combos += res["tc_combos"]
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
@@ -269,24 +278,52 @@ def run_ours(args):
     e2e_sec = time.perf_counter() - t0
     e2e_value = weak_value(world, e2e_cw, max_over_ranks(e2e_sec, dist, "cuda"))
 
-    # ---- roofline of the enumerator kernel ----
-    # Every codeword needs its stored words combined once (one logic op per 32-bit word,
-    # ALU pipe, 64 lanes/clk/SM) and at least one popcount (XU pipe, 16/clk/SM): peak =
-    # SMs x f_max x min(16 / 1, 64 / nwords) codewords/s.  The exact-count roofline
-    # (nwords popcounts per codeword) is reported beside it.
+    # ---- roofline of the dominant kernel ----
+    # The tensor-core enumerator contracts n_bits sign columns per codeword: 2 n_bits
+    # flops (fp8 operands) per codeword, timed per launch by the library's CUDA events on
+    # the launching stream.  Peak: the measured bf16 tensor throughput x the nominal
+    # fp8 / bf16 ratio.  The ALU enumerator (the small product blocks and levels) is
+    # reported beside it against its own pipe roofline.
     info = api.device_info()
     peaks = _peaks()
     sm_mhz = float(peaks.get("sm_max_mhz") or info["max_sm_clock_khz"] / 1e3)
     part = api.partition_host(G, n)
-    nwords = max(1, math.ceil((n - k) / 32)) if all(int(r) == k for r in part["ranks"]) else math.ceil(n / 32)
-    per_clk = min(POPC_PER_CLK_SM / 1.0, ALU_PER_CLK_SM / nwords)
-    peak = info["sm_count"] * sm_mhz * 1e6 * per_clk
-    exact_peak = info["sm_count"] * sm_mhz * 1e6 * POPC_PER_CLK_SM / nwords
-    achieved = combos / (kernel_ms / 1e3)
+    full = all(int(r) == k for r in part["ranks"])
+    n_bits = (n - k) if full else n
+    nwords = max(1, math.ceil(n_bits / 32))
     try:
-        mb = {w: api.microbench(w)["per_clock_per_sm"] for w in ("popc", "lop3", "step4", "step4_or2", "step4_or4")}
+        mb = {w: api.microbench(w)["per_clock_per_sm"]
+              for w in ("popc", "lop3", "step4", "step4_or2", "step4_or4", "mma")}
     except Exception:  # noqa: BLE001
         mb = None
+    per_clk = min(POPC_PER_CLK_SM / 1.0, ALU_PER_CLK_SM / nwords)
+    alu_peak = info["sm_count"] * sm_mhz * 1e6 * per_clk
+    alu_ms = kernel_ms - tc_ms
+    alu_achieved = (combos - tc_combos) / (alu_ms / 1e3) if alu_ms > 0 else None
+    alu_part = {"bound": "alu", "achieved": alu_achieved / 1e9 if alu_achieved else None, "peak": alu_peak / 1e9,
+                "unit": "Gcodewords/s", "frac": alu_achieved / alu_peak if alu_achieved else None,
+                "ms_per_step": alu_ms / args.steps, "codewords_per_step": (combos - tc_combos) // args.steps,
+                "peak_basis": f"{info['sm_count']} SMs x {sm_mhz:.0f} MHz x min({POPC_PER_CLK_SM} POPC, "
+                              f"{ALU_PER_CLK_SM} ALU / {nwords} words) per clk per SM"}
+    if tc_launches:
+        bf16 = peaks.get("bf16_tflops")
+        bf16_s = peaks.get("bf16_tflops_sustained")
+        basis = "of measured" if bf16 else "of fallback"
+        peak = (bf16 or 1900.0) * FP8_PER_BF16
+        achieved = 2.0 * n_bits * tc_combos / (tc_ms / 1e3) / 1e12
+        mma_peak = (2.0 * mb["mma"] * info["sm_count"] * sm_mhz * 1e6 / 1e12) if mb else None
+        roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                    "traffic": TRAFFIC_PER_LAUNCH.get(args.workload),
+                    "kernel": f"gram_kernel<{nwords}> (tcgen05 kind::f8f6f4, E4M3 sign operands, f16 accumulators)",
+                    "peak_basis": f"bf16 {bf16 or 1900.0} TFLOP/s x {FP8_PER_BF16} (nominal fp8/bf16 dense), {basis}",
+                    "frac_of_sustained": achieved / (bf16_s * FP8_PER_BF16) if bf16_s else None,
+                    "mma_probe_peak": mma_peak, "frac_of_mma_probe": achieved / mma_peak if mma_peak else None,
+                    "flops_per_codeword": 2 * n_bits, "launches_per_step": tc_launches / args.steps,
+                    "ms_per_launch": tc_ms / tc_launches, "codewords_per_launch": tc_combos / tc_launches,
+                    "share_of_kernel_time": tc_ms / kernel_ms if kernel_ms > 0 else None,
+                    "alu_kernel": alu_part, "microbench_per_clk_sm": mb}
+    else:
+        roofline = dict(alu_part, traffic=None, microbench_per_clk_sm=mb)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -300,17 +337,12 @@ def run_ours(args):
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms_max / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None, "dtype": "fp8+u32", "data": "synthetic",
             "config": {"workload": WORKLOADS[args.workload], "n": n, "k": k, "seed": seed, "d": res["d"],
                        "g_final": res["g_final"], "ranks": res["ranks"], "codewords_per_step": res["total_combos"],
                        "launches_per_step": res["launches"], "parallelism": f"replicas x{world}",
                        "l2": "flushed (256 MiB write) before every timed step; inputs ~2 KB"},
-            "roofline": {"bound": "alu", "achieved": achieved / 1e9, "peak": peak / 1e9, "unit": "Gcodewords/s",
-                         "frac": achieved / peak, "traffic": TRAFFIC_PER_LAUNCH.get(args.workload),
-                         "peak_basis": f"{info['sm_count']} SMs x {sm_mhz:.0f} MHz x min({POPC_PER_CLK_SM} POPC, "
-                                       f"{ALU_PER_CLK_SM} ALU / {nwords} words) per clk per SM",
-                         "exact_count_peak": exact_peak / 1e9, "exact_count_frac": achieved / exact_peak,
-                         "kernel_ms_per_step": kernel_ms / args.steps, "microbench_per_clk_sm": mb},
+            "roofline": roofline,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": launches,

@@ -100,7 +100,7 @@ typedef struct {
     int32_t g_final, j_final; /* last unit enumerated */
     int32_t m;                /* number of information sets */
     int32_t L_final, U_final;
-    int32_t launches;         /* enumerator kernel launches */
+    int32_t launches;         /* kernel launches (enumerators and the tensor-core enumerator's tables) */
     int32_t ranks[MDIST_MAX_SETS];
     uint64_t combos[MDIST_MAX_K + 1][MDIST_MAX_SETS]; /* combinations enumerated per (g, j) */
     uint64_t total_combos;
@@ -108,6 +108,10 @@ typedef struct {
     double kernel_ms;         /* summed CUDA-event time of the enumerator launches */
     uint64_t h2d_bytes;       /* host-to-device bytes copied by mdist_prepare and the run */
     uint64_t d2h_bytes;       /* device-to-host bytes copied by the run */
+    double tc_ms;             /* summed CUDA-event time of the tensor-core enumerator launches */
+    int32_t tc_launches;      /* tensor-core enumerator launches */
+    int32_t reserved;
+    uint64_t tc_combos;       /* combinations those launches enumerated */
 } mdist_stats;
 
 typedef struct mdist_code mdist_code; /* opaque */
@@ -288,10 +292,13 @@ void mdist_mlp_free(mdist_mlp *mlp);
 /* Instruction-throughput probe on the current device, for roofline arithmetic:
  * which = 0: 32-bit POPC, 1: 3-input XOR (LOP3), 2: enumerator inner step (XOR + POPC
  * over 4 words, sum, running min), 3 / 4: the lower-bound step of filter groups of 2 /
- * 4 words (threshold never reached), operands in registers.  One 1024-thread CTA
- * per SM, `iters` loop trips; *ops_per_clock_per_sm = operations (or codeword steps)
- * retired per SM per clock (clock64), *seconds = launch time.  Allocates 64 B + 8 B
- * per SM of device memory for its duration. */
+ * 4 words (threshold never reached), operands in registers; one 1024-thread CTA
+ * per SM, `iters` loop trips.  which = 5 / 6 / 7: tcgen05 kind::f8f6f4 MMAs (E4M3,
+ * f16 accumulator, 128 x 256 x 32) issued back to back by one thread per SM on
+ * shared-memory operands in the no-swizzle / 128-byte swizzle / 32-byte swizzle
+ * layout, 4 MMAs per loop trip.  *ops_per_clock_per_sm = operations (codeword steps;
+ * multiply-adds for the MMA probes) retired per SM per clock (clock64), *seconds =
+ * launch time.  Allocates 64 B + 8 B per SM of device memory for its duration. */
 int mdist_microbench(int which, int iters, double *ops_per_clock_per_sm, double *seconds);
 
 /* ---- one unit without any device allocation ---------------------------------------- */

@@ -74,6 +74,10 @@ class Stats(ctypes.Structure):
         ("kernel_ms", ctypes.c_double),
         ("h2d_bytes", ctypes.c_uint64),
         ("d2h_bytes", ctypes.c_uint64),
+        ("tc_ms", ctypes.c_double),
+        ("tc_launches", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
+        ("tc_combos", ctypes.c_uint64),
     ]
 
 

@@ -217,6 +217,9 @@ def _result_dict(d, wit, msg, key, st) -> dict:
         "kernel_ms": float(st.kernel_ms),
         "h2d_bytes": int(st.h2d_bytes),
         "d2h_bytes": int(st.d2h_bytes),
+        "tc_ms": float(st.tc_ms),
+        "tc_launches": int(st.tc_launches),
+        "tc_combos": int(st.tc_combos),
     }
 
 
@@ -337,8 +340,11 @@ def partition_host(G, n: int, max_sets: int = 0) -> dict:
 
 
 def microbench(which: str, iters: int = 20000) -> dict:
-    """Per-SM-per-clock throughput of 'popc', 'lop3' or 'step4' (see include/mdist.h)."""
-    idx = {"popc": 0, "lop3": 1, "step4": 2, "step4_or2": 3, "step4_or4": 4}[which]
+    """Per-SM-per-clock throughput of 'popc', 'lop3', 'step4', 'step4_or2', 'step4_or4' or
+    of the fp8 tensor-core MMA ('mma' no swizzle, 'mma_sw128', 'mma_sw32': multiply-adds)
+    (see include/mdist.h)."""
+    idx = {"popc": 0, "lop3": 1, "step4": 2, "step4_or2": 3, "step4_or4": 4, "mma": 5, "mma_sw128": 6,
+           "mma_sw32": 7}[which]
     v = ctypes.c_double()
     s = ctypes.c_double()
     L.check(L.lib().mdist_microbench(idx, int(iters), ctypes.byref(v), ctypes.byref(s)), "mdist_microbench")

@@ -29,6 +29,9 @@ struct RunState {
     int g_last = 0, j_last = -1;
     int launches = 0;
     double kernel_ms = 0.0;
+    double tc_ms = 0.0;
+    int tc_launches = 0;
+    uint64_t tc_combos = 0;
     double seconds = 0.0;
     uint64_t h2d_bytes = 0, d2h_bytes = 0;
     int last_group = 0;
@@ -56,6 +59,7 @@ struct mdist_code {
     UnitSlot *h_slot = nullptr;          // pinned
     unsigned long long *d_hist = nullptr;// n+1 bins, on demand
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    std::vector<cudaEvent_t> tc_ev;      // event pairs around tensor-core launches, one pair per unit of a wave
     uint64_t rows_bytes = 0;             // Gamma rows copied to the device by mdist_prepare
     int wave_cap = 0;                    // units a wave can hold: m * (k + 1)
     UnitSlot *d_wave = nullptr;          // [wave_cap] per-unit slots + 1 threshold word after them
@@ -101,6 +105,16 @@ void reset_state(mdist_code *c) {
     c->st.L = 1;
 }
 
+// At least `pairs` event pairs for timing tensor-core launches.
+bool tc_events(mdist_code *c, int pairs) {
+    while (c->tc_ev.size() < 2 * (size_t)pairs) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) return false;
+        c->tc_ev.push_back(e);
+    }
+    return true;
+}
+
 // Device bytes a code may hold in subset-sum tables; blocks whose tables would not fit
 // stay on the ALU enumerator.
 constexpr size_t kTableBudget = 16ull << 30;
@@ -142,6 +156,7 @@ int subset_table(mdist_code *c, int j, int half, int t, unsigned long long count
     }
     c->tabs[key] = d;
     c->tab_bytes += bytes;
+    c->st.launches += 1;
     *out = d;
     return MDIST_OK;
 }
@@ -206,8 +221,12 @@ int run_unit(mdist_code *c, int g, int j, int U_thr, bool hist_mode, bool *found
         const int rc = gram_tables(c, j, p, tabs);
         if (rc != MDIST_OK) return rc;
     }
+    if (!tc_events(c, 1)) return MDIST_ECUDA;
+    unsigned long long tc_combos = 0;
+    int kernels = 0;
     if (mdist::launch_unit_split(p, dr.nwords, group, hist_mode, c->sm_count, c->opt.blocks_per_sm,
-                                 hist_mode ? nullptr : tabs, c->stream) != cudaSuccess)
+                                 hist_mode ? nullptr : tabs, c->stream, c->tc_ev[0], c->tc_ev[1], &tc_combos,
+                                 &kernels) != cudaSuccess)
         return MDIST_ECUDA;
     if (cudaEventRecord(c->ev1, c->stream) != cudaSuccess) return MDIST_ECUDA;
     if (cudaMemcpyAsync(c->h_slot, c->d_slot, sizeof(UnitSlot), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess)
@@ -216,7 +235,12 @@ int run_unit(mdist_code *c, int g, int j, int U_thr, bool hist_mode, bool *found
     c->st.d2h_bytes += sizeof(UnitSlot);
     float ms = 0.f;
     if (cudaEventElapsedTime(&ms, c->ev0, c->ev1) == cudaSuccess) c->st.kernel_ms += ms;
-    c->st.launches += 1;
+    c->st.launches += kernels;
+    if (tc_combos && cudaEventElapsedTime(&ms, c->tc_ev[0], c->tc_ev[1]) == cudaSuccess) {
+        c->st.tc_ms += ms;
+        c->st.tc_launches += 1;
+        c->st.tc_combos += tc_combos;
+    }
     if (c->h_slot->status) return MDIST_ETIMEOUT;
     const unsigned long long key = c->h_slot->key;
     *found = key != mdist::kNoKey;
@@ -279,6 +303,7 @@ void mdist_free(mdist_code *c) {
     dev_release(c, c->d_wave);
     if (c->h_wave) cudaFreeHost(c->h_wave);
     if (c->h_slot) cudaFreeHost(c->h_slot);
+    for (cudaEvent_t e : c->tc_ev) cudaEventDestroy(e);
     if (c->ev0) cudaEventDestroy(c->ev0);
     if (c->ev1) cudaEventDestroy(c->ev1);
     delete c;
@@ -458,6 +483,9 @@ static int run_wave(mdist_code *c, int g_hi, int max_units, int *units_done) {
             cudaSuccess)
         return MDIST_ECUDA;
     s.h2d_bytes += sizeof(UnitSlot) * ((size_t)n_units + 1);
+    if (!tc_events(c, n_units)) return MDIST_ECUDA;
+    std::vector<unsigned long long> tc_combos((size_t)n_units, 0);
+    int launched = 0, kernels = 0;
     if (cudaEventRecord(c->ev0, c->stream) != cudaSuccess) return MDIST_ECUDA;
     for (int u = 0; u < n_units; ++u) {
         const int g = list[(size_t)u].g, j = list[(size_t)u].j;
@@ -478,8 +506,10 @@ static int run_wave(mdist_code *c, int g_hi, int max_units, int *units_done) {
         const int rc = gram_tables(c, j, q, tabs);
         if (rc != MDIST_OK) return rc;
         if (mdist::launch_unit_split(q, dr.nwords, group, false, c->sm_count, c->opt.blocks_per_sm, tabs,
-                                     c->stream) != cudaSuccess)
+                                     c->stream, c->tc_ev[2 * (size_t)u], c->tc_ev[2 * (size_t)u + 1],
+                                     &tc_combos[(size_t)u], &kernels) != cudaSuccess)
             return MDIST_ECUDA;
+        launched += kernels;
     }
     if (cudaEventRecord(c->ev1, c->stream) != cudaSuccess) return MDIST_ECUDA;
     if (cudaMemcpyAsync(c->h_wave, c->d_wave, sizeof(UnitSlot) * (size_t)n_units, cudaMemcpyDeviceToHost, c->stream) !=
@@ -489,7 +519,14 @@ static int run_wave(mdist_code *c, int g_hi, int max_units, int *units_done) {
     s.d2h_bytes += sizeof(UnitSlot) * (size_t)n_units;
     float ms = 0.f;
     if (cudaEventElapsedTime(&ms, c->ev0, c->ev1) == cudaSuccess) s.kernel_ms += ms;
-    s.launches += n_units;
+    s.launches += launched;
+    for (int u = 0; u < n_units; ++u)
+        if (tc_combos[(size_t)u] &&
+            cudaEventElapsedTime(&ms, c->tc_ev[2 * (size_t)u], c->tc_ev[2 * (size_t)u + 1]) == cudaSuccess) {
+            s.tc_ms += ms;
+            s.tc_launches += 1;
+            s.tc_combos += tc_combos[(size_t)u];
+        }
     for (int u = 0; u < n_units; ++u)
         if (c->h_wave[u].status) return MDIST_ETIMEOUT;
     // fold in (g, j) order
@@ -592,6 +629,9 @@ int mdist_result(const mdist_code *c, int *d, uint64_t *witness, uint64_t *messa
         stats->total_combos = tot;
         stats->seconds = s.seconds;
         stats->kernel_ms = s.kernel_ms;
+        stats->tc_ms = s.tc_ms;
+        stats->tc_launches = s.tc_launches;
+        stats->tc_combos = s.tc_combos;
         stats->h2d_bytes = s.h2d_bytes + c->rows_bytes;
         stats->d2h_bytes = s.d2h_bytes;
     }

@@ -150,19 +150,27 @@ size_t enum_smem_bytes(int k, int nwords) {
 // the others on the ALU kernel.  Both launches share the threshold word, key, count and
 // status of `p`.
 cudaError_t launch_unit_split(const EnumParams &p, int nwords, int group, bool hist_mode, int sm_count,
-                              int blocks_per_sm, const GramTables *tabs, cudaStream_t stream) {
+                              int blocks_per_sm, const GramTables *tabs, cudaStream_t stream, cudaEvent_t tc_ev0,
+                              cudaEvent_t tc_ev1, unsigned long long *tc_combos, int *kernels) {
     bool tc[kMaxBlocks] = {};
     int ntc = 0;
+    unsigned long long combos = 0;
     if (!hist_mode && tabs)
         for (int b = 0; b < p.nblocks; ++b)
             if (tabs[b].lane && tabs[b].walk && tabs[b].walk_exp) {
                 tc[b] = true;
                 ++ntc;
+                combos += p.blocks[b].lane_n * p.blocks[b].walk_n;
             }
+    if (tc_combos) *tc_combos = combos;
+    if (kernels) *kernels = 0;
     if (ntc) {
+        if (tc_ev0 && cudaEventRecord(tc_ev0, stream) != cudaSuccess) return cudaErrorUnknown;
         const cudaError_t e = launch_gram_unit(p, tabs, p.U, p.slot, reinterpret_cast<int *>(&p.slot->status),
                                                sm_count, stream);
         if (e != cudaSuccess) return e;
+        if (tc_ev1 && cudaEventRecord(tc_ev1, stream) != cudaSuccess) return cudaErrorUnknown;
+        if (kernels) *kernels += 1;
     }
     if (ntc == p.nblocks) return cudaSuccess;
     EnumParams q = p;
@@ -178,7 +186,9 @@ cudaError_t launch_unit_split(const EnumParams &p, int nwords, int group, bool h
     }
     q.nblocks = nb;
     q.total_tiles = tiles;
-    return launch_enum_unit(q, nwords, group, hist_mode, sm_count, blocks_per_sm, stream);
+    const cudaError_t e = launch_enum_unit(q, nwords, group, hist_mode, sm_count, blocks_per_sm, stream);
+    if (e == cudaSuccess && kernels) *kernels += 1;
+    return e;
 }
 
 cudaError_t launch_enum_unit(const EnumParams &p, int nwords, int group, bool hist_mode, int sm_count,

@@ -43,7 +43,7 @@ namespace {
 
 constexpr int kGM = 128;               // accumulator rows (A tile)
 constexpr int kGN = 256;               // accumulator columns (B tile)
-constexpr int kTilesPerUnit = 16;      // B tiles per work unit
+constexpr int kTilesPerUnit = 64;      // B tiles per work unit
 constexpr int kGramThreads = 352;      // 8 epilogue warps, builder warp, producer warp, MMA warp
 constexpr int kSmemOperandBudget = 200 << 10;
 
@@ -265,6 +265,7 @@ __global__ void __launch_bounds__(kGramThreads, 1) gram_kernel(const __grid_cons
         const int row = 32 * (warp & 3) + lane;  // TMEM lane = A row
         const int col0 = 128 * (warp >> 2);      // first accumulator column of this warp
         unsigned long long t = 0, cnt = 0;
+        unsigned int u_next = *(volatile unsigned int *)P.U;
         for (unsigned long long wu = blockIdx.x; wu < P.total_wu && !*s_abort; wu += gridDim.x) {
             int b;
             unsigned long long a_tile, bt0, bt1;
@@ -275,8 +276,9 @@ __global__ void __launch_bounds__(kGramThreads, 1) gram_kernel(const __grid_cons
             const unsigned long long a_valid_rows = B.a_n - a_tile * kGM < (unsigned long long)kGM
                                                         ? B.a_n - a_tile * kGM
                                                         : (unsigned long long)kGM;
-            // candidates: acc >= n_bits - 2 thr, with the threshold of the unit's start
-            const float bound = (float)(P.n_bits - 2 * ((int)(*(volatile unsigned int *)P.U) - P.base));
+            // candidates: acc >= n_bits - 2 thr, with a threshold read one unit ahead
+            const float bound = (float)(P.n_bits - 2 * ((int)u_next - P.base));
+            u_next = *(volatile unsigned int *)P.U;
             for (unsigned long long bt = bt0; bt < bt1; ++bt, ++t) {
                 const int ab = (int)(t & 1);
                 if (!mbar_wait(bar(ACC_FULL + ab), (uint32_t)((t >> 1) & 1), P.max_wait)) {

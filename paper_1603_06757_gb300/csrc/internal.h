@@ -97,9 +97,14 @@ size_t gram_expanded_bytes(int nwords, unsigned long long count);
 cudaError_t launch_expand_table(const uint32_t *packed, int nwords, unsigned long long count, int n_bits,
                                 uint8_t *out, int sm_count, cudaStream_t stream);
 // A unit: blocks with tables on the tensor cores, the others on the ALU kernel
-// (tabs may be null: every block on the ALU kernel).
+// (tabs may be null: every block on the ALU kernel).  When the tensor-core kernel is
+// launched and tc_ev0 / tc_ev1 are given they are recorded around it, *tc_combos (may
+// be null) receives the combinations it enumerates (else 0) and *kernels (may be null)
+// the number of kernels launched (0 to 2).
 cudaError_t launch_unit_split(const EnumParams &p, int nwords, int group, bool hist_mode, int sm_count,
-                              int blocks_per_sm, const GramTables *tabs, cudaStream_t stream);
+                              int blocks_per_sm, const GramTables *tabs, cudaStream_t stream,
+                              cudaEvent_t tc_ev0 = nullptr, cudaEvent_t tc_ev1 = nullptr,
+                              unsigned long long *tc_combos = nullptr, int *kernels = nullptr);
 
 // Filter variant for a unit: 0 (exact count for every codeword) or the OR-group size
 // 2, 3, 4 whose expected cost is least for this row width and threshold.
