@@ -251,8 +251,7 @@ __global__ void __launch_bounds__(kGramThreads, 1) gram_kernel(const __grid_cons
                     for (int ks = 0; ks < KSTEPS; ++ks)
                         mma_f8f6f4(d, smem_desc(a0 + ks * 256, 128, sbo), smem_desc(b0 + ks * 256, 128, sbo), idesc,
                                    ks > 0 ? 1u : 0u);
-                    mma_commit(bar(B_EMPTY + s));   // operand stage free again
-                    mma_commit(bar(ACC_FULL + ab));  // accumulator ready
+                    mma_commit(bar(ACC_FULL + ab));  // accumulator ready, B stage s read
                 }
                 mma_commit(bar(A_EMPTY + st));  // A tile free again
                 if (!ok) { fail(); break; }
@@ -286,6 +285,9 @@ __global__ void __launch_bounds__(kGramThreads, 1) gram_kernel(const __grid_cons
                     break;
                 }
                 tc_fence_after();
+                // MMA t has completed: its B stage is free (released here rather than by a
+                // commit, so that no thread but the epilogue waits on commit-driven barriers)
+                if (tid == 0) mbar_arrive(bar(B_EMPTY + (int)(t % S)));
                 const uint32_t base = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(ab * kGN + col0);
                 uint32_t v[2][32];  // 128 f16 accumulators, two per register
                 tmem_ld64_pack16_issue(base, v[0]);
