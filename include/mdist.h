@@ -82,8 +82,12 @@ typedef struct {
                                 synchronisation).  Sizing only: results never depend on it. */
     int tensor_cores;        /* product blocks on the tensor cores (tcgen05 Gram-matrix
                                 enumerator, stored rows of at most 7 words): 0 = blocks
-                                whose two sides hold >= 128 subsets each, 1 = none, 2 =
-                                every block.  Results are identical. */
+                                whose two sides hold >= 128 subsets each, and blocks of
+                                >= 2^24 codewords with a smaller side split into parts
+                                whose sides are large (the large side's half cut in two
+                                quarters); 1 = none; 2 = every block as it is; 3 = as 0
+                                with every block that has a side under 128 subsets split,
+                                whatever its size.  Results are identical. */
 } mdist_options;
 
 /* Witness key: the least (weight, g, j, rank) over the enumerated units (a total

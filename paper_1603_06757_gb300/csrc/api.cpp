@@ -64,8 +64,8 @@ struct mdist_code {
     int wave_cap = 0;                    // units a wave can hold: m * (k + 1)
     UnitSlot *d_wave = nullptr;          // [wave_cap] per-unit slots + 1 threshold word after them
     UnitSlot *h_wave = nullptr;          // pinned copy
-    // subset-sum tables for the tensor-core enumerator, key (j << 16 | half << 8 | t)
-    std::map<uint32_t, void *> tabs;
+    // tables of the tensor-core enumerator (side_key: set, side components, expanded)
+    std::map<uint64_t, void *> tabs;
     size_t tab_bytes = 0;
     RunState st;
 };
@@ -119,12 +119,45 @@ bool tc_events(mdist_code *c, int pairs) {
 // stay on the ALU enumerator.
 constexpr size_t kTableBudget = 16ull << 30;
 
-// Table of the sums of the t-subsets of half `half` of set j's rows (colex order) and,
-// with `expanded`, its expansion to tensor-core operand tiles; built on first use and
-// kept for later levels; null when over budget.
-int subset_table(mdist_code *c, int j, int half, int t, unsigned long long count, bool expanded, const void **out) {
+// Product blocks with fewer codewords than this and a side under kGramMinSide entries
+// stay on the ALU kernel; larger ones are split for the tensor cores.
+constexpr unsigned long long kSplitMin = 1ull << 24;
+
+mdist::GramSide make_side(int off0, int kc0, int t0, int off1 = 0, int kc1 = 0, int t1 = -1) {
+    mdist::GramSide S{};
+    S.nc = t1 >= 0 ? 2 : 1;
+    S.off[0] = (uint8_t)off0;
+    S.kc[0] = (uint8_t)kc0;
+    S.t[0] = (uint8_t)t0;
+    S.cnt0 = (uint32_t)mdist::binom_host(kc0, t0);
+    S.n = S.cnt0;
+    if (t1 >= 0) {
+        S.off[1] = (uint8_t)off1;
+        S.kc[1] = (uint8_t)kc1;
+        S.t[1] = (uint8_t)t1;
+        S.n *= mdist::binom_host(kc1, t1);
+    }
+    return S;
+}
+
+uint64_t side_key(int j, const mdist::GramSide &S, bool expanded) {
+    uint64_t key = ((uint64_t)j << 1) | (expanded ? 1u : 0u);
+    key = (key << 1) | (S.nc == 2 ? 1u : 0u);
+    for (int i = 0; i < 2; ++i) {
+        const bool on = i < S.nc;
+        key = (key << 6) | (on ? S.off[i] : 0u);
+        key = (key << 6) | (on ? S.kc[i] : 0u);
+        key = (key << 6) | (on ? S.t[i] : 0u);
+    }
+    return key;
+}
+
+// Table of the sums of a side's entries of set j and, with `expanded`, its expansion to
+// tensor-core operand tiles; built on first use and kept for later levels and runs;
+// null when over budget.
+int side_table(mdist_code *c, int j, const mdist::GramSide &S, bool expanded, const void **out) {
     *out = nullptr;
-    const uint32_t key = ((uint32_t)j << 16) | ((uint32_t)half << 8) | (uint32_t)t | (expanded ? 1u << 31 : 0u);
+    const uint64_t key = side_key(j, S, expanded);
     auto it = c->tabs.find(key);
     if (it != c->tabs.end()) {
         *out = it->second;
@@ -133,23 +166,19 @@ int subset_table(mdist_code *c, int j, int half, int t, unsigned long long count
     const DeviceRows &dr = c->rows[(size_t)j];
     const void *packed = nullptr;
     if (expanded) {
-        const int rc = subset_table(c, j, half, t, count, false, &packed);
+        const int rc = side_table(c, j, S, false, &packed);
         if (rc != MDIST_OK || !packed) return rc;
     }
-    const size_t bytes = expanded ? mdist::gram_expanded_bytes(dr.nwords, count)
-                                  : (size_t)count * (size_t)dr.nwords * sizeof(uint32_t);
+    const size_t bytes = expanded ? mdist::gram_expanded_bytes(dr.nwords, S.n)
+                                  : (size_t)S.n * (size_t)dr.nwords * sizeof(uint32_t);
     if (c->tab_bytes + bytes > kTableBudget) return MDIST_OK;
     void *d = dev_alloc(c, bytes);
     if (!d) return MDIST_OK;
-    cudaError_t e;
-    if (expanded) {
-        e = mdist::launch_expand_table((const uint32_t *)packed, dr.nwords, count, dr.n_bits, (uint8_t *)d,
-                                       c->sm_count, c->stream);
-    } else {
-        const int k1 = (c->k + 1) / 2, kh = half ? c->k - k1 : k1;
-        const uint32_t *rows = c->d_rows[(size_t)j] + (half ? (size_t)k1 * (size_t)dr.nwords : 0);
-        e = mdist::launch_subset_table(rows, dr.nwords, kh, t, count, (uint32_t *)d, c->sm_count, c->stream);
-    }
+    const cudaError_t e =
+        expanded ? mdist::launch_expand_table((const uint32_t *)packed, dr.nwords, S.n, dr.n_bits, (uint8_t *)d,
+                                              c->sm_count, c->stream)
+                 : mdist::launch_side_table(c->d_rows[(size_t)j], c->k, dr.nwords, S, (uint32_t *)d, c->sm_count,
+                                            c->stream);
     if (e != cudaSuccess) {
         dev_release(c, d);
         return MDIST_ECUDA;
@@ -161,27 +190,73 @@ int subset_table(mdist_code *c, int j, int half, int t, unsigned long long count
     return MDIST_OK;
 }
 
-// Tables of the product blocks of unit p (set j) that go to the tensor cores
-// (tensor_cores 0: blocks whose sides both hold >= kGramMinSide entries; 2: every block;
-// 1: none); all null for a block left to the ALU enumerator.
-int gram_tables(mdist_code *c, int j, const EnumParams &p, mdist::GramTables *tabs) {
-    for (int b = 0; b < mdist::kMaxBlocks; ++b) tabs[b] = mdist::GramTables{};
-    if (c->opt.tensor_cores == 1 || !mdist::gram_eligible(p.nwords)) return MDIST_OK;
+// One tensor-core block with its tables (false when a table is over budget).
+int add_gram_block(mdist_code *c, int j, mdist::GramSide A, mdist::GramSide B,
+                   std::vector<mdist::GramBlockSpec> &out, bool *ok) {
+    *ok = false;
+    if (B.n > A.n) std::swap(A, B);  // the streamed (B) side is the smaller one
+    const void *a = nullptr, *b = nullptr, *bx = nullptr;
+    int rc = side_table(c, j, A, false, &a);
+    if (rc == MDIST_OK && a) rc = side_table(c, j, B, false, &b);
+    if (rc == MDIST_OK && b) rc = side_table(c, j, B, true, &bx);
+    if (rc != MDIST_OK || !a || !b || !bx) return rc;
+    mdist::GramBlockSpec g;
+    g.a = A;
+    g.b = B;
+    g.a_tab = (const uint32_t *)a;
+    g.b_tab = (const uint32_t *)b;
+    g.b_exp = (const uint8_t *)bx;
+    out.push_back(g);
+    *ok = true;
+    return MDIST_OK;
+}
+
+// The tensor-core part of unit p (set j).  tensor_cores 0: a product block whose sides
+// both hold >= kGramMinSide entries goes there as it is; one with a smaller side and at
+// least kSplitMin codewords is split over the two quarters of its large side's half:
+// S x L_t = union over i of (S + Qa_i) x Qb_(t-i) (Vandermonde), every part with two
+// large sides.  tensor_cores 3: as 0, splitting every block with a small side whatever
+// its size; 2: every block as it is; 1: none.  covered[b] marks the blocks handled there.
+int gram_plan(mdist_code *c, int j, const EnumParams &p, std::vector<mdist::GramBlockSpec> &out, bool *covered) {
+    out.clear();
+    for (int b = 0; b < mdist::kMaxBlocks; ++b) covered[b] = false;
+    const int mode = c->opt.tensor_cores;
+    if (mode == 1 || !mdist::gram_eligible(p.nwords)) return MDIST_OK;
+    const int k1 = p.k1, k2 = p.k2;
     for (int b = 0; b < p.nblocks; ++b) {
         const mdist::ProductBlock &B = p.blocks[b];
+        const int loff = B.lane_half ? k1 : 0, lkc = B.lane_half ? k2 : k1;
+        const int woff = B.lane_half ? 0 : k1, wkc = B.lane_half ? k1 : k2;
         const unsigned long long small = B.lane_n < B.walk_n ? B.lane_n : B.walk_n;
-        if (c->opt.tensor_cores == 0 && small < (unsigned long long)mdist::kGramMinSide) continue;
-        const void *a = nullptr, *w = nullptr, *wx = nullptr;
-        const int walk_half = 1 - (int)B.lane_half;
-        int rc = subset_table(c, j, (int)B.lane_half, (int)B.lane_t, B.lane_n, false, &a);
-        if (rc == MDIST_OK && a) rc = subset_table(c, j, walk_half, (int)B.walk_t, B.walk_n, false, &w);
-        if (rc == MDIST_OK && w) rc = subset_table(c, j, walk_half, (int)B.walk_t, B.walk_n, true, &wx);
-        if (rc != MDIST_OK) return rc;
-        if (a && w && wx) {
-            tabs[b].lane = (const uint32_t *)a;
-            tabs[b].walk = (const uint32_t *)w;
-            tabs[b].walk_exp = (const uint8_t *)wx;
+        const size_t mark = out.size();
+        bool ok = false;
+        if (mode == 2 || small >= (unsigned long long)mdist::kGramMinSide) {
+            if ((int)out.size() + 1 > mdist::kMaxGramBlocks) continue;
+            const int rc = add_gram_block(c, j, make_side(loff, lkc, (int)B.lane_t), make_side(woff, wkc, (int)B.walk_t),
+                                          out, &ok);
+            if (rc != MDIST_OK) return rc;
+            covered[b] = ok;
+            continue;
         }
+        if (mode != 3 && B.lane_n * B.walk_n < kSplitMin) continue;
+        // large side L (t_L-subsets of kc_L rows at off_L), small side S
+        const bool lane_large = B.lane_n >= B.walk_n;
+        const int Loff = lane_large ? loff : woff, Lkc = lane_large ? lkc : wkc;
+        const int Lt = (int)(lane_large ? B.lane_t : B.walk_t);
+        const int Soff = lane_large ? woff : loff, Skc = lane_large ? wkc : lkc;
+        const int St = (int)(lane_large ? B.walk_t : B.lane_t);
+        const int qa = Lkc / 2, qb = Lkc - qa;
+        const int i0 = Lt - qb > 0 ? Lt - qb : 0, i1 = Lt < qa ? Lt : qa;
+        if (Lt < 1 || (int)out.size() + (i1 - i0 + 1) > mdist::kMaxGramBlocks) continue;
+        bool all = true;
+        for (int i = i0; i <= i1 && all; ++i) {
+            const mdist::GramSide A = St > 0 ? make_side(Soff, Skc, St, Loff, qa, i) : make_side(Loff, qa, i);
+            const int rc = add_gram_block(c, j, A, make_side(Loff + qa, qb, Lt - i), out, &ok);
+            if (rc != MDIST_OK) return rc;
+            all = ok;
+        }
+        if (all) covered[b] = true;
+        else out.resize(mark);  // a table over budget: the whole block stays on the ALU kernel
     }
     return MDIST_OK;
 }
@@ -216,17 +291,18 @@ int run_unit(mdist_code *c, int g, int j, int U_thr, bool hist_mode, bool *found
         if (!mdist::filter_group_valid(group, dr.nwords)) group = 0;
     }
     c->st.last_group = group;
-    mdist::GramTables tabs[mdist::kMaxBlocks];
+    std::vector<mdist::GramBlockSpec> gspecs;
+    bool covered[mdist::kMaxBlocks] = {};
     if (!hist_mode) {
-        const int rc = gram_tables(c, j, p, tabs);
+        const int rc = gram_plan(c, j, p, gspecs, covered);
         if (rc != MDIST_OK) return rc;
     }
     if (!tc_events(c, 1)) return MDIST_ECUDA;
     unsigned long long tc_combos = 0;
     int kernels = 0;
     if (mdist::launch_unit_split(p, dr.nwords, group, hist_mode, c->sm_count, c->opt.blocks_per_sm,
-                                 hist_mode ? nullptr : tabs, c->stream, c->tc_ev[0], c->tc_ev[1], &tc_combos,
-                                 &kernels) != cudaSuccess)
+                                 gspecs.data(), (int)gspecs.size(), covered, c->stream, c->tc_ev[0], c->tc_ev[1],
+                                 &tc_combos, &kernels) != cudaSuccess)
         return MDIST_ECUDA;
     if (cudaEventRecord(c->ev1, c->stream) != cudaSuccess) return MDIST_ECUDA;
     if (cudaMemcpyAsync(c->h_slot, c->d_slot, sizeof(UnitSlot), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess)
@@ -318,7 +394,7 @@ int mdist_prepare(const uint64_t *G, int n, int k, int words_per_row, const mdis
     mdist_code *c = new (std::nothrow) mdist_code();
     if (!c) return MDIST_ENOMEM;
     if (opts) c->opt = *opts;
-    if (c->opt.filter_group < 0 || c->opt.filter_group > 5 || c->opt.tensor_cores < 0 || c->opt.tensor_cores > 2) {
+    if (c->opt.filter_group < 0 || c->opt.filter_group > 5 || c->opt.tensor_cores < 0 || c->opt.tensor_cores > 3) {
         delete c;
         return MDIST_EINVAL;
     }
@@ -485,6 +561,7 @@ static int run_wave(mdist_code *c, int g_hi, int max_units, int *units_done) {
     s.h2d_bytes += sizeof(UnitSlot) * ((size_t)n_units + 1);
     if (!tc_events(c, n_units)) return MDIST_ECUDA;
     std::vector<unsigned long long> tc_combos((size_t)n_units, 0);
+    std::vector<mdist::GramBlockSpec> gspecs;
     int launched = 0, kernels = 0;
     if (cudaEventRecord(c->ev0, c->stream) != cudaSuccess) return MDIST_ECUDA;
     for (int u = 0; u < n_units; ++u) {
@@ -502,11 +579,12 @@ static int run_wave(mdist_code *c, int g_hi, int max_units, int *units_done) {
         const int fg = c->opt.filter_group;
         int group = fg == 0 ? mdist::choose_filter_group(dr.nwords, dr.n_bits, U_thr - q.base) : (fg == 1 ? 0 : fg);
         if (!mdist::filter_group_valid(group, dr.nwords)) group = 0;
-        mdist::GramTables tabs[mdist::kMaxBlocks];
-        const int rc = gram_tables(c, j, q, tabs);
+        bool covered[mdist::kMaxBlocks] = {};
+        const int rc = gram_plan(c, j, q, gspecs, covered);
         if (rc != MDIST_OK) return rc;
-        if (mdist::launch_unit_split(q, dr.nwords, group, false, c->sm_count, c->opt.blocks_per_sm, tabs,
-                                     c->stream, c->tc_ev[2 * (size_t)u], c->tc_ev[2 * (size_t)u + 1],
+        if (mdist::launch_unit_split(q, dr.nwords, group, false, c->sm_count, c->opt.blocks_per_sm, gspecs.data(),
+                                     (int)gspecs.size(), covered, c->stream, c->tc_ev[2 * (size_t)u],
+                                     c->tc_ev[2 * (size_t)u + 1],
                                      &tc_combos[(size_t)u], &kernels) != cudaSuccess)
             return MDIST_ECUDA;
         launched += kernels;

@@ -146,44 +146,40 @@ size_t enum_smem_bytes(int k, int nwords) {
            ((size_t)k * nwords + 33 * 33 + (size_t)kWarpsPerCta * walk_len_for(nwords) * walk_stride(nwords));
 }
 
-// One unit: the product blocks that come with subset-sum tables on the tensor cores,
-// the others on the ALU kernel.  Both launches share the threshold word, key, count and
-// status of `p`.
+// One unit: the tensor-core blocks, then the product blocks they do not cover on the
+// ALU kernel.  Both launches share the threshold word, key, count and status of `p`.
 cudaError_t launch_unit_split(const EnumParams &p, int nwords, int group, bool hist_mode, int sm_count,
-                              int blocks_per_sm, const GramTables *tabs, cudaStream_t stream, cudaEvent_t tc_ev0,
-                              cudaEvent_t tc_ev1, unsigned long long *tc_combos, int *kernels) {
-    bool tc[kMaxBlocks] = {};
-    int ntc = 0;
+                              int blocks_per_sm, const GramBlockSpec *gblocks, int ngblocks, const bool *covered,
+                              cudaStream_t stream, cudaEvent_t tc_ev0, cudaEvent_t tc_ev1,
+                              unsigned long long *tc_combos, int *kernels) {
+    if (hist_mode) {
+        ngblocks = 0;
+        covered = nullptr;
+    }
     unsigned long long combos = 0;
-    if (!hist_mode && tabs)
-        for (int b = 0; b < p.nblocks; ++b)
-            if (tabs[b].lane && tabs[b].walk && tabs[b].walk_exp) {
-                tc[b] = true;
-                ++ntc;
-                combos += p.blocks[b].lane_n * p.blocks[b].walk_n;
-            }
+    for (int i = 0; i < ngblocks; ++i) combos += gblocks[i].a.n * gblocks[i].b.n;
     if (tc_combos) *tc_combos = combos;
     if (kernels) *kernels = 0;
-    if (ntc) {
+    if (ngblocks > 0) {
         if (tc_ev0 && cudaEventRecord(tc_ev0, stream) != cudaSuccess) return cudaErrorUnknown;
-        const cudaError_t e = launch_gram_unit(p, tabs, p.U, p.slot, reinterpret_cast<int *>(&p.slot->status),
-                                               sm_count, stream);
+        const cudaError_t e = launch_gram_unit(p, gblocks, ngblocks, p.U, p.slot,
+                                               reinterpret_cast<int *>(&p.slot->status), sm_count, stream);
         if (e != cudaSuccess) return e;
         if (tc_ev1 && cudaEventRecord(tc_ev1, stream) != cudaSuccess) return cudaErrorUnknown;
         if (kernels) *kernels += 1;
     }
-    if (ntc == p.nblocks) return cudaSuccess;
     EnumParams q = p;
     const unsigned long long lane_chunk = 32ull * (unsigned long long)lane_entries_per_thread(nwords);
     int nb = 0;
     unsigned long long tiles = 0;
     for (int b = 0; b < p.nblocks; ++b) {
-        if (tc[b]) continue;
+        if (covered && covered[b]) continue;
         ProductBlock B = p.blocks[b];
         B.tile_begin = tiles;
         tiles += ((B.lane_n + lane_chunk - 1) / lane_chunk) * B.walk_chunks;
         q.blocks[nb++] = B;
     }
+    if (nb == 0) return cudaSuccess;
     q.nblocks = nb;
     q.total_tiles = tiles;
     const cudaError_t e = launch_enum_unit(q, nwords, group, hist_mode, sm_count, blocks_per_sm, stream);

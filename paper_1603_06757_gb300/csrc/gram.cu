@@ -57,14 +57,11 @@ __host__ __device__ constexpr int gram_b_stages(int nw) {
 }
 
 struct GramBlock {
-    unsigned int a_half;         // half of the rows the A side's subsets come from
-    unsigned int a_t, b_t;       // subset sizes
-    unsigned int pad;
-    unsigned long long a_n, b_n; // entries per side
+    GramSide a, b;               // the two sides (A: 128-row tiles, B: 256-row tiles)
     unsigned long long a_tiles, b_units, b_tiles;
     unsigned long long wu_begin;
-    const uint32_t *a_tab;       // a_n x nwords: subset sums of the A side, colex order
-    const uint32_t *b_tab;       // b_n x nwords
+    const uint32_t *a_tab;       // a.n x nwords: sums of the A side's entries
+    const uint32_t *b_tab;       // b.n x nwords
     const uint8_t *b_exp;        // b_tiles x (kGN x KA) bytes: expanded B tiles (layout of write_row)
 };
 
@@ -72,25 +69,38 @@ struct GramParams {
     unsigned int *U;
     UnitSlot *slot;
     int *status;
-    int k, k1, k2, g, nwords, n_bits, base;
+    int k, g, nwords, n_bits, base;
     int nblocks;
     unsigned long long total_wu;
     long long max_wait;
-    GramBlock blocks[kMaxBlocks];
+    GramBlock blocks[kMaxGramBlocks];
 };
 
 // work unit -> (block, A tile, B tile range); within a block the A tile runs fastest
 __device__ __forceinline__ void decode_wu(const GramParams &P, unsigned long long wu, int &b,
                                           unsigned long long &a_tile, unsigned long long &bt0,
                                           unsigned long long &bt1) {
-    b = 0;
-    while (b + 1 < P.nblocks && wu >= P.blocks[b + 1].wu_begin) ++b;
+    int lo = 0, hi = P.nblocks - 1;  // last block with wu_begin <= wu
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (P.blocks[mid].wu_begin <= wu) lo = mid;
+        else hi = mid - 1;
+    }
+    b = lo;
     const GramBlock &B = P.blocks[b];
     const unsigned long long w = wu - B.wu_begin;
     const unsigned long long bu = w / B.a_tiles;
     a_tile = w - bu * B.a_tiles;
     bt0 = bu * kTilesPerUnit;
     bt1 = bt0 + kTilesPerUnit < B.b_tiles ? bt0 + kTilesPerUnit : B.b_tiles;
+}
+
+// rows (as a k-bit mask) of the subset behind side entry e
+__device__ __forceinline__ unsigned long long side_mask(const uint32_t *bn, const GramSide &S, unsigned long long e) {
+    const unsigned long long e0 = S.nc == 2 ? e % S.cnt0 : e;
+    unsigned long long m = (unsigned long long)unrank_colex(bn, S.kc[0], S.t[0], (uint32_t)e0) << S.off[0];
+    if (S.nc == 2) m |= (unsigned long long)unrank_colex(bn, S.kc[1], S.t[1], (uint32_t)(e / S.cnt0)) << S.off[1];
+    return m;
 }
 
 // Operand row r of a tile (K-major, no-swizzle layout): per bit of the NW words one
@@ -117,15 +127,6 @@ __device__ __forceinline__ void write_row(uint8_t *tile, int r, const uint32_t (
                 make_uint4(q[0], q[1], q[2], q[3]);
         }
     }
-}
-
-template <int NW>
-__device__ __forceinline__ void subset_sum(const uint32_t *rows, const uint32_t *bn, int kh, int t, uint32_t rank,
-                                           uint32_t (&x)[NW], uint32_t &mask) {
-    mask = unrank_colex(bn, kh, t, rank);
-#pragma unroll
-    for (int w = 0; w < NW; ++w) x[w] = 0;
-    xor_rows<NW>(x, rows, mask);
 }
 
 template <int NW>
@@ -188,7 +189,7 @@ __global__ void __launch_bounds__(kGramThreads, 1) gram_kernel(const __grid_cons
             for (int h = 0; h < kGM / 32; ++h) {
                 const unsigned long long e = a_tile * kGM + (unsigned long long)(lane + 32 * h);
 #pragma unroll
-                for (int w = 0; w < NW; ++w) x[h][w] = e < B.a_n ? B.a_tab[e * NW + w] : 0u;
+                for (int w = 0; w < NW; ++w) x[h][w] = e < B.a.n ? B.a_tab[e * NW + w] : 0u;
             }
             if (!mbar_wait(bar(A_EMPTY + st), (uint32_t)(((u >> 1) & 1) ^ 1), P.max_wait)) { fail(); break; }
 #pragma unroll
@@ -271,9 +272,9 @@ __global__ void __launch_bounds__(kGramThreads, 1) gram_kernel(const __grid_cons
             decode_wu(P, wu, b, a_tile, bt0, bt1);
             const GramBlock &B = P.blocks[b];
             const unsigned long long a_e = a_tile * kGM + (unsigned long long)row;
-            const bool a_valid = a_e < B.a_n;
-            const unsigned long long a_valid_rows = B.a_n - a_tile * kGM < (unsigned long long)kGM
-                                                        ? B.a_n - a_tile * kGM
+            const bool a_valid = a_e < B.a.n;
+            const unsigned long long a_valid_rows = B.a.n - a_tile * kGM < (unsigned long long)kGM
+                                                        ? B.a.n - a_tile * kGM
                                                         : (unsigned long long)kGM;
             // candidates: acc >= n_bits - 2 thr, with a threshold read one unit ahead
             const float bound = (float)(P.n_bits - 2 * ((int)u_next - P.base));
@@ -303,7 +304,6 @@ __global__ void __launch_bounds__(kGramThreads, 1) gram_kernel(const __grid_cons
                 if (m >= bound && a_valid) {
                     // side path: which columns reach the bound, then the exact weight from
                     // the bit-packed rows, then the key
-                    const int a_kh = B.a_half ? P.k2 : P.k1, b_kh = B.a_half ? P.k1 : P.k2;
                     uint32_t x[NW];
 #pragma unroll
                     for (int w = 0; w < NW; ++w) x[w] = B.a_tab[a_e * NW + w];
@@ -320,16 +320,14 @@ __global__ void __launch_bounds__(kGramThreads, 1) gram_kernel(const __grid_cons
                             const int i = __ffsll((long long)neg) - 1;
                             neg &= neg - 1;
                             const unsigned long long b_e = bt * kGN + (unsigned long long)(col0 + 64 * q + i);
-                            if (b_e >= B.b_n) continue;
+                            if (b_e >= B.b.n) continue;
                             int w = 0;
 #pragma unroll
                             for (int z = 0; z < NW; ++z) w += __popc(x[z] ^ B.b_tab[b_e * NW + z]);
                             const int weight = w + P.base;
                             if (weight > (int)(*(volatile unsigned int *)P.U)) continue;
-                            const uint32_t am = unrank_colex(s_bn, a_kh, (int)B.a_t, (uint32_t)a_e);
-                            const uint32_t bm = unrank_colex(s_bn, b_kh, (int)B.b_t, (uint32_t)b_e);
-                            const unsigned long long h1 = B.a_half ? bm : am, h2 = B.a_half ? am : bm;
-                            const unsigned long long rank = lexrank64(h1 | (h2 << P.k1), P.k, P.g, DevBinomG{});
+                            const unsigned long long mask = side_mask(s_bn, B.a, a_e) | side_mask(s_bn, B.b, b_e);
+                            const unsigned long long rank = lexrank64(mask, P.k, P.g, DevBinomG{});
                             atomicMin(P.U, (unsigned int)weight);
                             atomicMin(&P.slot->key, ((unsigned long long)weight << kKeyRankBits) | rank);
                         }
@@ -338,7 +336,7 @@ __global__ void __launch_bounds__(kGramThreads, 1) gram_kernel(const __grid_cons
                 tc_fence_before();
                 mbar_arrive(bar(ACC_EMPTY + ab));
                 if (tid == 0) {
-                    const unsigned long long b_left = B.b_n - bt * kGN;
+                    const unsigned long long b_left = B.b.n - bt * kGN;
                     cnt += a_valid_rows * (b_left < (unsigned long long)kGN ? b_left : (unsigned long long)kGN);
                 }
             }
@@ -372,18 +370,26 @@ cudaError_t gram_launch_nw(const GramParams &p, int sm_count, cudaStream_t strea
     return cudaGetLastError();
 }
 
-// out[e * NW ..] = sum of the rows of the t-subset of {0..kh-1} with colex rank e
+// out[e * NW ..] = the sum of the rows of side entry e (rows: the k rows of the set)
 template <int NW>
-__global__ void subset_table_kernel(const uint32_t *rows, int kh, int t, unsigned long long count, uint32_t *out) {
+__global__ void side_table_kernel(const uint32_t *rows, int k, GramSide side, uint32_t *out) {
     __shared__ uint32_t s_bn[kBn * kBn];
-    __shared__ uint32_t s_rows[32 * NW];
+    __shared__ uint32_t s_rows[64 * NW];
     for (int i = threadIdx.x; i < kBn * kBn; i += blockDim.x) s_bn[i] = (uint32_t)c_binom_g.v[i / kBn][i % kBn];
-    for (int i = threadIdx.x; i < kh * NW; i += blockDim.x) s_rows[i] = rows[i];
+    for (int i = threadIdx.x; i < k * NW; i += blockDim.x) s_rows[i] = rows[i];
     __syncthreads();
-    for (unsigned long long e = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; e < count;
+    for (unsigned long long e = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; e < side.n;
          e += (unsigned long long)gridDim.x * blockDim.x) {
-        uint32_t x[NW], mask;
-        subset_sum<NW>(s_rows, s_bn, kh, t, (uint32_t)e, x, mask);
+        unsigned long long m = side_mask(s_bn, side, e);
+        uint32_t x[NW];
+#pragma unroll
+        for (int w = 0; w < NW; ++w) x[w] = 0;
+        while (m) {
+            const int r = __ffsll((long long)m) - 1;
+            m &= m - 1;
+#pragma unroll
+            for (int w = 0; w < NW; ++w) x[w] ^= s_rows[r * NW + w];
+        }
 #pragma unroll
         for (int w = 0; w < NW; ++w) out[e * NW + w] = x[w];
     }
@@ -406,13 +412,13 @@ __global__ void expand_table_kernel(const uint32_t *packed, unsigned long long c
 }
 
 template <int NW>
-cudaError_t table_launch_nw(const uint32_t *rows, int kh, int t, unsigned long long count, uint32_t *out,
-                            int sm_count, cudaStream_t stream) {
-    unsigned long long grid = (count + 255) / 256;
+cudaError_t table_launch_nw(const uint32_t *rows, int k, const GramSide &side, uint32_t *out, int sm_count,
+                            cudaStream_t stream) {
+    unsigned long long grid = (side.n + 255) / 256;
     const unsigned long long cap = (unsigned long long)sm_count * 8;
     if (grid > cap) grid = cap;
     if (grid < 1) grid = 1;
-    subset_table_kernel<NW><<<(unsigned int)grid, 256, 0, stream>>>(rows, kh, t, count, out);
+    side_table_kernel<NW><<<(unsigned int)grid, 256, 0, stream>>>(rows, k, side, out);
     return cudaGetLastError();
 }
 
@@ -430,16 +436,17 @@ cudaError_t expand_launch_nw(const uint32_t *packed, unsigned long long count, i
 
 }  // namespace
 
-cudaError_t launch_subset_table(const uint32_t *rows, int nwords, int kh, int t, unsigned long long count,
-                                uint32_t *out, int sm_count, cudaStream_t stream) {
+cudaError_t launch_side_table(const uint32_t *rows, int k, int nwords, const GramSide &side, uint32_t *out,
+                              int sm_count, cudaStream_t stream) {
+    if (k < 1 || k > 64) return cudaErrorInvalidValue;
     switch (nwords) {
-        case 1: return table_launch_nw<1>(rows, kh, t, count, out, sm_count, stream);
-        case 2: return table_launch_nw<2>(rows, kh, t, count, out, sm_count, stream);
-        case 3: return table_launch_nw<3>(rows, kh, t, count, out, sm_count, stream);
-        case 4: return table_launch_nw<4>(rows, kh, t, count, out, sm_count, stream);
-        case 5: return table_launch_nw<5>(rows, kh, t, count, out, sm_count, stream);
-        case 6: return table_launch_nw<6>(rows, kh, t, count, out, sm_count, stream);
-        case 7: return table_launch_nw<7>(rows, kh, t, count, out, sm_count, stream);
+        case 1: return table_launch_nw<1>(rows, k, side, out, sm_count, stream);
+        case 2: return table_launch_nw<2>(rows, k, side, out, sm_count, stream);
+        case 3: return table_launch_nw<3>(rows, k, side, out, sm_count, stream);
+        case 4: return table_launch_nw<4>(rows, k, side, out, sm_count, stream);
+        case 5: return table_launch_nw<5>(rows, k, side, out, sm_count, stream);
+        case 6: return table_launch_nw<6>(rows, k, side, out, sm_count, stream);
+        case 7: return table_launch_nw<7>(rows, k, side, out, sm_count, stream);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -464,15 +471,14 @@ cudaError_t launch_expand_table(const uint32_t *packed, int nwords, unsigned lon
 
 bool gram_eligible(int nwords) { return nwords >= 1 && nwords <= kGramMaxWords; }
 
-cudaError_t launch_gram_unit(const EnumParams &ep, const GramTables *tabs, unsigned int *U, UnitSlot *slot,
-                             int *status, int sm_count, cudaStream_t stream) {
+cudaError_t launch_gram_unit(const EnumParams &ep, const GramBlockSpec *blocks, int nblocks, unsigned int *U,
+                             UnitSlot *slot, int *status, int sm_count, cudaStream_t stream) {
+    if (nblocks > kMaxGramBlocks) return cudaErrorInvalidValue;
     GramParams p{};
     p.U = U;
     p.slot = slot;
     p.status = status;
     p.k = ep.k;
-    p.k1 = ep.k1;
-    p.k2 = ep.k2;
     p.g = ep.g;
     p.nwords = ep.nwords;
     p.n_bits = ep.n_bits;
@@ -480,22 +486,17 @@ cudaError_t launch_gram_unit(const EnumParams &ep, const GramTables *tabs, unsig
     p.max_wait = 200000000ll;
     int nb = 0;
     unsigned long long wu = 0;
-    for (int b = 0; b < ep.nblocks; ++b) {
-        const GramTables &T = tabs[b];
-        if (!T.lane || !T.walk || !T.walk_exp) continue;
-        const ProductBlock &E = ep.blocks[b];
+    for (int i = 0; i < nblocks; ++i) {
+        const GramBlockSpec &S = blocks[i];
+        if (!S.a_tab || !S.b_tab || !S.b_exp || S.a.n == 0 || S.b.n == 0) return cudaErrorInvalidValue;
         GramBlock &G = p.blocks[nb++];
-        G.a_tab = T.lane;
-        G.b_tab = T.walk;
-        G.b_exp = T.walk_exp;
-        G.a_half = E.lane_half;
-        G.a_t = E.lane_t;
-        G.b_t = E.walk_t;
-        G.pad = 0;
-        G.a_n = E.lane_n;
-        G.b_n = E.walk_n;
-        G.a_tiles = (E.lane_n + kGM - 1) / kGM;
-        G.b_tiles = (E.walk_n + kGN - 1) / kGN;
+        G.a = S.a;
+        G.b = S.b;
+        G.a_tab = S.a_tab;
+        G.b_tab = S.b_tab;
+        G.b_exp = S.b_exp;
+        G.a_tiles = (S.a.n + kGM - 1) / kGM;
+        G.b_tiles = (S.b.n + kGN - 1) / kGN;
         G.b_units = (G.b_tiles + kTilesPerUnit - 1) / kTilesPerUnit;
         G.wu_begin = wu;
         wu += G.a_tiles * G.b_units;

@@ -73,37 +73,51 @@ cudaError_t launch_enum_unit(const EnumParams &p, int nwords, int group, bool hi
                              int blocks_per_sm, cudaStream_t stream);
 
 // Tensor-core (tcgen05) enumerator for the large product blocks of a unit (gram.cu).
-// A block goes there when both of its sides hold at least kGramMinSide entries and the
-// stored rows are at most kGramMaxWords words.  `tc_block[b]` selects blocks of `ep`.
+// A block goes there directly when both of its sides hold at least kGramMinSide
+// entries and the stored rows are at most kGramMaxWords words; a large block with a
+// smaller side is split into sub-blocks whose sides are all large (the large side's
+// half cut in two quarters).
 constexpr int kGramMinSide = 128;
 constexpr int kGramMaxWords = 7;
+constexpr int kMaxGramBlocks = 128;
 bool gram_eligible(int nwords);
-// Device tables of one product block for the tensor-core enumerator: the subset sums of
-// its lane side and of its walk side (colex order, nwords words each) and the walk side
-// expanded to operand tiles (gram_expanded_bytes).  All null: the block stays on the
-// ALU kernel.
-struct GramTables {
-    const uint32_t *lane = nullptr;
-    const uint32_t *walk = nullptr;
-    const uint8_t *walk_exp = nullptr;
+
+// One side of a tensor-core block: per entry the sum of one subset of the rows.  The
+// subset is the union of one or two components; component c is a t[c]-subset of the
+// kc[c] rows starting at row off[c] (kc[c] <= 32), and entry e has colex rank e % cnt0
+// in component 0 and e / cnt0 in component 1.
+struct GramSide {
+    uint8_t nc, off[2], kc[2], t[2], pad;
+    uint32_t cnt0;               // C(kc[0], t[0])
+    unsigned long long n;        // entries: cnt0 (x C(kc[1], t[1]))
 };
-cudaError_t launch_gram_unit(const EnumParams &ep, const GramTables *tabs, unsigned int *U, UnitSlot *slot,
-                             int *status, int sm_count, cudaStream_t stream);
-// out[e * nwords ..] = sum of the rows of the t-subset of rows[0..kh) with colex rank e
-cudaError_t launch_subset_table(const uint32_t *rows, int nwords, int kh, int t, unsigned long long count,
-                                uint32_t *out, int sm_count, cudaStream_t stream);
+
+// A block of the tensor-core enumerator: every pair (A entry, B entry), with the
+// device tables of both sides' sums (packed, nwords words per entry, entry order) and
+// the B side expanded to operand tiles (gram_expanded_bytes).
+struct GramBlockSpec {
+    GramSide a, b;
+    const uint32_t *a_tab = nullptr;
+    const uint32_t *b_tab = nullptr;
+    const uint8_t *b_exp = nullptr;
+};
+cudaError_t launch_gram_unit(const EnumParams &ep, const GramBlockSpec *blocks, int nblocks, unsigned int *U,
+                             UnitSlot *slot, int *status, int sm_count, cudaStream_t stream);
+// out[e * nwords ..] = the sum of the rows (rows: all k rows of the set) of side entry e
+cudaError_t launch_side_table(const uint32_t *rows, int k, int nwords, const GramSide &side, uint32_t *out,
+                              int sm_count, cudaStream_t stream);
 // bytes of the expanded operand tiles of a packed table of `count` entries
 size_t gram_expanded_bytes(int nwords, unsigned long long count);
 cudaError_t launch_expand_table(const uint32_t *packed, int nwords, unsigned long long count, int n_bits,
                                 uint8_t *out, int sm_count, cudaStream_t stream);
-// A unit: blocks with tables on the tensor cores, the others on the ALU kernel
-// (tabs may be null: every block on the ALU kernel).  When the tensor-core kernel is
-// launched and tc_ev0 / tc_ev1 are given they are recorded around it, *tc_combos (may
-// be null) receives the combinations it enumerates (else 0) and *kernels (may be null)
-// the number of kernels launched (0 to 2).
+// A unit: the tensor-core blocks (may be none), then the product blocks of `p` not
+// marked in `covered` (null: none covered) on the ALU kernel.  When the tensor-core
+// kernel is launched and tc_ev0 / tc_ev1 are given they are recorded around it,
+// *tc_combos (may be null) receives the combinations it enumerates (else 0) and
+// *kernels (may be null) the number of kernels launched (0 to 2).
 cudaError_t launch_unit_split(const EnumParams &p, int nwords, int group, bool hist_mode, int sm_count,
-                              int blocks_per_sm, const GramTables *tabs, cudaStream_t stream,
-                              cudaEvent_t tc_ev0 = nullptr, cudaEvent_t tc_ev1 = nullptr,
+                              int blocks_per_sm, const GramBlockSpec *gblocks, int ngblocks, const bool *covered,
+                              cudaStream_t stream, cudaEvent_t tc_ev0 = nullptr, cudaEvent_t tc_ev1 = nullptr,
                               unsigned long long *tc_combos = nullptr, int *kernels = nullptr);
 
 // Filter variant for a unit: 0 (exact count for every codeword) or the OR-group size

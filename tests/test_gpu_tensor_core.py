@@ -1,6 +1,7 @@
 """The tensor-core (tcgen05 Gram-matrix) enumerator against the oracle: every product
-block forced onto it (tensor_cores=2), and the default split (large blocks on the tensor
-cores, the rest on the ALU kernel)."""
+block forced onto it (tensor_cores=2), every block with a small side split into parts
+with two large sides (tensor_cores=3), and the default split (large blocks on the
+tensor cores, large blocks with a small side split, the rest on the ALU kernel)."""
 
 import math
 
@@ -31,11 +32,12 @@ CASES = [(30, 12, 1), (48, 24, 2), (100, 40, 3), (150, 40, 4), (170, 41, 5), (19
          (96, 24, 5), (129, 64, 8)]
 
 
+@pytest.mark.parametrize("mode", [2, 3])
 @pytest.mark.parametrize("n,k,seed", CASES)
-def test_unit_keys_all_blocks_on_tensor_cores(api, n, k, seed):
+def test_unit_keys_all_blocks_on_tensor_cores(api, mode, n, k, seed):
     G = synth.random_systematic(n, k, seed)
     part = oracle.partition(G, n)
-    with api.Code(G, n, tensor_cores=2) as c:
+    with api.Code(G, n, tensor_cores=mode) as c:
         for j in range(part["m"]):
             for g in range(1, k + 1):
                 if math.comb(k, g) > 3_000_000:
@@ -49,7 +51,7 @@ def test_unit_keys_all_blocks_on_tensor_cores(api, n, k, seed):
                 assert key2 is None and U2 == want["min_w"] - 1
 
 
-@pytest.mark.parametrize("mode", [0, 2])
+@pytest.mark.parametrize("mode", [0, 2, 3])
 @pytest.mark.parametrize("n,k,seed", [(120, 36, 3), (150, 36, 14), (96, 24, 5), (180, 36, 13), (60, 30, 1)])
 def test_min_distance_tensor_cores(api, mode, n, k, seed):
     G = synth.random_systematic(n, k, seed)
@@ -70,3 +72,18 @@ def test_large_level_matches_alu_kernel(api):
     with api.Code(G, 192, tensor_cores=0) as c:
         got = c.enumerate_level(7, 1, U=40)
     assert got == want
+
+
+@pytest.mark.parametrize("g,j", [(6, 0), (7, 0), (6, 1)])
+def test_split_blocks_default_mode_vs_oracle(api, g, j):
+    # [80,64]: blocks X_1 x Y_(g-1) of >= 2^24 codewords are split over the quarters of
+    # H2 in the default mode; set 0 stores 1 word per row, set 1 (rank 16) 3 words
+    G = synth.random_systematic(80, 64, 3)
+    part = oracle.partition(G, 80)
+    want = oracle.enumerate_unit(part["gammas"][j], 80, g, want_hist=False)
+    with api.Code(G, 80) as c:
+        U, key, combos = c.enumerate_level(g, j, U=80)
+        assert combos == [math.comb(64, g)]
+        assert key == (want["min_w"], g, j, want["min_rank"])
+        U2, key2, _ = c.enumerate_level(g, j, U=want["min_w"] - 1)
+        assert key2 is None and U2 == want["min_w"] - 1
