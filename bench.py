@@ -420,7 +420,7 @@ def run_plain(codes, hints=None):
     return len(codes) / (time.perf_counter() - t0), res
 
 
-def run_batched(codes, hints=None):
+def run_batched(codes, hints=None, blocks_per_sm=0, rounds_per_graph=0):
     """All codes in one batched run (rounds captured in one CUDA graph)."""
     import torch
 
@@ -428,10 +428,10 @@ def run_batched(codes, hints=None):
 
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    with api.Batch() as b:
+    with api.Batch(blocks_per_sm=blocks_per_sm) as b:
         for i, (n, k, G, _) in enumerate(codes):
             b.add(G, n, wstar_hint=hints[i] if hints else 0)
-        b.run()
+        b.run(rounds_per_graph)
         res = [b.result(i) for i in range(len(codes))]
         info = b.info()
     torch.cuda.synchronize()
@@ -474,17 +474,24 @@ def run_batch_bench(args):
     # warm-up of every path
     run_batched(test[:64])
     run_plain(test[:16])
-    cps_batch, res_b, info_b = run_batched(test)
+    cps_batch_untuned, res_b, info_b = run_batched(test)
     p_mlp, p_gv, errs = predictor_report(mlp, test, res_b)
     h_mlp = [w for (w, d) in p_mlp]
     h_gv = [w for (w, d) in p_gv]
-    cps_batch_mlp, res_bm, info_bm = run_batched(test, h_mlp)
-    cps_batch_gv, _, info_bg = run_batched(test, h_gv)
+    # launch shapes of the batched engine, tuned on a seeded sample (not timed)
+    from paper_1603_06757_gb300 import tune
+
+    tuned = tune.autotune_batch([(G, n, h) for (n, k, G, _), h in zip(test, h_mlp)], sample=args.tune_sample)
+    shape = {"blocks_per_sm": tuned["blocks_per_sm"], "rounds_per_graph": tuned["rounds_per_graph"]}
+    cps_batch, res_bt, info_bt = run_batched(test, None, **shape)
+    cps_batch_mlp, res_bm, info_bm = run_batched(test, h_mlp, **shape)
+    cps_batch_gv, _, info_bg = run_batched(test, h_gv, **shape)
     cps_plain, res_p = run_plain(test)
     cps_plain_mlp, _ = run_plain(test, h_mlp)
     cps_plain_gv, _ = run_plain(test, h_gv)
     same = all(a["d"] == b["d"] and a["key"] == b["key"] and np.array_equal(a["counts"], b["counts"])
-               for a, b in zip(res_b, res_p)) and all(a["key"] == b["key"] for a, b in zip(res_b, res_bm))
+               for a, b in zip(res_b, res_p)) and all(a["key"] == b["key"] for a, b in zip(res_b, res_bm)) and \
+        all(a["key"] == b["key"] and np.array_equal(a["counts"], b["counts"]) for a, b in zip(res_b, res_bt))
     cw = sum(r["total_combos"] for r in res_b)
     line = {
         "metric": "codes/s, batched vs plain (one code per prepare/run)", "unit": "codes/s",
@@ -493,9 +500,12 @@ def run_batch_bench(args):
                                f"kept: GV work estimate <= {cap:.0e} codewords",
                    "codes": len(test), "codewords": cw, "train_codes": len(train)},
         "codes_per_s": {"plain": cps_plain, "plain_gv_hint": cps_plain_gv, "plain_mlp_hint": cps_plain_mlp,
-                        "batched": cps_batch, "batched_gv_hint": cps_batch_gv, "batched_mlp_hint": cps_batch_mlp},
-        "rounds": {"batched": info_b["rounds"], "batched_mlp_hint": info_bm["rounds"],
+                        "batched_untuned": cps_batch_untuned, "batched": cps_batch, "batched_gv_hint": cps_batch_gv,
+                        "batched_mlp_hint": cps_batch_mlp},
+        "rounds": {"batched": info_bt["rounds"], "batched_mlp_hint": info_bm["rounds"],
                    "batched_gv_hint": info_bg["rounds"]},
+        "autotune": {"chosen": shape, "sample": tuned["sample"], "seconds_best": tuned["seconds_best"],
+                     "seconds_worst": tuned["seconds_worst"], "candidates": len(tuned["table"])},
         "predictor": errs, "train_loss_last": float(curve[-50:].mean()),
         "results_identical": bool(same),
     }
@@ -610,6 +620,7 @@ def main():
     ap.add_argument("--batch-codes", type=int, default=4096)
     ap.add_argument("--batch-train", type=int, default=1500)
     ap.add_argument("--batch-cap", type=float, default=1e10)
+    ap.add_argument("--tune-sample", type=int, default=256, help="codes the batched launch-shape autotuner times")
     ap.add_argument("--serve-requests", type=int, default=20000)
     ap.add_argument("--serve-cap", type=float, default=1e11)
     ap.add_argument("--serve-load", type=float, default=0.7)
