@@ -278,6 +278,27 @@ def run_ours(args):
     e2e_sec = time.perf_counter() - t0
     e2e_value = weak_value(world, e2e_cw, max_over_ranks(e2e_sec, dist, "cuda"))
 
+    # ---- the same runs on the ALU enumerator alone (XOR / POPC, no tensor cores) ----
+    alu_steps = 2
+    code_alu = api.Code(G, n, tensor_cores=1)
+    code_alu.reset()
+    code_alu.run()
+    torch.cuda.synchronize()
+    alu_ms, alu_wall, alu_cw = 0.0, 0.0, 0
+    for _ in range(alu_steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        code_alu.reset()
+        code_alu.run()
+        r_alu = code_alu.result()
+        torch.cuda.synchronize()
+        alu_wall += time.perf_counter() - t0
+        alu_cw += r_alu["total_combos"]
+    code_alu.close()
+    alu_ms = 1e3 * alu_wall
+    assert r_alu["key"] == res["key"] and r_alu["d"] == res["d"]
+
     # ---- roofline of the dominant kernel ----
     # The tensor-core enumerator contracts n_bits sign columns per codeword: 2 n_bits
     # flops (fp8 operands) per codeword, timed per launch by the library's CUDA events on
@@ -305,6 +326,13 @@ def run_ours(args):
                 "ms_per_step": alu_ms / args.steps, "codewords_per_step": (combos - tc_combos) // args.steps,
                 "peak_basis": f"{info['sm_count']} SMs x {sm_mhz:.0f} MHz x min({POPC_PER_CLK_SM} POPC, "
                               f"{ALU_PER_CLK_SM} ALU / {nwords} words) per clk per SM"}
+    alu_only = alu_cw / (alu_ms / 1e3)
+    alu_path = {"value": alu_only, "unit": UNIT, "ms_per_step": alu_ms / alu_steps, "steps": alu_steps,
+                "timing": "host clock around each synchronised run",
+                "frac_of_alu_popc_roofline": alu_only / alu_peak,
+                "frac_of_exact_popc_roofline": alu_only / (info["sm_count"] * sm_mhz * 1e6 * POPC_PER_CLK_SM / nwords),
+                "note": "tensor_cores=1: every codeword by XOR / POPC (OR-group lower bounds first), same d, key "
+                        "and counts"}
     if tc_launches:
         bf16 = peaks.get("bf16_tflops")
         bf16_s = peaks.get("bf16_tflops_sustained")
@@ -343,6 +371,7 @@ def run_ours(args):
                        "launches_per_step": res["launches"], "parallelism": f"replicas x{world}",
                        "l2": "flushed (256 MiB write) before every timed step; inputs ~2 KB"},
             "roofline": roofline,
+            "alu_path": alu_path,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": launches,

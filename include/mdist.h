@@ -88,6 +88,17 @@ typedef struct {
                                 quarters); 1 = none; 2 = every block as it is; 3 = as 0
                                 with every block that has a side under 128 subsets split,
                                 whatever its size.  Results are identical. */
+    int skip_idle_sets;      /* 1: at level g leave out the sets whose bound term
+                                max(0, g+1-(k-r_j)) is still 0; a set enumerates the
+                                levels it skipped when its term first becomes positive;
+                                ties are kept and the witness key is the least
+                                (weight, g, j, rank) over the units enumerated (visited
+                                set by set, levels ascending).  d is the same as with 0
+                                (the paper's Alg. 1, every set at every level).  Level
+                                check only (MDIST_EINVAL with check_per_matrix);
+                                single-code handles only (MDIST_EINVAL in batch and
+                                server handles); mdist_run's max_units is rounded up to
+                                whole levels. */
 } mdist_options;
 
 /* Witness key: the least (weight, g, j, rank) over the enumerated units (a total

@@ -72,6 +72,8 @@ def _load():
                                                ctypes.c_int, PI, P64, P64, P64, P64]
             lib.orc_min_distance.argtypes = [P64, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                              ctypes.c_int, ctypes.c_int, ctypes.POINTER(OrcResult)]
+            lib.orc_min_distance_skip.argtypes = [P64, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                                  ctypes.c_int, ctypes.POINTER(OrcResult)]
             lib.orc_unrank_lex.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_uint64]
             lib.orc_unrank_lex.restype = ctypes.c_uint64
             lib.orc_binomial.argtypes = [ctypes.c_int, ctypes.c_int]
@@ -161,14 +163,22 @@ def enumerate_unit(gamma, n: int, g: int, nthreads: int | None = None, want_hist
 
 
 def min_distance(G, n: int, check_per_matrix: bool = False, max_sets: int = MAX_SETS,
-                 nthreads: int | None = None) -> dict:
+                 nthreads: int | None = None, skip_idle_sets: bool = False) -> dict:
     """Alg. 1 (plain Brouwer-Zimmerman).  Returns a dict with d, key (w, g, j, rank),
-    message, witness[W], g_final, j_final, m, ranks, counts[g][j], L_final, U_final."""
+    message, witness[W], g_final, j_final, m, ranks, counts[g][j], L_final, U_final.
+    skip_idle_sets: the sets whose bound term is still 0 are left out until it becomes
+    positive, then catch up (orc_min_distance_skip; level check only)."""
     G = _as_matrix(G, n)
     k, W = G.shape
     res = OrcResult()
-    rc = _load().orc_min_distance(_p64(G), n, k, W, 1 if check_per_matrix else 0, max_sets,
-                                  nthreads or default_threads(), ctypes.byref(res))
+    if skip_idle_sets:
+        if check_per_matrix:
+            raise ValueError("skip_idle_sets works with the level check only")
+        rc = _load().orc_min_distance_skip(_p64(G), n, k, W, max_sets, nthreads or default_threads(),
+                                           ctypes.byref(res))
+    else:
+        rc = _load().orc_min_distance(_p64(G), n, k, W, 1 if check_per_matrix else 0, max_sets,
+                                      nthreads or default_threads(), ctypes.byref(res))
     if rc == -2:
         raise ValueError("rank(G) < k")
     if rc != 0:

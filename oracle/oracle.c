@@ -27,6 +27,13 @@
  *                             L(g) = sum_j max(0, g+1-(k-r_j)) (Alg. 1 line 7 written
  *                             for any number of sets, each of rank r_j).
  *
+ *   orc_min_distance_skip  -- the same loop with the sets whose bound term
+ *                             max(0, g+1-(k-r_j)) is still 0 left out; a set first
+ *                             enumerated at level g first runs the levels it skipped
+ *                             (1 .. g), so that its term counts all of its combinations
+ *                             of weight <= g.  The key is the least (weight, g, j, rank)
+ *                             over the units run.
+ *
  * Bit layout: an R x n matrix is R rows of W uint64 words, bit i of a row in word i>>6
  * at bit i&63.  Parallelism: POSIX threads over the first element of each combination
  * with a shared counter (the dynamic schedule over the first recursion level of §4.3).
@@ -366,6 +373,74 @@ typedef struct {
 static int set_bound(int h, int k, int r) {
     int v = h + 1 - (k - r);
     return v > 0 ? v : 0;
+}
+
+/* (w, g, j, rank) < (key_w, key_g, key_j, key_rank) of out, lexicographically */
+static int key_before(const orc_result *out, int w, int g, int j, u64 rank) {
+    if (w != out->key_w) return w < out->key_w;
+    if (g != out->key_g) return g < out->key_g;
+    if (j != out->key_j) return j < out->key_j;
+    return rank < out->key_rank;
+}
+
+static void witness_of_key(const u64 *G, int k, int W, const u64 *tr, orc_result *out) {
+    u64 c = orc_unrank_lex(k, out->key_g, out->key_rank);
+    u64 msg = 0;
+    for (int r = 0; r < k; r++)
+        if ((c >> r) & 1) msg ^= tr[(size_t)out->key_j * k + r];
+    out->message = msg;
+    for (int b = 0; b < k; b++)
+        if ((msg >> b) & 1)
+            for (int w = 0; w < W; w++) out->witness[w] ^= G[(size_t)b * W + w];
+}
+
+int orc_min_distance_skip(const u64 *G, int n, int k, int W, int max_sets, int nthreads, orc_result *out) {
+    if (check_shape(G, n, k, W) != ORC_OK || !out) return ORC_EINVAL;
+    memset(out, 0, sizeof *out);
+    int m = 0;
+    int *ranks = (int *)calloc(ORC_MAX_SETS, sizeof(int));
+    int *piv = (int *)calloc((size_t)ORC_MAX_SETS * k, sizeof(int));
+    u64 *gam = (u64 *)calloc((size_t)ORC_MAX_SETS * k * W, sizeof(u64));
+    u64 *tr = (u64 *)calloc((size_t)ORC_MAX_SETS * k, sizeof(u64));
+    int *done = (int *)calloc(ORC_MAX_SETS, sizeof(int));  /* levels run per set */
+    if (!ranks || !piv || !gam || !tr || !done) {
+        free(ranks); free(piv); free(gam); free(tr); free(done);
+        return ORC_ENOMEM;
+    }
+    int rc = orc_partition(G, n, k, W, max_sets, &m, ranks, piv, gam, tr);
+    if (rc != ORC_OK) { free(ranks); free(piv); free(gam); free(tr); free(done); return rc; }
+    out->m = m;
+    for (int j = 0; j < m; j++) out->ranks[j] = ranks[j];
+
+    int L = 1, U = n - k + 1;
+    int have_key = 0;
+    int g = 1;
+    while (g <= k && L < U) {
+        for (int j = 0; j < m; j++) {
+            if (set_bound(g, k, ranks[j]) == 0) continue;    /* idle at this level */
+            for (int h = done[j] + 1; h <= g; h++) {        /* catch up, then level g */
+                int w; u64 rank, cnt;
+                orc_enumerate_unit(gam + (size_t)j * k * W, n, k, W, h, nthreads, &w, &rank, &cnt, NULL, NULL);
+                out->counts[h * ORC_MAX_SETS + j] = cnt;
+                out->g_final = h; out->j_final = j;
+                if (!have_key || key_before(out, w, h, j, rank)) {
+                    out->key_w = w; out->key_g = h; out->key_j = j; out->key_rank = rank;
+                    have_key = 1;
+                }
+                if (w < U) U = w;
+            }
+            done[j] = g;
+        }
+        L = 0;
+        for (int i = 0; i < m; i++) L += set_bound(g, k, ranks[i]);
+        if (L >= U) break;
+        g++;
+    }
+    out->d = U;
+    out->L_final = L; out->U_final = U;
+    witness_of_key(G, k, W, tr, out);
+    free(ranks); free(piv); free(gam); free(tr); free(done);
+    return ORC_OK;
 }
 
 int orc_min_distance(const u64 *G, int n, int k, int W, int check_per_matrix, int max_sets, int nthreads,

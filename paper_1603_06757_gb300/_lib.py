@@ -43,6 +43,7 @@ class Options(ctypes.Structure):
         ("alloc_ctx", ctypes.c_void_p),
         ("wstar_hint", ctypes.c_int),
         ("tensor_cores", ctypes.c_int),
+        ("skip_idle_sets", ctypes.c_int),
     ]
 
 

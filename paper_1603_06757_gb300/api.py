@@ -62,8 +62,8 @@ class Code:
     """A prepared code: information sets on the host, packed Gamma_j on the device."""
 
     def __init__(self, G, n: int, *, check_per_matrix: bool = False, max_sets: int = 0, blocks_per_sm: int = 0,
-                 filter_group: int = 0, wstar_hint: int = 0, tensor_cores: int = 0, stream=None,
-                 torch_alloc: bool = True):
+                 filter_group: int = 0, wstar_hint: int = 0, tensor_cores: int = 0, skip_idle_sets: bool = False,
+                 stream=None, torch_alloc: bool = True):
         torch = _torch()
         self.n = int(n)
         self.G = as_packed(G, n)
@@ -78,6 +78,7 @@ class Code:
         opts.filter_group = int(filter_group)
         opts.wstar_hint = int(wstar_hint)
         opts.tensor_cores = int(tensor_cores)
+        opts.skip_idle_sets = 1 if skip_idle_sets else 0
         if self._alloc is not None:
             opts.dev_alloc = self._alloc.alloc_cb
             opts.dev_free = self._alloc.free_cb

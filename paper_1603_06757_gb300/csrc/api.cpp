@@ -35,6 +35,7 @@ struct RunState {
     double seconds = 0.0;
     uint64_t h2d_bytes = 0, d2h_bytes = 0;
     int last_group = 0;
+    int done_level[MDIST_MAX_SETS];  // skip_idle_sets: highest level enumerated per set
     uint64_t counts[MDIST_MAX_K + 1][MDIST_MAX_SETS];
 };
 
@@ -394,7 +395,8 @@ int mdist_prepare(const uint64_t *G, int n, int k, int words_per_row, const mdis
     mdist_code *c = new (std::nothrow) mdist_code();
     if (!c) return MDIST_ENOMEM;
     if (opts) c->opt = *opts;
-    if (c->opt.filter_group < 0 || c->opt.filter_group > 5 || c->opt.tensor_cores < 0 || c->opt.tensor_cores > 3) {
+    if (c->opt.filter_group < 0 || c->opt.filter_group > 5 || c->opt.tensor_cores < 0 || c->opt.tensor_cores > 3 ||
+        c->opt.skip_idle_sets < 0 || c->opt.skip_idle_sets > 1 || (c->opt.skip_idle_sets && c->opt.check_per_matrix)) {
         delete c;
         return MDIST_EINVAL;
     }
@@ -510,37 +512,26 @@ int mdist_unit_histogram(mdist_code *c, int g, int j, uint64_t *hist, uint64_t *
     return MDIST_OK;
 }
 
-// One wave: the units from (next_g, next_j) through the end of level g_hi (at most
-// max_units of them) are launched back to back, each with its own slot, sharing one
-// candidate threshold (the current best weight, ties kept); one host synchronisation;
-// then their results are folded in (g, j) order with the bounds checked after every
-// unit (per-matrix mode) or level, exactly as if the units had run one at a time: a
-// codeword first met past the termination level weighs at least L >= U, so the shared
-// threshold never prunes the unit holding the final U, and folding stops at the
-// termination unit.
-static int run_wave(mdist_code *c, int g_hi, int max_units, int *units_done) {
+struct UnitRef {
+    int g, j;
+};
+
+// Launch the units of `list` back to back, each with its own slot, sharing one
+// candidate threshold that starts at U_thr (candidates: weight <= threshold); one host
+// synchronisation; the results are left in c->h_wave[0 .. list.size()).  The list is
+// cut at the first unit beyond the device key range (MDIST_ERANGE when that is the
+// first one).
+static int launch_units(mdist_code *c, std::vector<UnitRef> &list, int U_thr) {
     RunState &s = c->st;
-    struct U2 { int g, j; };
-    std::vector<U2> list;
-    for (int g = s.next_g; g <= g_hi && g <= c->k; ++g)
-        for (int j = (g == s.next_g ? s.next_j : 0); j < c->m; ++j) {
-            if (max_units > 0 && (int)list.size() >= max_units) break;
-            list.push_back({g, j});
-        }
-    if (list.empty()) return MDIST_OK;
-    const int nu = (int)list.size();
     EnumParams p{};
-    for (int u = 0; u < nu; ++u) {  // every level must be within the device key range
-        if (!mdist::plan_level(c->k, list[(size_t)u].g, c->rows[(size_t)list[(size_t)u].j].nwords, p)) {
+    for (size_t u = 0; u < list.size(); ++u) {  // every level must be within the device key range
+        if (!mdist::plan_level(c->k, list[u].g, c->rows[(size_t)list[u].j].nwords, p)) {
             if (u == 0) return MDIST_ERANGE;
-            list.resize((size_t)u);
+            list.resize(u);
             break;
         }
     }
     const int n_units = (int)list.size();
-    // every unit of the wave follows the key's unit in (g, j) order, so only lighter
-    // codewords can replace the key; weights found inside the wave keep their ties
-    const int U_thr = s.have_key ? s.key.weight - 1 : s.U;
     for (int u = 0; u < n_units; ++u) {
         c->h_wave[u].U = 0;
         c->h_wave[u].status = 0;
@@ -607,6 +598,32 @@ static int run_wave(mdist_code *c, int g_hi, int max_units, int *units_done) {
         }
     for (int u = 0; u < n_units; ++u)
         if (c->h_wave[u].status) return MDIST_ETIMEOUT;
+    return MDIST_OK;
+}
+
+// One wave: the units from (next_g, next_j) through the end of level g_hi (at most
+// max_units of them) are launched back to back, each with its own slot, sharing one
+// candidate threshold (the current best weight, ties kept); one host synchronisation;
+// then their results are folded in (g, j) order with the bounds checked after every
+// unit (per-matrix mode) or level, exactly as if the units had run one at a time: a
+// codeword first met past the termination level weighs at least L >= U, so the shared
+// threshold never prunes the unit holding the final U, and folding stops at the
+// termination unit.
+static int run_wave(mdist_code *c, int g_hi, int max_units, int *units_done) {
+    RunState &s = c->st;
+    std::vector<UnitRef> list;
+    for (int g = s.next_g; g <= g_hi && g <= c->k; ++g)
+        for (int j = (g == s.next_g ? s.next_j : 0); j < c->m; ++j) {
+            if (max_units > 0 && (int)list.size() >= max_units) break;
+            list.push_back({g, j});
+        }
+    if (list.empty()) return MDIST_OK;
+    // every unit of the wave follows the key's unit in (g, j) order, so only lighter
+    // codewords can replace the key; weights found inside the wave keep their ties
+    const int U_thr = s.have_key ? s.key.weight - 1 : s.U;
+    const int rc = launch_units(c, list, U_thr);
+    if (rc != MDIST_OK) return rc;
+    const int n_units = (int)list.size();
     // fold in (g, j) order
     for (int u = 0; u < n_units && !s.finished; ++u) {
         const int g = list[(size_t)u].g, j = list[(size_t)u].j;
@@ -645,6 +662,53 @@ static int run_wave(mdist_code *c, int g_hi, int max_units, int *units_done) {
     return MDIST_OK;
 }
 
+// skip_idle_sets: level g = next_g.  A set whose bound term t_j(g) = max(0, g+1-(k-r_j))
+// is still 0 is left out; a set enumerated for the first time at level g first runs the
+// levels it skipped (done_level[j]+1 .. g), so that its term rests on all of its
+// combinations of weight <= g.  All units of the level are one wave; ties are
+// candidates and the key is the least (weight, g, j, rank) over the enumerated units,
+// visited set by set with levels ascending.
+static int run_skip_level(mdist_code *c, int *units_done) {
+    RunState &s = c->st;
+    const int g = s.next_g;
+    std::vector<UnitRef> list;
+    for (int j = 0; j < c->m; ++j)
+        if (set_bound(g, c->k, c->part.sets[(size_t)j].rank) > 0)
+            for (int h = s.done_level[j] + 1; h <= g; ++h) list.push_back({h, j});
+    if (!list.empty()) {
+        const size_t want = list.size();
+        const int rc = launch_units(c, list, s.U);
+        if (rc != MDIST_OK) return rc;
+        if (list.size() != want) return MDIST_ERANGE;
+        for (size_t u = 0; u < list.size(); ++u) {
+            const int h = list[u].g, j = list[u].j;
+            const UnitSlot &r = c->h_wave[u];
+            s.counts[h][j] = r.count;
+            s.g_last = h;
+            s.j_last = j;
+            s.done_level[j] = h;
+            ++*units_done;
+            if (r.key != mdist::kNoKey) {
+                const int w = (int)(r.key >> mdist::kKeyRankBits);
+                const mdist_key cand{w, h, j, 0, r.key & ((1ull << mdist::kKeyRankBits) - 1)};
+                if (!s.have_key || key_less(cand, s.key)) {
+                    s.key = cand;
+                    s.have_key = 1;
+                }
+                if (w < s.U) s.U = w;
+            }
+        }
+    }
+    int Lg = 0;  // Alg. 1, line 7: the idle sets' terms are 0
+    for (int i = 0; i < c->m; ++i) Lg += set_bound(g, c->k, c->part.sets[(size_t)i].rank);
+    s.L = Lg;
+    if (s.L >= s.U) s.finished = 1;
+    s.next_g = g + 1;
+    s.next_j = 0;
+    if (s.next_g > c->k) s.finished = 1;
+    return MDIST_OK;
+}
+
 int mdist_reset(mdist_code *c) {
     if (!c) return MDIST_EINVAL;
     reset_state(c);
@@ -658,6 +722,11 @@ int mdist_run(mdist_code *c, int max_units, int *finished) {
     int units = 0;
     int rc = MDIST_OK;
     while (!s.finished && (max_units <= 0 || units < max_units)) {
+        if (c->opt.skip_idle_sets) {
+            rc = run_skip_level(c, &units);
+            if (rc != MDIST_OK) break;
+            continue;
+        }
         // first wave: every level below the predicted termination level at once
         int g_hi = s.next_g;
         if (c->opt.wstar_hint > 1 && s.next_g == 1 && s.next_j == 0) g_hi = std::min(c->k, c->opt.wstar_hint - 1);

@@ -331,7 +331,8 @@ void serve_loop(mdist_server *s) {
 extern "C" {
 
 int mdist_server_create(const mdist_options *opts, int max_slots, size_t rows_pool_bytes, mdist_server **out) {
-    if (!out || max_slots < 1 || max_slots > (1 << 16) || rows_pool_bytes < 4096) return MDIST_EINVAL;
+    if (!out || max_slots < 1 || max_slots > (1 << 16) || rows_pool_bytes < 4096 || (opts && opts->skip_idle_sets))
+        return MDIST_EINVAL;
     *out = nullptr;
     mdist_server *s = new (std::nothrow) mdist_server();
     if (!s) return MDIST_ENOMEM;

@@ -1,0 +1,67 @@
+"""skip_idle_sets on the GPU: every output (d, key, message, witness, counts, last unit)
+equal to the oracle's skip mode, on codes whose partial sets are idle at the low
+levels; the [150,64] config (a rank-22 set, idle below level 42) gives the same d with
+a third less work; the mode is refused with the per-matrix check."""
+
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from synth.configs import single_code
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def api():
+    import torch
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    assert torch.cuda.is_available()
+    from paper_1603_06757_gb300 import api as a
+
+    return a
+
+
+CASES = [(30 + s % 9, 20, s) for s in range(1, 241, 8)] + [(60, 36, 3), (70, 40, 5), (96, 48, 7), (90, 64, 2)]
+
+
+@pytest.mark.parametrize("tc", [0, 2])
+@pytest.mark.parametrize("n,k,seed", CASES)
+def test_skip_mode_vs_oracle(api, tc, n, k, seed):
+    G = synth.random_systematic(n, k, seed)
+    want = oracle.min_distance(G, n, skip_idle_sets=True)
+    with api.Code(G, n, skip_idle_sets=True, tensor_cores=tc) as c:
+        got = c.min_distance()
+    for key in ("d", "key", "message", "g_final", "j_final", "L_final"):
+        assert got[key] == want[key], key
+    assert np.array_equal(got["witness"], want["witness"])
+    assert np.array_equal(got["counts"], want["counts"])
+
+
+def test_skip_mode_150x64(api):
+    n, k, seed, G = single_code("150x64", lambda G, n, k: [int(r) for r in oracle.partition(G, n)["ranks"]])
+    with api.Code(G, n) as c:
+        full = c.min_distance()
+    with api.Code(G, n, skip_idle_sets=True) as c:
+        skip = c.min_distance()
+    assert full["ranks"] == [64, 64, 22]
+    assert skip["d"] == full["d"]
+    assert int(skip["counts"][:, 2].sum()) == 0  # the rank-22 set never contributes
+    assert skip["total_combos"] < 0.7 * full["total_combos"]
+    msg = np.array([(skip["message"] >> b) & 1 for b in range(k)], dtype=np.int64)
+    cw = (msg @ synth.unpack_bits(G, n).astype(np.int64)) % 2
+    assert int(cw.sum()) == skip["d"]
+
+
+def test_skip_mode_refused_with_per_matrix_check(api):
+    from paper_1603_06757_gb300 import _lib as L
+
+    G = synth.random_systematic(40, 20, 1)
+    with pytest.raises(L.MdistError):
+        api.Code(G, 40, skip_idle_sets=True, check_per_matrix=True)

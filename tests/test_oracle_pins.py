@@ -325,3 +325,58 @@ def test_planted_mistake_is_caught():
             caught = True
             break
     assert caught
+
+
+def _skip_codes():
+    # rate > 1/2: the greedy sets after the first are partial, so some sets are idle at
+    # the low levels
+    out = []
+    for seed in range(1, 241):
+        n, k = 30 + seed % 9, 20
+        out.append((n, k, synth.random_systematic(n, k, seed)))
+    return out
+
+
+def test_skip_idle_sets_equals_bruteforce():
+    # the mode that leaves idle sets out (and lets them catch up) reaches the same d as
+    # the plain definition, enumerates each set's levels as a prefix 1..h_j, and its key
+    # is a codeword of weight d
+    saved = 0
+    for n, k, G in _skip_codes():
+        d = oracle.brute_force_distance(G, n)
+        r = oracle.min_distance(G, n, skip_idle_sets=True)
+        full = oracle.min_distance(G, n)
+        assert r["d"] == d == full["d"]
+        assert r["key"][0] == d
+        cw = synth.unpack_bits(r["witness"][None, :], n)[0]
+        assert int(cw.sum()) == d
+        msg = np.array([(r["message"] >> b) & 1 for b in range(k)], dtype=np.int64)
+        assert np.array_equal((msg @ synth.unpack_bits(G, n).astype(np.int64)) % 2, cw.astype(np.int64))
+        for j in range(r["m"]):
+            col = [int(x) for x in r["counts"][1:, j]]
+            h = sum(1 for x in col if x)
+            assert all(col[g - 1] == math.comb(k, g) for g in range(1, h + 1)), (j, col)
+            assert all(x == 0 for x in col[h:])
+        saved += int(full["counts"].sum()) - int(r["counts"].sum())
+    assert saved > 0
+
+
+def test_skip_without_catch_up_is_caught():
+    # planted mistake: idle sets left out but never caught up; the comparison with brute
+    # force has to catch it on some code of the same family
+    caught = 0
+    for n, k, G in _skip_codes():
+        part = oracle.partition(G, n)
+        ranks = [int(x) for x in part["ranks"]]
+        U, L, g = n - k + 1, 1, 1
+        while g <= k and L < U:
+            for j in range(part["m"]):
+                if max(0, g + 1 - (k - ranks[j])) > 0:
+                    U = min(U, oracle.enumerate_unit(part["gammas"][j], n, g, want_hist=False)["min_w"])
+            L = sum(max(0, g + 1 - (k - r)) for r in ranks)
+            if L >= U:
+                break
+            g += 1
+        if U != oracle.brute_force_distance(G, n):
+            caught += 1
+    assert caught > 0
