@@ -68,6 +68,13 @@ struct mdist_code {
     // tables of the tensor-core enumerator (side_key: set, side components, expanded)
     std::map<uint64_t, void *> tabs;
     size_t tab_bytes = 0;
+    // tables allocated but not built yet (all of one set), built together by flush_tables
+    int pend_j = -1;
+    std::vector<mdist::GramSide> pend_sides;
+    std::vector<uint32_t *> pend_outs;
+    std::vector<const uint32_t *> pend_xpacked;
+    std::vector<unsigned long long> pend_xcount;
+    std::vector<uint8_t *> pend_xout;
     RunState st;
 };
 
@@ -153,9 +160,36 @@ uint64_t side_key(int j, const mdist::GramSide &S, bool expanded) {
     return key;
 }
 
+// Build the pending tables of set c->pend_j: one launch for the packed sums, one for
+// the expansions (after them, on the same stream).
+int flush_tables(mdist_code *c) {
+    if (c->pend_j < 0) return MDIST_OK;
+    const DeviceRows &dr = c->rows[(size_t)c->pend_j];
+    cudaError_t e = cudaSuccess;
+    for (size_t i = 0; i < c->pend_sides.size() && e == cudaSuccess; i += mdist::kMaxTableJobs) {
+        const int n = (int)std::min<size_t>(mdist::kMaxTableJobs, c->pend_sides.size() - i);
+        e = mdist::launch_side_tables(c->d_rows[(size_t)c->pend_j], c->k, dr.nwords, &c->pend_sides[i],
+                                      &c->pend_outs[i], n, c->sm_count, c->stream);
+        c->st.launches += 1;
+    }
+    for (size_t i = 0; i < c->pend_xout.size() && e == cudaSuccess; i += mdist::kMaxTableJobs) {
+        const int n = (int)std::min<size_t>(mdist::kMaxTableJobs, c->pend_xout.size() - i);
+        e = mdist::launch_expand_tables(dr.nwords, dr.n_bits, &c->pend_xpacked[i], &c->pend_xcount[i],
+                                        &c->pend_xout[i], n, c->sm_count, c->stream);
+        c->st.launches += 1;
+    }
+    c->pend_j = -1;
+    c->pend_sides.clear();
+    c->pend_outs.clear();
+    c->pend_xpacked.clear();
+    c->pend_xcount.clear();
+    c->pend_xout.clear();
+    return e == cudaSuccess ? MDIST_OK : MDIST_ECUDA;
+}
+
 // Table of the sums of a side's entries of set j and, with `expanded`, its expansion to
-// tensor-core operand tiles; built on first use and kept for later levels and runs;
-// null when over budget.
+// tensor-core operand tiles; allocated on first use (built by the next flush_tables)
+// and kept for later levels and runs; null when over budget.
 int side_table(mdist_code *c, int j, const mdist::GramSide &S, bool expanded, const void **out) {
     *out = nullptr;
     const uint64_t key = side_key(j, S, expanded);
@@ -163,6 +197,10 @@ int side_table(mdist_code *c, int j, const mdist::GramSide &S, bool expanded, co
     if (it != c->tabs.end()) {
         *out = it->second;
         return MDIST_OK;
+    }
+    if (c->pend_j >= 0 && c->pend_j != j) {
+        const int rc = flush_tables(c);
+        if (rc != MDIST_OK) return rc;
     }
     const DeviceRows &dr = c->rows[(size_t)j];
     const void *packed = nullptr;
@@ -175,18 +213,17 @@ int side_table(mdist_code *c, int j, const mdist::GramSide &S, bool expanded, co
     if (c->tab_bytes + bytes > kTableBudget) return MDIST_OK;
     void *d = dev_alloc(c, bytes);
     if (!d) return MDIST_OK;
-    const cudaError_t e =
-        expanded ? mdist::launch_expand_table((const uint32_t *)packed, dr.nwords, S.n, dr.n_bits, (uint8_t *)d,
-                                              c->sm_count, c->stream)
-                 : mdist::launch_side_table(c->d_rows[(size_t)j], c->k, dr.nwords, S, (uint32_t *)d, c->sm_count,
-                                            c->stream);
-    if (e != cudaSuccess) {
-        dev_release(c, d);
-        return MDIST_ECUDA;
+    c->pend_j = j;
+    if (expanded) {
+        c->pend_xpacked.push_back((const uint32_t *)packed);
+        c->pend_xcount.push_back(S.n);
+        c->pend_xout.push_back((uint8_t *)d);
+    } else {
+        c->pend_sides.push_back(S);
+        c->pend_outs.push_back((uint32_t *)d);
     }
     c->tabs[key] = d;
     c->tab_bytes += bytes;
-    c->st.launches += 1;
     *out = d;
     return MDIST_OK;
 }
@@ -259,7 +296,7 @@ int gram_plan(mdist_code *c, int j, const EnumParams &p, std::vector<mdist::Gram
         if (all) covered[b] = true;
         else out.resize(mark);  // a table over budget: the whole block stays on the ALU kernel
     }
-    return MDIST_OK;
+    return flush_tables(c);
 }
 
 // One (g, j) unit on the GPU.  Candidates: codewords of weight <= U_thr.

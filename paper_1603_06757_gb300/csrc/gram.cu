@@ -370,17 +370,47 @@ cudaError_t gram_launch_nw(const GramParams &p, int sm_count, cudaStream_t strea
     return cudaGetLastError();
 }
 
-// out[e * NW ..] = the sum of the rows of side entry e (rows: the k rows of the set)
+// Several tables in one launch: job i covers the global entries [begin[i], begin[i+1]).
+struct SideJobs {
+    int njobs;
+    unsigned long long begin[kMaxTableJobs + 1];
+    GramSide side[kMaxTableJobs];
+    uint32_t *out[kMaxTableJobs];
+};
+
+struct ExpandJobs {
+    int njobs, n_bits;
+    unsigned long long begin[kMaxTableJobs + 1];  // padded rows (multiples of kGN)
+    unsigned long long count[kMaxTableJobs];
+    const uint32_t *packed[kMaxTableJobs];
+    uint8_t *out[kMaxTableJobs];
+};
+
+template <int N>
+__device__ __forceinline__ int job_of(const unsigned long long (&begin)[N], int njobs, unsigned long long e) {
+    int lo = 0, hi = njobs - 1;  // last job with begin <= e
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (begin[mid] <= e) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// out_i[e * NW ..] = the sum of the rows of entry e of side i (rows: the k rows of the set)
 template <int NW>
-__global__ void side_table_kernel(const uint32_t *rows, int k, GramSide side, uint32_t *out) {
+__global__ void side_tables_kernel(const uint32_t *rows, int k, const __grid_constant__ SideJobs J) {
     __shared__ uint32_t s_bn[kBn * kBn];
     __shared__ uint32_t s_rows[64 * NW];
     for (int i = threadIdx.x; i < kBn * kBn; i += blockDim.x) s_bn[i] = (uint32_t)c_binom_g.v[i / kBn][i % kBn];
     for (int i = threadIdx.x; i < k * NW; i += blockDim.x) s_rows[i] = rows[i];
     __syncthreads();
-    for (unsigned long long e = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; e < side.n;
-         e += (unsigned long long)gridDim.x * blockDim.x) {
-        unsigned long long m = side_mask(s_bn, side, e);
+    const unsigned long long total = J.begin[J.njobs];
+    for (unsigned long long g = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; g < total;
+         g += (unsigned long long)gridDim.x * blockDim.x) {
+        const int i = job_of(J.begin, J.njobs, g);
+        const unsigned long long e = g - J.begin[i];
+        unsigned long long m = side_mask(s_bn, J.side[i], e);
         uint32_t x[NW];
 #pragma unroll
         for (int w = 0; w < NW; ++w) x[w] = 0;
@@ -390,63 +420,71 @@ __global__ void side_table_kernel(const uint32_t *rows, int k, GramSide side, ui
 #pragma unroll
             for (int w = 0; w < NW; ++w) x[w] ^= s_rows[r * NW + w];
         }
+        uint32_t *out = J.out[i];
 #pragma unroll
         for (int w = 0; w < NW; ++w) out[e * NW + w] = x[w];
     }
 }
 
-// B tiles of a packed table: row e of tile e / kGN is the sign row of entry e (write_row
-// with the code's n_bits); rows past `count` are padding (zero bytes).
+// B tiles of packed tables: row e of tile e / kGN of job i is the sign row of entry e
+// (write_row with the code's n_bits); rows past the job's count are padding (zeros).
 template <int NW>
-__global__ void expand_table_kernel(const uint32_t *packed, unsigned long long count, unsigned long long rows,
-                                    int n_bits, uint8_t *out) {
+__global__ void expand_tables_kernel(const __grid_constant__ ExpandJobs J) {
     constexpr int KA = gram_ka(NW);
-    for (unsigned long long e = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; e < rows;
-         e += (unsigned long long)gridDim.x * blockDim.x) {
+    const unsigned long long total = J.begin[J.njobs];
+    for (unsigned long long g = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; g < total;
+         g += (unsigned long long)gridDim.x * blockDim.x) {
+        const int i = job_of(J.begin, J.njobs, g);
+        const unsigned long long e = g - J.begin[i], count = J.count[i];
+        const uint32_t *packed = J.packed[i];
         uint32_t y[NW];
 #pragma unroll
         for (int w = 0; w < NW; ++w) y[w] = e < count ? packed[e * NW + w] : 0u;
-        write_row<NW>(out + (e / kGN) * (unsigned long long)(kGN * KA), (int)(e % kGN), y,
-                      e < count ? n_bits : 0);
+        write_row<NW>(J.out[i] + (e / kGN) * (unsigned long long)(kGN * KA), (int)(e % kGN), y,
+                      e < count ? J.n_bits : 0);
     }
 }
 
-template <int NW>
-cudaError_t table_launch_nw(const uint32_t *rows, int k, const GramSide &side, uint32_t *out, int sm_count,
-                            cudaStream_t stream) {
-    unsigned long long grid = (side.n + 255) / 256;
+unsigned int table_grid(unsigned long long work, int sm_count) {
+    unsigned long long grid = (work + 255) / 256;
     const unsigned long long cap = (unsigned long long)sm_count * 8;
     if (grid > cap) grid = cap;
-    if (grid < 1) grid = 1;
-    side_table_kernel<NW><<<(unsigned int)grid, 256, 0, stream>>>(rows, k, side, out);
+    return (unsigned int)(grid < 1 ? 1 : grid);
+}
+
+template <int NW>
+cudaError_t side_tables_nw(const uint32_t *rows, int k, const SideJobs &J, int sm_count, cudaStream_t stream) {
+    side_tables_kernel<NW><<<table_grid(J.begin[J.njobs], sm_count), 256, 0, stream>>>(rows, k, J);
     return cudaGetLastError();
 }
 
 template <int NW>
-cudaError_t expand_launch_nw(const uint32_t *packed, unsigned long long count, int n_bits, uint8_t *out,
-                             int sm_count, cudaStream_t stream) {
-    const unsigned long long rows = (count + kGN - 1) / kGN * kGN;
-    unsigned long long grid = (rows + 255) / 256;
-    const unsigned long long cap = (unsigned long long)sm_count * 8;
-    if (grid > cap) grid = cap;
-    if (grid < 1) grid = 1;
-    expand_table_kernel<NW><<<(unsigned int)grid, 256, 0, stream>>>(packed, count, rows, n_bits, out);
+cudaError_t expand_tables_nw(const ExpandJobs &J, int sm_count, cudaStream_t stream) {
+    expand_tables_kernel<NW><<<table_grid(J.begin[J.njobs], sm_count), 256, 0, stream>>>(J);
     return cudaGetLastError();
 }
 
 }  // namespace
 
-cudaError_t launch_side_table(const uint32_t *rows, int k, int nwords, const GramSide &side, uint32_t *out,
-                              int sm_count, cudaStream_t stream) {
-    if (k < 1 || k > 64) return cudaErrorInvalidValue;
+cudaError_t launch_side_tables(const uint32_t *rows, int k, int nwords, const GramSide *sides, uint32_t *const *outs,
+                               int n, int sm_count, cudaStream_t stream) {
+    if (k < 1 || k > 64 || n < 0 || n > kMaxTableJobs) return cudaErrorInvalidValue;
+    if (n == 0) return cudaSuccess;
+    SideJobs J{};
+    J.njobs = n;
+    for (int i = 0; i < n; ++i) {
+        J.side[i] = sides[i];
+        J.out[i] = outs[i];
+        J.begin[i + 1] = J.begin[i] + sides[i].n;
+    }
     switch (nwords) {
-        case 1: return table_launch_nw<1>(rows, k, side, out, sm_count, stream);
-        case 2: return table_launch_nw<2>(rows, k, side, out, sm_count, stream);
-        case 3: return table_launch_nw<3>(rows, k, side, out, sm_count, stream);
-        case 4: return table_launch_nw<4>(rows, k, side, out, sm_count, stream);
-        case 5: return table_launch_nw<5>(rows, k, side, out, sm_count, stream);
-        case 6: return table_launch_nw<6>(rows, k, side, out, sm_count, stream);
-        case 7: return table_launch_nw<7>(rows, k, side, out, sm_count, stream);
+        case 1: return side_tables_nw<1>(rows, k, J, sm_count, stream);
+        case 2: return side_tables_nw<2>(rows, k, J, sm_count, stream);
+        case 3: return side_tables_nw<3>(rows, k, J, sm_count, stream);
+        case 4: return side_tables_nw<4>(rows, k, J, sm_count, stream);
+        case 5: return side_tables_nw<5>(rows, k, J, sm_count, stream);
+        case 6: return side_tables_nw<6>(rows, k, J, sm_count, stream);
+        case 7: return side_tables_nw<7>(rows, k, J, sm_count, stream);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -455,16 +493,28 @@ size_t gram_expanded_bytes(int nwords, unsigned long long count) {
     return (size_t)((count + kGN - 1) / kGN) * (size_t)kGN * (size_t)gram_ka(nwords);
 }
 
-cudaError_t launch_expand_table(const uint32_t *packed, int nwords, unsigned long long count, int n_bits,
-                                uint8_t *out, int sm_count, cudaStream_t stream) {
+cudaError_t launch_expand_tables(int nwords, int n_bits, const uint32_t *const *packed,
+                                 const unsigned long long *counts, uint8_t *const *outs, int n, int sm_count,
+                                 cudaStream_t stream) {
+    if (n < 0 || n > kMaxTableJobs) return cudaErrorInvalidValue;
+    if (n == 0) return cudaSuccess;
+    ExpandJobs J{};
+    J.njobs = n;
+    J.n_bits = n_bits;
+    for (int i = 0; i < n; ++i) {
+        J.packed[i] = packed[i];
+        J.count[i] = counts[i];
+        J.out[i] = outs[i];
+        J.begin[i + 1] = J.begin[i] + (counts[i] + kGN - 1) / kGN * kGN;
+    }
     switch (nwords) {
-        case 1: return expand_launch_nw<1>(packed, count, n_bits, out, sm_count, stream);
-        case 2: return expand_launch_nw<2>(packed, count, n_bits, out, sm_count, stream);
-        case 3: return expand_launch_nw<3>(packed, count, n_bits, out, sm_count, stream);
-        case 4: return expand_launch_nw<4>(packed, count, n_bits, out, sm_count, stream);
-        case 5: return expand_launch_nw<5>(packed, count, n_bits, out, sm_count, stream);
-        case 6: return expand_launch_nw<6>(packed, count, n_bits, out, sm_count, stream);
-        case 7: return expand_launch_nw<7>(packed, count, n_bits, out, sm_count, stream);
+        case 1: return expand_tables_nw<1>(J, sm_count, stream);
+        case 2: return expand_tables_nw<2>(J, sm_count, stream);
+        case 3: return expand_tables_nw<3>(J, sm_count, stream);
+        case 4: return expand_tables_nw<4>(J, sm_count, stream);
+        case 5: return expand_tables_nw<5>(J, sm_count, stream);
+        case 6: return expand_tables_nw<6>(J, sm_count, stream);
+        case 7: return expand_tables_nw<7>(J, sm_count, stream);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -103,13 +103,18 @@ struct GramBlockSpec {
 };
 cudaError_t launch_gram_unit(const EnumParams &ep, const GramBlockSpec *blocks, int nblocks, unsigned int *U,
                              UnitSlot *slot, int *status, int sm_count, cudaStream_t stream);
-// out[e * nwords ..] = the sum of the rows (rows: all k rows of the set) of side entry e
-cudaError_t launch_side_table(const uint32_t *rows, int k, int nwords, const GramSide &side, uint32_t *out,
-                              int sm_count, cudaStream_t stream);
+// Tables built together (one launch each for the packed sums and for the expansions).
+constexpr int kMaxTableJobs = 128;
+// for i < n: outs[i][e * nwords ..] = the sum of the rows (rows: all k rows of the set)
+// of entry e of sides[i]
+cudaError_t launch_side_tables(const uint32_t *rows, int k, int nwords, const GramSide *sides, uint32_t *const *outs,
+                               int n, int sm_count, cudaStream_t stream);
 // bytes of the expanded operand tiles of a packed table of `count` entries
 size_t gram_expanded_bytes(int nwords, unsigned long long count);
-cudaError_t launch_expand_table(const uint32_t *packed, int nwords, unsigned long long count, int n_bits,
-                                uint8_t *out, int sm_count, cudaStream_t stream);
+// for i < n: outs[i] = the operand tiles of packed[i] (counts[i] entries)
+cudaError_t launch_expand_tables(int nwords, int n_bits, const uint32_t *const *packed,
+                                 const unsigned long long *counts, uint8_t *const *outs, int n, int sm_count,
+                                 cudaStream_t stream);
 // A unit: the tensor-core blocks (may be none), then the product blocks of `p` not
 // marked in `covered` (null: none covered) on the ALU kernel.  When the tensor-core
 // kernel is launched and tc_ev0 / tc_ev1 are given they are recorded around it,
