@@ -68,6 +68,9 @@ struct mdist_code {
     // tables of the tensor-core enumerator (side_key: set, side components, expanded)
     std::map<uint64_t, void *> tabs;
     size_t tab_bytes = 0;
+    // device memory of the tables: chunks from the allocator, handed out in order
+    std::vector<void *> tab_chunks;
+    size_t chunk_used = 0, chunk_size = 0;
     // tables allocated but not built yet (all of one set), built together by flush_tables
     int pend_j = -1;
     std::vector<mdist::GramSide> pend_sides;
@@ -160,6 +163,24 @@ uint64_t side_key(int j, const mdist::GramSide &S, bool expanded) {
     return key;
 }
 
+// Device memory for a table: 256-byte aligned pieces of chunks of at least 64 MiB, so
+// that a run's hundreds of tables cost a handful of allocator calls.
+void *table_alloc(mdist_code *c, size_t bytes) {
+    constexpr size_t kChunk = 64ull << 20, kAlign = 256;
+    bytes = (bytes + kAlign - 1) / kAlign * kAlign;
+    if (c->tab_chunks.empty() || c->chunk_used + bytes > c->chunk_size) {
+        const size_t size = bytes > kChunk ? bytes : kChunk;
+        void *p = dev_alloc(c, size);
+        if (!p) return nullptr;
+        c->tab_chunks.push_back(p);
+        c->chunk_size = size;
+        c->chunk_used = 0;
+    }
+    void *p = (char *)c->tab_chunks.back() + c->chunk_used;
+    c->chunk_used += bytes;
+    return p;
+}
+
 // Build the pending tables of set c->pend_j: one launch for the packed sums, one for
 // the expansions (after them, on the same stream).
 int flush_tables(mdist_code *c) {
@@ -211,7 +232,7 @@ int side_table(mdist_code *c, int j, const mdist::GramSide &S, bool expanded, co
     const size_t bytes = expanded ? mdist::gram_expanded_bytes(dr.nwords, S.n)
                                   : (size_t)S.n * (size_t)dr.nwords * sizeof(uint32_t);
     if (c->tab_bytes + bytes > kTableBudget) return MDIST_OK;
-    void *d = dev_alloc(c, bytes);
+    void *d = table_alloc(c, bytes);
     if (!d) return MDIST_OK;
     c->pend_j = j;
     if (expanded) {
@@ -411,7 +432,7 @@ void mdist_free(mdist_code *c) {
     if (!c) return;
     cudaStreamSynchronize(c->stream);
     for (uint32_t *p : c->d_rows) dev_release(c, p);
-    for (auto &kv : c->tabs) dev_release(c, kv.second);
+    for (void *p : c->tab_chunks) dev_release(c, p);
     dev_release(c, c->d_slot);
     dev_release(c, c->d_hist);
     dev_release(c, c->d_wave);
