@@ -22,6 +22,23 @@
 // shared memory as one bulk copy; A tiles are expanded per work unit from the
 // bit-packed subset sums.
 //
+// Persistent grid, one CTA per SM, 352 threads in four roles:
+//   warps 0-7  epilogue   (warp w: TMEM lanes 32 (w % 4) .. + 31 = rows of the
+//              accumulator tile, columns 128 (w / 4) .. + 127; two packed loads of
+//              64 f16 columns per wait, maximum of the half2 pairs),
+//   warp  8    A builder  (four A rows per lane: load the packed sum, expand),
+//   warp  9    B producer (one lane: a bulk copy of a whole B tile per stage),
+//   warp  10   MMA issue  (one lane) and TMEM allocation.
+// A work unit is (block, 128-row A tile, up to kTilesPerUnit 256-row B tiles); within a
+// block the A tile runs fastest, so the CTAs running at the same time read the same B
+// tiles from L2.  Every role walks the same static sequence of work units (CTA c takes
+// c, c + grid, ...).  Stages: A two, B up to four, accumulators two TMEM buffers of 256
+// columns.  Hand-offs are mbarriers: A and accumulator-full by tcgen05.commit, B full
+// by the copies' transaction bytes, B stages and accumulators freed by the epilogue
+// (its thread 0 frees a B stage once the accumulator-full commit of its tile has
+// arrived).  Every wait is bounded; a timeout sets the status word, and the kernel
+// ends after its copies and MMAs have drained.
+//
 #include <cuda_fp16.h>
 
 #include <cstdint>
