@@ -6,8 +6,11 @@ One step = one whole Alg. 1 run over the prepared code (every (g, j) unit from g
 until L >= U) with d, the witness key and the counters exact.  `value` is timed with
 CUDA events on the launching stream (inputs resident on the device); `e2e` is the same
 run through the C-ABI from host buffers (prepare = information sets + host-to-device
-copy, run, result read back) timed on the host clock.  `--impl reference` times the
-CPU oracle on a bounded sample of the same run.
+copy, run, result read back) timed on the host clock.  `roofline` is the dominant
+kernel's (the tcgen05 enumerator's flops against the measured bf16 tensor peak x 2);
+`alu_path` is the same run on the ALU enumerator alone (`tensor_cores=1`) against the
+integer/POPC roofline.  `--impl reference` times the CPU oracle on a bounded sample of
+the same run.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 """
