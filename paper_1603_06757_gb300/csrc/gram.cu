@@ -8,11 +8,12 @@
 // so the weights of a whole 128 x 256 tile of codewords follow from a Gram matrix: a
 // dense contraction over the n_bits columns.  Operand rows are the signs as E4M3 bytes
 // (+1.0 / -1.0; the B side has zero bytes past n_bits), one kind::f8f6f4 MMA chain
-// with f16 accumulation gives every acc = n_bits - 2 wt(x ^ y) exactly (every partial
-// sum is an integer of magnitude <= n_bits <= 224), and a codeword
-// is a candidate iff acc >= n_bits - 2 thr (thr = largest reduced weight still a
-// candidate).  The epilogue takes the maximum of the accumulators it reads from TMEM;
-// only a maximum at or above that bound sends a lane to the side path, which recomputes
+// with f32 accumulation gives every acc = n_bits - 2 wt(x ^ y) exactly (integers of
+// magnitude <= n_bits <= 224), and a codeword is a candidate iff
+// acc >= n_bits - 2 thr (thr = largest reduced weight still a candidate).  The
+// epilogue reads the accumulators from TMEM with loads that also return their maximum
+// (tcgen05.ld.red .max); only a maximum at or above that bound sends a lane to the
+// side path, which recomputes
 // the weight from the bit-packed rows before touching the key.  A bound read late is
 // only lower, never higher, than the current one: more candidates, all rechecked
 // exactly.
@@ -24,8 +25,8 @@
 //
 // Persistent grid, one CTA per SM, 352 threads in four roles:
 //   warps 0-7  epilogue   (warp w: TMEM lanes 32 (w % 4) .. + 31 = rows of the
-//              accumulator tile, columns 128 (w / 4) .. + 127; two packed loads of
-//              64 f16 columns per wait, maximum of the half2 pairs),
+//              accumulator tile, columns 128 (w / 4) .. + 127; four reducing loads of
+//              32 f32 columns per wait),
 //   warp  8    A builder  (four A rows per lane: load the packed sum, expand),
 //   warp  9    B producer (one lane: a bulk copy of a whole B tile per stage),
 //   warp  10   MMA issue  (one lane) and TMEM allocation.
@@ -39,8 +40,6 @@
 // arrived).  Every wait is bounded; a timeout sets the status word, and the kernel
 // ends after its copies and MMAs have drained.
 //
-#include <cuda_fp16.h>
-
 #include <cstdint>
 
 #include "combinatorics.cuh"
@@ -245,7 +244,7 @@ __global__ void __launch_bounds__(kGramThreads, 1) gram_kernel(const __grid_cons
     } else if (warp == 10) {
         // ---------------- MMA issue ----------------
         if (lane == 0) {
-            const uint32_t idesc = idesc_f8f6f4_e4m3_f16(kGM, kGN);
+            const uint32_t idesc = idesc_f8f6f4_e4m3_f32(kGM, kGN);
             const uint32_t sbo = (uint32_t)(KA / 16) * 128u;
             unsigned long long t = 0, u = 0;
             for (unsigned long long wu = blockIdx.x; wu < P.total_wu && !*s_abort; wu += gridDim.x, ++u) {
@@ -307,17 +306,21 @@ __global__ void __launch_bounds__(kGramThreads, 1) gram_kernel(const __grid_cons
                 // commit, so that no thread but the epilogue waits on commit-driven barriers)
                 if (tid == 0) mbar_arrive(bar(B_EMPTY + (int)(t % S)));
                 const uint32_t base = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(ab * kGN + col0);
-                uint32_t v[2][32];  // 128 f16 accumulators, two per register
-                tmem_ld64_pack16_issue(base, v[0]);
-                tmem_ld64_pack16_issue(base + 64u, v[1]);
+                uint32_t v[4][32];  // 128 f32 accumulators
+                float m0, m1, m2, m3;
+                tmem_ldred32_max_issue(base, v[0], m0);
+                tmem_ldred32_max_issue(base + 32u, v[1], m1);
+                tmem_ldred32_max_issue(base + 64u, v[2], m2);
+                tmem_ldred32_max_issue(base + 96u, v[3], m3);
                 tmem_wait_ld(v[0]);
                 tmem_regs_ready(v[1]);
-                __half2 m2 = *reinterpret_cast<const __half2 *>(&v[0][0]);
-#pragma unroll
-                for (int q = 0; q < 2; ++q)
-#pragma unroll
-                    for (int i = 0; i < 32; ++i) m2 = __hmax2(m2, *reinterpret_cast<const __half2 *>(&v[q][i]));
-                const float m = fmaxf(__low2float(m2), __high2float(m2));
+                tmem_regs_ready(v[2]);
+                tmem_regs_ready(v[3]);
+                float_ready(m0);
+                float_ready(m1);
+                float_ready(m2);
+                float_ready(m3);
+                const float m = fmaxf(fmaxf(m0, m1), fmaxf(m2, m3));
                 if (m >= bound && a_valid) {
                     // side path: which columns reach the bound, then the exact weight from
                     // the bit-packed rows, then the key
@@ -325,18 +328,14 @@ __global__ void __launch_bounds__(kGramThreads, 1) gram_kernel(const __grid_cons
 #pragma unroll
                     for (int w = 0; w < NW; ++w) x[w] = B.a_tab[a_e * NW + w];
 #pragma unroll
-                    for (int q = 0; q < 2; ++q) {
-                        unsigned long long neg = 0;
+                    for (int q = 0; q < 4; ++q) {
+                        uint32_t neg = 0;
 #pragma unroll
-                        for (int i = 0; i < 32; ++i) {
-                            const __half2 h = *reinterpret_cast<const __half2 *>(&v[q][i]);
-                            neg |= (unsigned long long)(__low2float(h) >= bound ? 1u : 0u) << (2 * i);
-                            neg |= (unsigned long long)(__high2float(h) >= bound ? 1u : 0u) << (2 * i + 1);
-                        }
+                        for (int i = 0; i < 32; ++i) neg |= (__uint_as_float(v[q][i]) >= bound ? 1u : 0u) << i;
                         while (neg) {
-                            const int i = __ffsll((long long)neg) - 1;
+                            const int i = __ffs(neg) - 1;
                             neg &= neg - 1;
-                            const unsigned long long b_e = bt * kGN + (unsigned long long)(col0 + 64 * q + i);
+                            const unsigned long long b_e = bt * kGN + (unsigned long long)(col0 + 32 * q + i);
                             if (b_e >= B.b.n) continue;
                             int w = 0;
 #pragma unroll

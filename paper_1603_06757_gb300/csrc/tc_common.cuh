@@ -145,19 +145,22 @@ __device__ __forceinline__ void tmem_ld32_issue(uint32_t taddr, uint32_t (&r)[32
         : "memory");
 }
 
-// 64 consecutive columns of 16-bit values, packed in pairs (column 2i in the low half
-// of r[i]; .x32 counts destination registers)
-__device__ __forceinline__ void tmem_ld64_pack16_issue(uint32_t taddr, uint32_t (&r)[32]) {
+// 32 consecutive f32 columns of this thread's TMEM lane and their maximum (tcgen05.ld
+// with a max reduction over the loaded columns); wait with tmem_wait_ld /
+// tmem_regs_ready and float_ready like the other loads
+__device__ __forceinline__ void tmem_ldred32_max_issue(uint32_t taddr, uint32_t (&r)[32], float &mx) {
     asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.pack::16b.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        "tcgen05.ld.red.sync.aligned.32x32b.x32.max.f32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, %32, [%33];"
         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
           "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
           "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31]), "=f"(mx)
         : "r"(taddr)
         : "memory");
 }
+
+__device__ __forceinline__ void float_ready(float &x) { asm volatile("" : "+f"(x) : : "memory"); }
 
 __device__ __forceinline__ void tmem_wait_ld(uint32_t (&r)[32]) {
     asm volatile("tcgen05.wait::ld.sync.aligned;"
