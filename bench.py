@@ -345,7 +345,7 @@ def run_ours(args):
         mma_peak = (2.0 * mb["mma"] * info["sm_count"] * sm_mhz * 1e6 / 1e12) if mb else None
         roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                     "traffic": TRAFFIC_PER_LAUNCH.get(args.workload),
-                    "kernel": f"gram_kernel<{nwords}> (tcgen05 kind::f8f6f4, E4M3 sign operands, f16 accumulators)",
+                    "kernel": f"gram_kernel<{nwords}> (tcgen05 kind::f8f6f4, E4M3 sign operands, f32 accumulators, max-reducing TMEM loads)",
                     "peak_basis": f"bf16 {bf16 or 1900.0} TFLOP/s x {FP8_PER_BF16} (nominal fp8/bf16 dense), {basis}",
                     "frac_of_sustained": achieved / (bf16_s * FP8_PER_BF16) if bf16_s else None,
                     "mma_probe_peak": mma_peak, "frac_of_mma_probe": achieved / mma_peak if mma_peak else None,
