@@ -30,7 +30,8 @@
 //   warp  8    A builder  (four A rows per lane: load the packed sum, expand),
 //   warp  9    B producer (one lane: a bulk copy of a whole B tile per stage),
 //   warp  10   MMA issue  (one lane) and TMEM allocation.
-// A work unit is (block, 128-row A tile, up to kTilesPerUnit 256-row B tiles); within a
+// A work unit is (block, 128-row A tile, up to 64 or 128 256-row B tiles: 128 when the
+// launch still has at least 8 work units per SM, fewer A rebuilds); within a
 // block the A tile runs fastest, so the CTAs running at the same time read the same B
 // tiles from L2.  Every role walks the same static sequence of work units (CTA c takes
 // c, c + grid, ...).  Stages: A two, B up to four, accumulators two TMEM buffers of 256
@@ -59,7 +60,8 @@ namespace {
 
 constexpr int kGM = 128;               // accumulator rows (A tile)
 constexpr int kGN = 256;               // accumulator columns (B tile)
-constexpr int kTilesPerUnit = 64;      // B tiles per work unit
+constexpr int kTilesPerUnit = 64;      // B tiles per work unit (doubled for large launches)
+constexpr int kUnitsPerSmForLong = 8;  // work units per SM needed to use the doubled unit
 constexpr int kGramThreads = 352;      // 8 epilogue warps, builder warp, producer warp, MMA warp
 constexpr int kSmemOperandBudget = 200 << 10;
 
@@ -87,6 +89,7 @@ struct GramParams {
     int *status;
     int k, g, nwords, n_bits, base;
     int nblocks;
+    unsigned int tiles_per_unit;  // B tiles per work unit
     unsigned long long total_wu;
     long long max_wait;
     GramBlock blocks[kMaxGramBlocks];
@@ -107,8 +110,8 @@ __device__ __forceinline__ void decode_wu(const GramParams &P, unsigned long lon
     const unsigned long long w = wu - B.wu_begin;
     const unsigned long long bu = w / B.a_tiles;
     a_tile = w - bu * B.a_tiles;
-    bt0 = bu * kTilesPerUnit;
-    bt1 = bt0 + kTilesPerUnit < B.b_tiles ? bt0 + kTilesPerUnit : B.b_tiles;
+    bt0 = bu * P.tiles_per_unit;
+    bt1 = bt0 + P.tiles_per_unit < B.b_tiles ? bt0 + P.tiles_per_unit : B.b_tiles;
 }
 
 // rows (as a k-bit mask) of the subset behind side entry e
@@ -552,20 +555,27 @@ cudaError_t launch_gram_unit(const EnumParams &ep, const GramBlockSpec *blocks, 
     p.max_wait = 200000000ll;
     int nb = 0;
     unsigned long long wu = 0;
-    for (int i = 0; i < nblocks; ++i) {
-        const GramBlockSpec &S = blocks[i];
-        if (!S.a_tab || !S.b_tab || !S.b_exp || S.a.n == 0 || S.b.n == 0) return cudaErrorInvalidValue;
-        GramBlock &G = p.blocks[nb++];
-        G.a = S.a;
-        G.b = S.b;
-        G.a_tab = S.a_tab;
-        G.b_tab = S.b_tab;
-        G.b_exp = S.b_exp;
-        G.a_tiles = (S.a.n + kGM - 1) / kGM;
-        G.b_tiles = (S.b.n + kGN - 1) / kGN;
-        G.b_units = (G.b_tiles + kTilesPerUnit - 1) / kTilesPerUnit;
-        G.wu_begin = wu;
-        wu += G.a_tiles * G.b_units;
+    for (int pass = 0; pass < 2; ++pass) {
+        // first with the doubled unit; keep it if the launch still has enough units
+        p.tiles_per_unit = pass == 0 ? 2 * kTilesPerUnit : kTilesPerUnit;
+        nb = 0;
+        wu = 0;
+        for (int i = 0; i < nblocks; ++i) {
+            const GramBlockSpec &S = blocks[i];
+            if (!S.a_tab || !S.b_tab || !S.b_exp || S.a.n == 0 || S.b.n == 0) return cudaErrorInvalidValue;
+            GramBlock &G = p.blocks[nb++];
+            G.a = S.a;
+            G.b = S.b;
+            G.a_tab = S.a_tab;
+            G.b_tab = S.b_tab;
+            G.b_exp = S.b_exp;
+            G.a_tiles = (S.a.n + kGM - 1) / kGM;
+            G.b_tiles = (S.b.n + kGN - 1) / kGN;
+            G.b_units = (G.b_tiles + p.tiles_per_unit - 1) / p.tiles_per_unit;
+            G.wu_begin = wu;
+            wu += G.a_tiles * G.b_units;
+        }
+        if (wu >= (unsigned long long)kUnitsPerSmForLong * (unsigned long long)sm_count) break;
     }
     p.nblocks = nb;
     p.total_wu = wu;
