@@ -242,8 +242,13 @@ void mdist_batch_free(mdist_batch *b);
  * rows; admitted requests join the next round next to those already in flight.  Gamma
  * rows and the per-request Alg. 1 state stay on the device until the request finishes.
  * A request forms at most 8 information sets (fewer if opts->max_sets is smaller); its
- * result equals mdist_min_distance's with the same max_sets.  All calls are thread-
- * safe.  The server uses its own CUDA stream. */
+ * result equals mdist_min_distance's with the same max_sets.  Large requests — at least
+ * 10^9 codewords up to the predicted termination level (the request's hint, else the
+ * Gilbert-Varshamov estimate) — are run one at a time between two rounds on the
+ * single-code path with the tensor-core enumerator instead (opts->tensor_cores: 0 as
+ * described, 1 never, 2 every request); their device memory comes from chunks the
+ * server allocates with cudaMalloc and keeps for reuse until mdist_server_free.  All
+ * calls are thread-safe.  The server uses its own CUDA stream. */
 typedef struct mdist_server mdist_server;
 
 int mdist_server_create(const mdist_options *opts, int max_slots, size_t rows_pool_bytes, mdist_server **out);

@@ -244,7 +244,9 @@ class Server:
     """Continuous-batching serving loop (mdist_server_*)."""
 
     def __init__(self, *, max_slots: int = 1024, rows_pool_bytes: int = 64 << 20, check_per_matrix: bool = False,
-                 max_sets: int = 0, blocks_per_sm: int = 0, torch_alloc: bool = True):
+                 max_sets: int = 0, blocks_per_sm: int = 0, tensor_cores: int = 0, torch_alloc: bool = True):
+        """tensor_cores: 0 = large requests (>= 10^9 codewords estimated) on the single-code
+        tensor-core path, 1 = every request batched, 2 = every request on that path."""
         torch = _torch()
         self._lib = L.lib()
         self._alloc = _TorchAllocator(torch, torch.cuda.current_device()) if torch_alloc else None
@@ -252,6 +254,7 @@ class Server:
         opts.check_per_matrix = 1 if check_per_matrix else 0
         opts.max_sets = int(max_sets)
         opts.blocks_per_sm = int(blocks_per_sm)
+        opts.tensor_cores = int(tensor_cores)
         if self._alloc is not None:
             opts.dev_alloc = self._alloc.alloc_cb
             opts.dev_free = self._alloc.free_cb

@@ -30,12 +30,16 @@ namespace {
 
 constexpr int kServeMaxSets = 8;   // information sets per request
 constexpr int kServeMaxSpec = 16;  // levels a request may take in its first round
+// requests whose estimated work (codewords up to the predicted termination level) is at
+// least this run one at a time on the single-code path with the tensor-core enumerator
+constexpr double kServeTensorWork = 1e9;
 
 using Clock = std::chrono::steady_clock;
 
 struct Request {
     long long id = 0;
     int n = 0, k = 0, W = 0, wstar = 0;
+    bool large = false;               // routed to the single-code tensor-core path
     std::vector<uint64_t> G;
     Partition part;
     std::vector<DeviceRows> rows;
@@ -98,6 +102,7 @@ struct mdist_server {
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
     std::deque<Request *> queue;
+    std::deque<Request *> large_queue;  // requests for the single-code tensor-core path
     std::map<long long, Done> done;
     long long next_id = 1;
     bool stopping = false;
@@ -111,6 +116,9 @@ struct mdist_server {
     std::atomic<long long> rounds{0}, completed{0}, admitted{0};
     std::atomic<int> error{MDIST_OK};
     double gpu_ms = 0;
+    // device memory of the single-code handles: chunks kept for reuse (size -> free chunks)
+    std::multimap<size_t, void *> chunk_free;
+    std::map<void *, size_t> chunk_size;
 };
 
 namespace {
@@ -141,6 +149,85 @@ unsigned long long unrank_lex(int k, int g, unsigned long long rank) {
         --d;
     }
     return mask;
+}
+
+// Allocator of the single-code handles the server runs: chunks rounded up to 2 MiB
+// (64 MiB and up to a power of two) are kept after use and handed out again.
+void *chunk_alloc(size_t bytes, void *ctx) {
+    mdist_server *s = static_cast<mdist_server *>(ctx);
+    size_t size = (bytes + (2u << 20) - 1) / (2u << 20) * (2u << 20);
+    if (size >= (64u << 20)) {
+        size_t p2 = 64u << 20;
+        while (p2 < size) p2 <<= 1;
+        size = p2;
+    }
+    auto it = s->chunk_free.find(size);
+    if (it != s->chunk_free.end()) {
+        void *p = it->second;
+        s->chunk_free.erase(it);
+        return p;
+    }
+    void *p = nullptr;
+    if (cudaMalloc(&p, size) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    s->chunk_size[p] = size;
+    return p;
+}
+
+void chunk_free(void *p, void *ctx) {
+    mdist_server *s = static_cast<mdist_server *>(ctx);
+    auto it = s->chunk_size.find(p);
+    if (it != s->chunk_size.end()) s->chunk_free.emplace(it->second, p);
+}
+
+// Estimated codewords of a request: every set up to the predicted termination level
+// (the hint, else the Gilbert-Varshamov estimate).
+double request_work(const Request &rq) {
+    const int m = (int)rq.part.sets.size();
+    int w = rq.wstar;
+    if (w < 1) {
+        std::vector<int> ranks((size_t)m);
+        for (int j = 0; j < m; ++j) ranks[(size_t)j] = rq.part.sets[(size_t)j].rank;
+        int d_gv = 0;
+        mdist_gv_estimate(rq.n, rq.k, m, ranks.data(), &d_gv, &w);
+    }
+    double work = 0;
+    for (int g = 1; g <= w && g <= rq.k; ++g) work += (double)binom_host(rq.k, g);
+    return work * m;
+}
+
+// A large request on the single-code path (tensor-core enumerator), on the server's
+// stream; the result goes to the done table like a retired slot's.
+void run_large(mdist_server *s, Request *rq) {
+    rq->t_start = Clock::now();
+    Done out;
+    mdist_options o{};
+    o.check_per_matrix = s->opt.check_per_matrix;
+    o.max_sets = s->opt.max_sets > 0 && s->opt.max_sets < kServeMaxSets ? s->opt.max_sets : kServeMaxSets;
+    o.wstar_hint = rq->wstar;
+    o.dev_alloc = chunk_alloc;
+    o.dev_free = chunk_free;
+    o.alloc_ctx = s;
+    mdist_code *h = nullptr;
+    out.status = mdist_prepare(rq->G.data(), rq->n, rq->k, rq->W, &o, s->stream, &h);
+    if (out.status == MDIST_OK) {
+        out.witness.assign((size_t)rq->W, 0);
+        out.status = mdist_min_distance(h, &out.d, out.witness.data(), &out.message, &out.key, &out.stats);
+    }
+    if (h) mdist_free(h);
+    s->gpu_ms += out.stats.kernel_ms;
+    rq->t_done = Clock::now();
+    out.latency = std::chrono::duration<double>(rq->t_done - rq->t_submit).count();
+    out.queue_wait = std::chrono::duration<double>(rq->t_start - rq->t_submit).count();
+    {
+        std::lock_guard<std::mutex> lock(s->mu);
+        s->done[rq->id] = std::move(out);
+    }
+    s->admitted++;
+    s->completed++;
+    delete rq;
 }
 
 // Admit one request into slot `slot` (rows already placed at rq->rows_off).
@@ -266,14 +353,19 @@ void serve_loop(mdist_server *s) {
     for (;;) {
         // admit first come, first served while a slot and rows memory are free
         std::vector<Request *> newly;
+        Request *large = nullptr;
         {
             std::unique_lock<std::mutex> lock(s->mu);
             if (s->stopping) break;
             bool any_active = false;
             for (Request *r : s->occupant) any_active |= r != nullptr;
-            if (!any_active && s->queue.empty()) {
+            if (!any_active && s->queue.empty() && s->large_queue.empty()) {
                 s->cv_work.wait_for(lock, std::chrono::milliseconds(50));
                 continue;
+            }
+            if (!s->large_queue.empty()) {
+                large = s->large_queue.front();
+                s->large_queue.pop_front();
             }
             while (!s->queue.empty() && !s->free_slots.empty()) {
                 Request *rq = s->queue.front();
@@ -292,6 +384,10 @@ void serve_loop(mdist_server *s) {
             const int rc = admit(s, rq);
             if (rc != MDIST_OK) s->error = rc;
             s->admitted++;
+        }
+        if (large) {  // one large request between two rounds of the others
+            run_large(s, large);
+            s->cv_done.notify_all();
         }
         // one round over every occupied slot
         bool present[kBatchBuckets] = {};
@@ -418,11 +514,14 @@ int mdist_server_submit(mdist_server *s, const uint64_t *G, int n, int k, int wo
         rq->rows_words += rq->rows[j].words.size();
     }
     if (rq->rows_words > s->pool_words) { delete rq; return MDIST_ENOMEM; }
+    const int tc = s->opt.tensor_cores;
+    rq->large = tc == 2 || (tc == 0 && request_work(*rq) >= kServeTensorWork);
     std::lock_guard<std::mutex> lock(s->mu);
     if (s->stopping) { delete rq; return MDIST_ECANCELLED; }
     rq->id = s->next_id++;
     *request_id = rq->id;
-    s->queue.push_back(rq);
+    if (rq->large) s->large_queue.push_back(rq);
+    else s->queue.push_back(rq);
     s->cv_work.notify_one();
     return MDIST_OK;
 }
@@ -463,7 +562,7 @@ int mdist_server_info(mdist_server *s, long long *admitted, long long *completed
     if (admitted) *admitted = s->admitted;
     if (completed) *completed = s->completed;
     if (rounds) *rounds = s->rounds;
-    if (queued) *queued = (int)s->queue.size();
+    if (queued) *queued = (int)(s->queue.size() + s->large_queue.size());
     if (in_flight) *in_flight = (int)(s->admitted - s->completed);
     if (gpu_ms) *gpu_ms = s->gpu_ms;
     return s->error;
@@ -475,13 +574,16 @@ void mdist_server_free(mdist_server *s) {
         std::lock_guard<std::mutex> lock(s->mu);
         s->stopping = true;
         for (Request *rq : s->queue) delete rq;
+        for (Request *rq : s->large_queue) delete rq;
         s->queue.clear();
+        s->large_queue.clear();
         s->cv_work.notify_all();
     }
     if (s->th.joinable()) s->th.join();
     for (Request *rq : s->occupant) delete rq;
     cudaStreamSynchronize(s->stream);
     sfree_all(s);
+    for (auto &kv : s->chunk_size) cudaFree(kv.first);
     cudaStreamDestroy(s->stream);
     delete s;
 }

@@ -1,5 +1,6 @@
 """Serving loop: requests admitted while others are in flight (continuous batching),
-bounded by slots and rows memory; every result equals the code's run alone."""
+bounded by slots and rows memory; large requests routed to the single-code tensor-core
+path between rounds; every result equals the code's run alone."""
 
 import time
 
@@ -91,3 +92,21 @@ def test_oversize_request_rejected(api):
         with pytest.raises(L.MdistError) as e:
             srv.submit(G, 300)
         assert e.value.code == L.ENOMEM
+
+
+@pytest.mark.parametrize("tc", [0, 2])
+def test_large_requests_on_the_tensor_core_path(api, tc):
+    # tc=2: every request on the single-code path; tc=0: the large ones only (k up to 56:
+    # several exceed 10^9 estimated codewords); both mixed with batched requests
+    reqs = _requests(24, 3, k_lo=20, k_hi=56)
+    with api.Server(max_slots=16, rows_pool_bytes=4 << 20, tensor_cores=tc) as srv:
+        ids = []
+        for i, (n, k, G) in enumerate(reqs):
+            ids.append(srv.submit(G, n))
+            if i % 6 == 5:
+                time.sleep(0.01)
+        res = _drain(srv, ids, timeout_s=300)
+        info = srv.info()
+    assert info["completed"] == len(reqs) and info["queued"] == 0 and info["in_flight"] == 0
+    for rid, (n, k, G) in zip(ids, reqs):
+        _same(res[rid], api.min_distance(G, n, max_sets=8))
