@@ -390,9 +390,11 @@ cudaError_t gram_launch_nw(const GramParams &p, int sm_count, cudaStream_t strea
 }
 
 // Several tables in one launch: job i covers the global entries [begin[i], begin[i+1]).
+constexpr int kTableChunk = 16;  // consecutive entries a thread builds
+
 struct SideJobs {
     int njobs;
-    unsigned long long begin[kMaxTableJobs + 1];
+    unsigned long long begin[kMaxTableJobs + 1];  // chunks of kTableChunk entries
     GramSide side[kMaxTableJobs];
     uint32_t *out[kMaxTableJobs];
 };
@@ -416,7 +418,10 @@ __device__ __forceinline__ int job_of(const unsigned long long (&begin)[N], int 
     return lo;
 }
 
-// out_i[e * NW ..] = the sum of the rows of entry e of side i (rows: the k rows of the set)
+// out_i[e * NW ..] = the sum of the rows of entry e of side i (rows: the k rows of the set).
+// A thread takes kTableChunk consecutive entries: it unranks the first, then steps to
+// the next subset of each component in colex order (Gosper's rule; component 1 steps
+// when component 0 wraps) and XORs only the rows that changed.  J.begin counts chunks.
 template <int NW>
 __global__ void side_tables_kernel(const uint32_t *rows, int k, const __grid_constant__ SideJobs J) {
     __shared__ uint32_t s_bn[kBn * kBn];
@@ -424,24 +429,49 @@ __global__ void side_tables_kernel(const uint32_t *rows, int k, const __grid_con
     for (int i = threadIdx.x; i < kBn * kBn; i += blockDim.x) s_bn[i] = (uint32_t)c_binom_g.v[i / kBn][i % kBn];
     for (int i = threadIdx.x; i < k * NW; i += blockDim.x) s_rows[i] = rows[i];
     __syncthreads();
-    const unsigned long long total = J.begin[J.njobs];
-    for (unsigned long long g = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; g < total;
-         g += (unsigned long long)gridDim.x * blockDim.x) {
-        const int i = job_of(J.begin, J.njobs, g);
-        const unsigned long long e = g - J.begin[i];
-        unsigned long long m = side_mask(s_bn, J.side[i], e);
-        uint32_t x[NW];
-#pragma unroll
-        for (int w = 0; w < NW; ++w) x[w] = 0;
+    auto add_rows = [&](uint32_t (&x)[NW], unsigned long long m) {
         while (m) {
             const int r = __ffsll((long long)m) - 1;
             m &= m - 1;
 #pragma unroll
             for (int w = 0; w < NW; ++w) x[w] ^= s_rows[r * NW + w];
         }
-        uint32_t *out = J.out[i];
+    };
+    const unsigned long long total = J.begin[J.njobs];
+    for (unsigned long long c = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; c < total;
+         c += (unsigned long long)gridDim.x * blockDim.x) {
+        const int i = job_of(J.begin, J.njobs, c);
+        const GramSide &S = J.side[i];
+        unsigned long long e = (c - J.begin[i]) * kTableChunk;
+        const unsigned long long e_end = e + kTableChunk < S.n ? e + kTableChunk : S.n;
+        unsigned long long e0 = S.nc == 2 ? e % S.cnt0 : e;
+        uint32_t m0 = unrank_colex(s_bn, S.kc[0], S.t[0], (uint32_t)e0);
+        uint32_t m1 = S.nc == 2 ? unrank_colex(s_bn, S.kc[1], S.t[1], (uint32_t)(e / S.cnt0)) : 0u;
+        uint32_t x[NW];
 #pragma unroll
-        for (int w = 0; w < NW; ++w) out[e * NW + w] = x[w];
+        for (int w = 0; w < NW; ++w) x[w] = 0;
+        add_rows(x, ((unsigned long long)m0 << S.off[0]) | ((unsigned long long)m1 << S.off[1]));
+        uint32_t *out = J.out[i];
+        for (;;) {
+#pragma unroll
+            for (int w = 0; w < NW; ++w) out[e * NW + w] = x[w];
+            if (++e >= e_end) break;
+            unsigned long long diff;
+            if (e0 + 1 < S.cnt0) {
+                const uint32_t n0 = next_colex(m0);
+                diff = (unsigned long long)(m0 ^ n0) << S.off[0];
+                m0 = n0;
+                ++e0;
+            } else {  // component 0 wraps to its first subset, component 1 steps
+                const uint32_t n0 = S.t[0] >= 32 ? 0xFFFFFFFFu : (1u << S.t[0]) - 1u;
+                const uint32_t n1 = next_colex(m1);
+                diff = ((unsigned long long)(m0 ^ n0) << S.off[0]) | ((unsigned long long)(m1 ^ n1) << S.off[1]);
+                m0 = n0;
+                m1 = n1;
+                e0 = 0;
+            }
+            add_rows(x, diff);
+        }
     }
 }
 
@@ -494,7 +524,7 @@ cudaError_t launch_side_tables(const uint32_t *rows, int k, int nwords, const Gr
     for (int i = 0; i < n; ++i) {
         J.side[i] = sides[i];
         J.out[i] = outs[i];
-        J.begin[i + 1] = J.begin[i] + sides[i].n;
+        J.begin[i + 1] = J.begin[i] + (sides[i].n + kTableChunk - 1) / kTableChunk;
     }
     switch (nwords) {
         case 1: return side_tables_nw<1>(rows, k, J, sm_count, stream);
