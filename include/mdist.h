@@ -396,6 +396,21 @@ int mdist_debug_filter_choice(int nwords, int n_bits, int thr, int *group);
 int mdist_debug_level_plan(int k, int g, int nwords, int *nblocks, uint64_t *blocks, uint64_t *total_tiles,
                            int *lane_chunk, int *walk_chunk);
 
+/* Tensor-core plan of one level (same k, g, nwords as mdist_debug_level_plan) under
+ * mdist_options.tensor_cores = tensor_cores, before any table is built: the parts the
+ * tensor-core enumerator takes, each a product A x B of two sides, and which product
+ * blocks of the level plan they cover.  A side is the set of sums of one t0-subset of
+ * rows [off0, off0 + kc0) and, when it has two components, one t1-subset of rows
+ * [off1, off1 + kc1).  parts[15 * i ..]: block, then for A and for B in turn off0,
+ * kc0, t0, off1, kc1, t1 (-1 for an absent second component) and the component count;
+ * sizes[2 * i ..]: the entry counts of A and B; covered[b] (34 entries): 1 if block b
+ * is split into parts, 0 if it stays on the ALU kernel.  Capacity 128 parts.  The
+ * library swaps A and B when B is the larger side; this reports them unswapped.
+ * MDIST_EINVAL on a null pointer or a mode outside 0..3, MDIST_ERANGE if
+ * C(k, g) >= 2^54.  Host only, no CUDA calls. */
+int mdist_debug_gram_plan(int k, int g, int nwords, int tensor_cores, int *nparts, int *parts, uint64_t *sizes,
+                          int *covered);
+
 #ifdef __cplusplus
 }
 #endif

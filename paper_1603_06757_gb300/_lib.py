@@ -161,6 +161,8 @@ SIGNATURES = {
     "mdist_debug_lexrank": (ctypes.c_int, [ctypes.c_uint64, ctypes.c_int, ctypes.c_int, P64]),
     "mdist_debug_filter_choice": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, PI]),
     "mdist_debug_level_plan": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, PI, P64, P64, PI, PI]),
+    "mdist_debug_gram_plan": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, PI, PI, P64,
+                                             PI]),
 }
 
 

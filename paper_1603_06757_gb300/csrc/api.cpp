@@ -270,49 +270,59 @@ int add_gram_block(mdist_code *c, int j, mdist::GramSide A, mdist::GramSide B,
     return MDIST_OK;
 }
 
-// The tensor-core part of unit p (set j).  tensor_cores 0: a product block whose sides
-// both hold >= kGramMinSide entries goes there as it is; one with a smaller side and at
-// least kSplitMin codewords is split over the two quarters of its large side's half:
+// The tensor-core parts of product block B of a level with halves of k1 and k2 rows,
+// written to A[], Bs[] (at most `cap`); returns their count, 0 when the block stays on
+// the ALU kernel.  tensor_cores 0: a block whose sides both hold >= kGramMinSide
+// entries is one part as it is; one with a smaller side and at least kSplitMin
+// codewords is split over the two quarters of its large side's half:
 // S x L_t = union over i of (S + Qa_i) x Qb_(t-i) (Vandermonde), every part with two
 // large sides.  tensor_cores 3: as 0, splitting every block with a small side whatever
-// its size; 2: every block as it is; 1: none.  covered[b] marks the blocks handled there.
+// its size; 2: every block as it is; 1: none.  No tables, no device calls.
+int gram_block_parts(int mode, int k1, int k2, const mdist::ProductBlock &B, int cap, mdist::GramSide *A,
+                     mdist::GramSide *Bs) {
+    if (mode == 1) return 0;
+    const int loff = B.lane_half ? k1 : 0, lkc = B.lane_half ? k2 : k1;
+    const int woff = B.lane_half ? 0 : k1, wkc = B.lane_half ? k1 : k2;
+    const unsigned long long small = B.lane_n < B.walk_n ? B.lane_n : B.walk_n;
+    if (mode == 2 || small >= (unsigned long long)mdist::kGramMinSide) {
+        if (cap < 1) return 0;
+        A[0] = make_side(loff, lkc, (int)B.lane_t);
+        Bs[0] = make_side(woff, wkc, (int)B.walk_t);
+        return 1;
+    }
+    if (mode != 3 && B.lane_n * B.walk_n < kSplitMin) return 0;
+    // large side L (t_L-subsets of kc_L rows at off_L), small side S
+    const bool lane_large = B.lane_n >= B.walk_n;
+    const int Loff = lane_large ? loff : woff, Lkc = lane_large ? lkc : wkc;
+    const int Lt = (int)(lane_large ? B.lane_t : B.walk_t);
+    const int Soff = lane_large ? woff : loff, Skc = lane_large ? wkc : lkc;
+    const int St = (int)(lane_large ? B.walk_t : B.lane_t);
+    const int qa = Lkc / 2, qb = Lkc - qa;
+    const int i0 = Lt - qb > 0 ? Lt - qb : 0, i1 = Lt < qa ? Lt : qa;
+    if (Lt < 1 || i1 - i0 + 1 > cap) return 0;
+    for (int i = i0; i <= i1; ++i) {
+        A[i - i0] = St > 0 ? make_side(Soff, Skc, St, Loff, qa, i) : make_side(Loff, qa, i);
+        Bs[i - i0] = make_side(Loff + qa, qb, Lt - i);
+    }
+    return i1 - i0 + 1;
+}
+
+// The tensor-core part of unit p (set j): gram_block_parts of every product block,
+// with its tables; a block any of whose tables is over budget stays on the ALU kernel
+// as a whole.  covered[b] marks the blocks handled there.
 int gram_plan(mdist_code *c, int j, const EnumParams &p, std::vector<mdist::GramBlockSpec> &out, bool *covered) {
     out.clear();
     for (int b = 0; b < mdist::kMaxBlocks; ++b) covered[b] = false;
-    const int mode = c->opt.tensor_cores;
-    if (mode == 1 || !mdist::gram_eligible(p.nwords)) return MDIST_OK;
-    const int k1 = p.k1, k2 = p.k2;
+    if (!mdist::gram_eligible(p.nwords)) return MDIST_OK;
+    mdist::GramSide A[mdist::kMaxGramBlocks], Bs[mdist::kMaxGramBlocks];
     for (int b = 0; b < p.nblocks; ++b) {
-        const mdist::ProductBlock &B = p.blocks[b];
-        const int loff = B.lane_half ? k1 : 0, lkc = B.lane_half ? k2 : k1;
-        const int woff = B.lane_half ? 0 : k1, wkc = B.lane_half ? k1 : k2;
-        const unsigned long long small = B.lane_n < B.walk_n ? B.lane_n : B.walk_n;
+        const int np = gram_block_parts(c->opt.tensor_cores, p.k1, p.k2, p.blocks[b],
+                                        mdist::kMaxGramBlocks - (int)out.size(), A, Bs);
         const size_t mark = out.size();
-        bool ok = false;
-        if (mode == 2 || small >= (unsigned long long)mdist::kGramMinSide) {
-            if ((int)out.size() + 1 > mdist::kMaxGramBlocks) continue;
-            const int rc = add_gram_block(c, j, make_side(loff, lkc, (int)B.lane_t), make_side(woff, wkc, (int)B.walk_t),
-                                          out, &ok);
+        bool all = np > 0;
+        for (int i = 0; i < np && all; ++i) {
+            const int rc = add_gram_block(c, j, A[i], Bs[i], out, &all);
             if (rc != MDIST_OK) return rc;
-            covered[b] = ok;
-            continue;
-        }
-        if (mode != 3 && B.lane_n * B.walk_n < kSplitMin) continue;
-        // large side L (t_L-subsets of kc_L rows at off_L), small side S
-        const bool lane_large = B.lane_n >= B.walk_n;
-        const int Loff = lane_large ? loff : woff, Lkc = lane_large ? lkc : wkc;
-        const int Lt = (int)(lane_large ? B.lane_t : B.walk_t);
-        const int Soff = lane_large ? woff : loff, Skc = lane_large ? wkc : lkc;
-        const int St = (int)(lane_large ? B.walk_t : B.lane_t);
-        const int qa = Lkc / 2, qb = Lkc - qa;
-        const int i0 = Lt - qb > 0 ? Lt - qb : 0, i1 = Lt < qa ? Lt : qa;
-        if (Lt < 1 || (int)out.size() + (i1 - i0 + 1) > mdist::kMaxGramBlocks) continue;
-        bool all = true;
-        for (int i = i0; i <= i1 && all; ++i) {
-            const mdist::GramSide A = St > 0 ? make_side(Soff, Skc, St, Loff, qa, i) : make_side(Loff, qa, i);
-            const int rc = add_gram_block(c, j, A, make_side(Loff + qa, qb, Lt - i), out, &ok);
-            if (rc != MDIST_OK) return rc;
-            all = ok;
         }
         if (all) covered[b] = true;
         else out.resize(mark);  // a table over budget: the whole block stays on the ALU kernel
@@ -925,6 +935,40 @@ int mdist_device_info(int *sm_count, int *max_sm_clock_khz, int *cc_major, int *
         if (cudaDeviceGetAttribute(&v, cudaDevAttrComputeCapabilityMinor, dev) != cudaSuccess) return MDIST_ECUDA;
         *cc_minor = v;
     }
+    return MDIST_OK;
+}
+
+int mdist_debug_gram_plan(int k, int g, int nwords, int tensor_cores, int *nparts, int *parts /* 128 * 15 */,
+                          uint64_t *sizes /* 128 * 2 */, int *covered /* 34 */) {
+    if (!nparts || !parts || !sizes || !covered || nwords < 1 || nwords > 16 || tensor_cores < 0 ||
+        tensor_cores > 3)
+        return MDIST_EINVAL;
+    mdist::EnumParams p{};
+    if (!mdist::plan_level(k, g, nwords, p)) return MDIST_ERANGE;
+    mdist::GramSide A[mdist::kMaxGramBlocks], Bs[mdist::kMaxGramBlocks];
+    int n = 0;
+    for (int b = 0; b < mdist::kMaxBlocks; ++b) covered[b] = 0;
+    for (int b = 0; b < p.nblocks && mdist::gram_eligible(nwords); ++b) {
+        const int np = gram_block_parts(tensor_cores, p.k1, p.k2, p.blocks[b], mdist::kMaxGramBlocks - n, A, Bs);
+        covered[b] = np > 0;
+        for (int i = 0; i < np; ++i, ++n) {
+            int *o = parts + 15 * n;
+            o[0] = b;
+            const mdist::GramSide *S[2] = {&A[i], &Bs[i]};
+            for (int s = 0; s < 2; ++s) {
+                for (int q = 0; q < 2; ++q) {
+                    const bool on = q < S[s]->nc;
+                    o[1 + 7 * s + 3 * q] = on ? S[s]->off[q] : -1;
+                    o[2 + 7 * s + 3 * q] = on ? S[s]->kc[q] : -1;
+                    o[3 + 7 * s + 3 * q] = on ? S[s]->t[q] : -1;
+                }
+                o[7 + 7 * s] = S[s]->nc;
+            }
+            sizes[2 * n] = A[i].n;
+            sizes[2 * n + 1] = Bs[i].n;
+        }
+    }
+    *nparts = n;
     return MDIST_OK;
 }
 

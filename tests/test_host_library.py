@@ -244,6 +244,126 @@ def test_level_plan_covers_level(lib, k, nw):
         assert tt == tiles
 
 
+def _gram_plan(lib, k, g, nw, mode):
+    n = ctypes.c_int()
+    parts = np.zeros(128 * 15, dtype=np.int32)
+    sizes = np.zeros(128 * 2, dtype=np.uint64)
+    cov = np.zeros(34, dtype=np.int32)
+    rc = lib.mdist_debug_gram_plan(k, g, nw, mode, ctypes.byref(n), parts.ctypes.data_as(L.PI),
+                                   sizes.ctypes.data_as(P64), cov.ctypes.data_as(L.PI))
+    return rc, parts.reshape(128, 15)[: n.value], sizes.reshape(128, 2)[: n.value], cov
+
+
+def _side_components(row):
+    """[(off, kc, t)] of one side of a part (7 ints: off0 kc0 t0 off1 kc1 t1 nc)."""
+    comps = [tuple(int(v) for v in row[0:3])]
+    if int(row[6]) == 2:
+        comps.append(tuple(int(v) for v in row[3:6]))
+    else:
+        assert int(row[6]) == 1 and tuple(int(v) for v in row[3:6]) == (-1, -1, -1)
+    return comps
+
+
+def _component_masks(comps):
+    """Every mask that takes a t-subset of rows [off, off + kc) from each component."""
+    out = [0]
+    for off, kc, t in comps:
+        out = [m | sum(1 << (off + e) for e in c) for m in out for c in itertools.combinations(range(kc), t)]
+    return out
+
+
+def _check_parts_structure(k, g, parts, sizes):
+    """Per part: components inside [0, k), pairwise disjoint, t's adding up to g, sizes
+    their binomial products; per covered block: sizes multiply out to the block's size."""
+    per_block = {}
+    for prt, (na, nb) in zip(parts, sizes):
+        b = int(prt[0])
+        comps_a, comps_b = _side_components(prt[1:8]), _side_components(prt[8:15])
+        rows = []
+        for off, kc, t in comps_a + comps_b:
+            assert 0 <= off and off + kc <= k and 0 <= t <= kc
+            rows += range(off, off + kc)
+        assert len(rows) == len(set(rows))  # components on disjoint rows
+        assert sum(t for _, _, t in comps_a + comps_b) == g
+        assert int(na) == math.prod(math.comb(kc, t) for _, kc, t in comps_a)
+        assert int(nb) == math.prod(math.comb(kc, t) for _, kc, t in comps_b)
+        per_block.setdefault(b, []).append((comps_a, comps_b, int(na) * int(nb)))
+    return per_block
+
+
+@pytest.mark.parametrize("mode", [0, 1, 2, 3])
+@pytest.mark.parametrize("k", [6, 9, 13, 16])
+def test_gram_plan_partitions_level_bruteforce(lib, k, mode):
+    """Every covered block is split into parts whose codeword sets are disjoint and
+    whose union is the block's set (checked mask by mask); uncovered blocks plus covered
+    ones give C(k, g)."""
+    k1 = (k + 1) // 2
+    for g in range(1, k + 1):
+        rc, blocks, _, _, _ = _plan(lib, k, g, 4)
+        assert rc == 0
+        rc, parts, sizes, cov = _gram_plan(lib, k, g, 4, mode)
+        assert rc == 0
+        per_block = _check_parts_structure(k, g, parts, sizes)
+        assert set(per_block) == {b for b in range(len(blocks)) if cov[b]}
+        assert not cov[len(blocks):].any()
+        for b, row in enumerate(blocks):
+            half, lt, wt, ln, wn = (int(v) for v in row[:5])
+            lane = (0, k1) if half == 0 else (k1, k - k1)
+            walk = (k1, k - k1) if half == 0 else (0, k1)
+            want = set(_component_masks([(lane[0], lane[1], lt), (walk[0], walk[1], wt)]))
+            assert len(want) == ln * wn
+            if not cov[b]:
+                continue
+            got = []
+            for comps_a, comps_b, size in per_block[b]:
+                ms = [a | c for a in _component_masks(comps_a) for c in _component_masks(comps_b)]
+                assert len(ms) == size
+                got += ms
+            assert len(got) == len(set(got)) and set(got) == want  # disjoint, exact cover
+        if mode == 1:
+            assert len(parts) == 0
+        if mode == 2:  # every block as it is, one part each
+            assert list(cov[: len(blocks)]) == [1] * len(blocks) and len(parts) == len(blocks)
+        if mode == 3:  # everything with a non-empty large side goes to the tensor cores
+            for b, row in enumerate(blocks):
+                lt, wt, ln, wn = (int(v) for v in row[1:5])
+                big_t = lt if ln >= wn else wt
+                assert cov[b] == (1 if (min(ln, wn) >= 128 or big_t >= 1) else 0), (k, g, b)
+
+
+@pytest.mark.parametrize("k", [40, 54, 64])
+@pytest.mark.parametrize("mode", [0, 3])
+def test_gram_plan_counts_large_levels(lib, k, mode):
+    """At full code sizes: part sizes multiply out to each covered block's size, blocks
+    with both sides >= 128 entries are one part, mode 0 splits exactly the blocks with a
+    smaller side and >= 2^24 codewords, and rows of more than 7 words get no parts."""
+    for g in range(1, k + 1):
+        rc, blocks, _, _, _ = _plan(lib, k, g, 4)
+        if rc == L.ERANGE:
+            continue
+        assert rc == 0
+        rc, parts, sizes, cov = _gram_plan(lib, k, g, 4, mode)
+        assert rc == 0
+        per_block = _check_parts_structure(k, g, parts, sizes)
+        for b, row in enumerate(blocks):
+            lt, wt, ln, wn = (int(v) for v in row[1:5])
+            if min(ln, wn) >= 128:
+                assert cov[b] and len(per_block[b]) == 1
+            elif mode == 0:
+                assert cov[b] == (1 if ln * wn >= 1 << 24 else 0), (k, g, b)
+            if cov[b]:
+                assert sum(sz for _, _, sz in per_block[b]) == ln * wn
+        rc, parts, _, cov = _gram_plan(lib, k, g, 8, mode)
+        assert rc == 0 and len(parts) == 0 and not cov.any()
+
+
+def test_gram_plan_rejects_bad_arguments(lib):
+    rc, *_ = _gram_plan(lib, 20, 3, 4, 4)
+    assert rc == L.EINVAL
+    rc, *_ = _gram_plan(lib, 20, 3, 4, -1)
+    assert rc == L.EINVAL
+
+
 def _choice(lib, nw, nb, thr):
     g = ctypes.c_int()
     assert lib.mdist_debug_filter_choice(nw, nb, thr, ctypes.byref(g)) == 0
