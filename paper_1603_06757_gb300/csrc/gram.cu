@@ -27,17 +27,21 @@
 //   warps 0-7  epilogue   (warp w: TMEM lanes 32 (w % 4) .. + 31 = rows of the
 //              accumulator tile, columns 128 (w / 4) .. + 127; four reducing loads of
 //              32 f32 columns per wait),
-//   warp  8    A builder  (four A rows per lane: load the packed sum, expand),
+//   warp  8    A builder  (four A rows per lane and A tile: load the packed sum, expand),
 //   warp  9    B producer (one lane: a bulk copy of a whole B tile per stage),
 //   warp  10   MMA issue  (one lane) and TMEM allocation.
-// A work unit is (block, 128-row A tile, up to 64 or 128 256-row B tiles: 128 when the
-// launch still has at least 8 work units per SM, fewer A rebuilds); within a
-// block the A tile runs fastest, so the CTAs running at the same time read the same B
-// tiles from L2.  Every role walks the same static sequence of work units (CTA c takes
-// c, c + grid, ...).  Stages: A two, B up to four, accumulators two TMEM buffers of 256
-// columns.  Hand-offs are mbarriers: A and accumulator-full by tcgen05.commit, B full
-// by the copies' transaction bytes, B stages and accumulators freed by the epilogue
-// (its thread 0 frees a B stage once the accumulator-full commit of its tile has
+// A work unit is (block, group of MA 128-row A tiles, up to 64 or 128 256-row B tiles:
+// 128 when the launch still has at least 8 work units per SM, fewer A rebuilds); MA is
+// two for rows of up to four words (one above, where two A stages of two tiles would
+// leave fewer than four B stages).  Each B tile meets the MA A tiles in turn, one
+// accumulator each, so a B tile copied from L2 serves 128 MA rows.  Within a block the A
+// group runs fastest, so the CTAs running at the same time read the same B tiles from
+// L2.  Every role walks the same static sequence of work units (CTA c takes c, c + grid,
+// ...).  Stages: A two (of MA tiles), B up to four, accumulators two TMEM buffers of 256
+// columns, used in turn by the MA accumulators of every B tile.  Hand-offs are
+// mbarriers: A and accumulator-full by tcgen05.commit, B full by the copies'
+// transaction bytes, B stages and accumulators freed by the epilogue (its thread 0
+// frees a B stage once the accumulator-full commit of the tile's last accumulator has
 // arrived).  Every wait is bounded; a timeout sets the status word, and the kernel
 // ends after its copies and MMAs have drained.
 //
@@ -67,16 +71,22 @@ constexpr int kSmemOperandBudget = 200 << 10;
 
 __host__ __device__ constexpr int gram_ka(int nw) { return 32 * nw; }  // bytes per operand row
 
+// A tiles per work unit: every B tile meets both in turn (two accumulators per B tile),
+// which halves the B bytes each multiply-add needs from L2; one where two would leave
+// fewer than four B stages
+__host__ __device__ constexpr int gram_ma(int nw) { return nw <= 4 ? 2 : 1; }
+
 // B stages that fit beside the two A stages
 __host__ __device__ constexpr int gram_b_stages(int nw) {
-    return (kSmemOperandBudget - 2 * kGM * gram_ka(nw)) / (kGN * gram_ka(nw)) < 4
-               ? (kSmemOperandBudget - 2 * kGM * gram_ka(nw)) / (kGN * gram_ka(nw))
+    return (kSmemOperandBudget - 2 * gram_ma(nw) * kGM * gram_ka(nw)) / (kGN * gram_ka(nw)) < 4
+               ? (kSmemOperandBudget - 2 * gram_ma(nw) * kGM * gram_ka(nw)) / (kGN * gram_ka(nw))
                : 4;
 }
 
 struct GramBlock {
     GramSide a, b;               // the two sides (A: 128-row tiles, B: 256-row tiles)
-    unsigned long long a_tiles, b_units, b_tiles;
+    unsigned long long a_tiles;  // groups of gram_ma 128-row A tiles
+    unsigned long long b_units, b_tiles;
     unsigned long long wu_begin;
     const uint32_t *a_tab;       // a.n x nwords: sums of the A side's entries
     const uint32_t *b_tab;       // b.n x nwords
@@ -95,7 +105,7 @@ struct GramParams {
     GramBlock blocks[kMaxGramBlocks];
 };
 
-// work unit -> (block, A tile, B tile range); within a block the A tile runs fastest
+// work unit -> (block, A tile group, B tile range); within a block the A group runs fastest
 __device__ __forceinline__ void decode_wu(const GramParams &P, unsigned long long wu, int &b,
                                           unsigned long long &a_tile, unsigned long long &bt0,
                                           unsigned long long &bt1) {
@@ -153,14 +163,15 @@ __global__ void __launch_bounds__(kGramThreads, 1) gram_kernel(const __grid_cons
     constexpr int KA = gram_ka(NW);
     constexpr int KSTEPS = KA / 32;
     constexpr int S = gram_b_stages(NW);
+    constexpr int MA = gram_ma(NW);  // A tiles per stage (rows 128 h .. of the group)
     constexpr int A_BYTES = kGM * KA, B_BYTES = kGN * KA;
     static_assert(S >= 2, "two B stages at least");
     extern __shared__ __align__(1024) uint8_t sm[];
-    uint8_t *sA0 = sm;
-    uint8_t *sB0 = sm + 2 * A_BYTES;
+    uint8_t *sA0 = sm;  // stage st, tile h at sA0 + (st * MA + h) * A_BYTES
+    uint8_t *sB0 = sm + 2 * MA * A_BYTES;
     // barriers: 0-1 a_full, 2-3 a_empty, 4-5 acc_full, 6-7 acc_empty, 8 drain,
     //           9 .. 9+S-1 b_full, 9+S .. 9+2S-1 b_empty
-    uint64_t *bars = reinterpret_cast<uint64_t *>(sm + 2 * A_BYTES + S * B_BYTES);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(sm + 2 * MA * A_BYTES + S * B_BYTES);
     uint32_t *s_tmem = reinterpret_cast<uint32_t *>(bars + 20);
     volatile int *s_abort = reinterpret_cast<volatile int *>(s_tmem + 1);
     uint32_t *s_bn = reinterpret_cast<uint32_t *>(bars + 24);
@@ -203,16 +214,17 @@ __global__ void __launch_bounds__(kGramThreads, 1) gram_kernel(const __grid_cons
             decode_wu(P, wu, b, a_tile, bt0, bt1);
             const GramBlock &B = P.blocks[b];
             const int st = (int)(u & 1);
-            uint32_t x[kGM / 32][NW];
+            uint32_t x[MA * kGM / 32][NW];
 #pragma unroll
-            for (int h = 0; h < kGM / 32; ++h) {
-                const unsigned long long e = a_tile * kGM + (unsigned long long)(lane + 32 * h);
+            for (int h = 0; h < MA * kGM / 32; ++h) {
+                const unsigned long long e = a_tile * (MA * kGM) + (unsigned long long)(lane + 32 * h);
 #pragma unroll
                 for (int w = 0; w < NW; ++w) x[h][w] = e < B.a.n ? B.a_tab[e * NW + w] : 0u;
             }
             if (!mbar_wait(bar(A_EMPTY + st), (uint32_t)(((u >> 1) & 1) ^ 1), P.max_wait)) { fail(); break; }
 #pragma unroll
-            for (int h = 0; h < kGM / 32; ++h) write_row<NW>(sA0 + st * A_BYTES, lane + 32 * h, x[h], 32 * NW);
+            for (int h = 0; h < MA * kGM / 32; ++h)  // group row lane + 32 h: tile h / 4, row lane + 32 (h % 4)
+                write_row<NW>(sA0 + (st * MA + h / (kGM / 32)) * A_BYTES, lane + 32 * (h % (kGM / 32)), x[h], 32 * NW);
             fence_async_smem();
             mbar_arrive(bar(A_FULL + st));
         }
@@ -249,7 +261,7 @@ __global__ void __launch_bounds__(kGramThreads, 1) gram_kernel(const __grid_cons
         if (lane == 0) {
             const uint32_t idesc = idesc_f8f6f4_e4m3_f32(kGM, kGN);
             const uint32_t sbo = (uint32_t)(KA / 16) * 128u;
-            unsigned long long t = 0, u = 0;
+            unsigned long long t = 0, u = 0, q = 0;  // B tiles, work units, accumulators
             for (unsigned long long wu = blockIdx.x; wu < P.total_wu && !*s_abort; wu += gridDim.x, ++u) {
                 int b;
                 unsigned long long a_tile, bt0, bt1;
@@ -257,21 +269,29 @@ __global__ void __launch_bounds__(kGramThreads, 1) gram_kernel(const __grid_cons
                 const int st = (int)(u & 1);
                 if (!mbar_wait(bar(A_FULL + st), (uint32_t)((u >> 1) & 1), P.max_wait)) { fail(); break; }
                 bool ok = true;
-                for (unsigned long long bt = bt0; bt < bt1; ++bt, ++t) {
-                    const int s = (int)(t % S), ab = (int)(t & 1);
-                    if (!mbar_wait(bar(B_FULL + s), (uint32_t)((t / S) & 1), P.max_wait) ||
-                        !mbar_wait(bar(ACC_EMPTY + ab), (uint32_t)(((t >> 1) & 1) ^ 1), P.max_wait)) {
+                for (unsigned long long bt = bt0; bt < bt1 && ok; ++bt, ++t) {
+                    const int s = (int)(t % S);
+                    if (!mbar_wait(bar(B_FULL + s), (uint32_t)((t / S) & 1), P.max_wait)) {
                         ok = false;
                         break;
                     }
-                    tc_fence_after();
-                    const uint32_t a0 = smem_addr(sA0 + st * A_BYTES), b0 = smem_addr(sB0 + s * B_BYTES);
-                    const uint32_t d = tmem + (uint32_t)(ab * kGN);
+                    const uint32_t b0 = smem_addr(sB0 + s * B_BYTES);
 #pragma unroll
-                    for (int ks = 0; ks < KSTEPS; ++ks)
-                        mma_f8f6f4(d, smem_desc(a0 + ks * 256, 128, sbo), smem_desc(b0 + ks * 256, 128, sbo), idesc,
-                                   ks > 0 ? 1u : 0u);
-                    mma_commit(bar(ACC_FULL + ab));  // accumulator ready, B stage s read
+                    for (int h = 0; h < MA; ++h, ++q) {
+                        const int ab = (int)(q & 1);
+                        if (!mbar_wait(bar(ACC_EMPTY + ab), (uint32_t)(((q >> 1) & 1) ^ 1), P.max_wait)) {
+                            ok = false;
+                            break;
+                        }
+                        tc_fence_after();
+                        const uint32_t a0 = smem_addr(sA0 + (st * MA + h) * A_BYTES);
+                        const uint32_t d = tmem + (uint32_t)(ab * kGN);
+#pragma unroll
+                        for (int ks = 0; ks < KSTEPS; ++ks)
+                            mma_f8f6f4(d, smem_desc(a0 + ks * 256, 128, sbo), smem_desc(b0 + ks * 256, 128, sbo),
+                                       idesc, ks > 0 ? 1u : 0u);
+                        mma_commit(bar(ACC_FULL + ab));  // accumulator ready; after tile MA-1: B stage s read
+                    }
                 }
                 mma_commit(bar(A_EMPTY + st));  // A tile free again
                 if (!ok) { fail(); break; }
@@ -283,80 +303,88 @@ __global__ void __launch_bounds__(kGramThreads, 1) gram_kernel(const __grid_cons
         // ---------------- epilogue (warps 0-7) ----------------
         const int row = 32 * (warp & 3) + lane;  // TMEM lane = A row
         const int col0 = 128 * (warp >> 2);      // first accumulator column of this warp
-        unsigned long long t = 0, cnt = 0;
+        unsigned long long t = 0, q = 0, cnt = 0;  // B tiles, accumulators, codewords counted
         unsigned int u_next = *(volatile unsigned int *)P.U;
-        for (unsigned long long wu = blockIdx.x; wu < P.total_wu && !*s_abort; wu += gridDim.x) {
+        bool ok = true;
+        for (unsigned long long wu = blockIdx.x; wu < P.total_wu && ok && !*s_abort; wu += gridDim.x) {
             int b;
             unsigned long long a_tile, bt0, bt1;
             decode_wu(P, wu, b, a_tile, bt0, bt1);
             const GramBlock &B = P.blocks[b];
-            const unsigned long long a_e = a_tile * kGM + (unsigned long long)row;
-            const bool a_valid = a_e < B.a.n;
-            const unsigned long long a_valid_rows = B.a.n - a_tile * kGM < (unsigned long long)kGM
-                                                        ? B.a.n - a_tile * kGM
-                                                        : (unsigned long long)kGM;
             // candidates: acc >= n_bits - 2 thr, with a threshold read one unit ahead
             const float bound = (float)(P.n_bits - 2 * ((int)u_next - P.base));
             u_next = *(volatile unsigned int *)P.U;
-            for (unsigned long long bt = bt0; bt < bt1; ++bt, ++t) {
-                const int ab = (int)(t & 1);
-                if (!mbar_wait(bar(ACC_FULL + ab), (uint32_t)((t >> 1) & 1), P.max_wait)) {
-                    fail();
-                    break;
-                }
-                tc_fence_after();
-                // MMA t has completed: its B stage is free (released here rather than by a
-                // commit, so that no thread but the epilogue waits on commit-driven barriers)
-                if (tid == 0) mbar_arrive(bar(B_EMPTY + (int)(t % S)));
-                const uint32_t base = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(ab * kGN + col0);
-                uint32_t v[4][32];  // 128 f32 accumulators
-                float m0, m1, m2, m3;
-                tmem_ldred32_max_issue(base, v[0], m0);
-                tmem_ldred32_max_issue(base + 32u, v[1], m1);
-                tmem_ldred32_max_issue(base + 64u, v[2], m2);
-                tmem_ldred32_max_issue(base + 96u, v[3], m3);
-                tmem_wait_ld(v[0]);
-                tmem_regs_ready(v[1]);
-                tmem_regs_ready(v[2]);
-                tmem_regs_ready(v[3]);
-                float_ready(m0);
-                float_ready(m1);
-                float_ready(m2);
-                float_ready(m3);
-                const float m = fmaxf(fmaxf(m0, m1), fmaxf(m2, m3));
-                if (m >= bound && a_valid) {
-                    // side path: which columns reach the bound, then the exact weight from
-                    // the bit-packed rows, then the key
-                    uint32_t x[NW];
+            for (unsigned long long bt = bt0; bt < bt1 && ok; ++bt, ++t) {
+#pragma unroll 1
+                for (int h = 0; h < MA; ++h, ++q) {
+                    const int ab = (int)(q & 1);
+                    if (!mbar_wait(bar(ACC_FULL + ab), (uint32_t)((q >> 1) & 1), P.max_wait)) {
+                        fail();
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    // the last MMA on B tile t has completed: its B stage is free (released
+                    // here rather than by a commit, so that no thread but the epilogue waits
+                    // on commit-driven barriers)
+                    if (tid == 0 && h == MA - 1) mbar_arrive(bar(B_EMPTY + (int)(t % S)));
+                    const unsigned long long a_lo = (a_tile * MA + (unsigned long long)h) * kGM;
+                    const unsigned long long a_e = a_lo + (unsigned long long)row;
+                    const bool a_valid = a_e < B.a.n;
+                    const uint32_t base = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(ab * kGN + col0);
+                    uint32_t v[4][32];  // 128 f32 accumulators
+                    float m0, m1, m2, m3;
+                    tmem_ldred32_max_issue(base, v[0], m0);
+                    tmem_ldred32_max_issue(base + 32u, v[1], m1);
+                    tmem_ldred32_max_issue(base + 64u, v[2], m2);
+                    tmem_ldred32_max_issue(base + 96u, v[3], m3);
+                    tmem_wait_ld(v[0]);
+                    tmem_regs_ready(v[1]);
+                    tmem_regs_ready(v[2]);
+                    tmem_regs_ready(v[3]);
+                    float_ready(m0);
+                    float_ready(m1);
+                    float_ready(m2);
+                    float_ready(m3);
+                    const float m = fmaxf(fmaxf(m0, m1), fmaxf(m2, m3));
+                    if (m >= bound && a_valid) {
+                        // side path: which columns reach the bound, then the exact weight
+                        // from the bit-packed rows, then the key
+                        uint32_t x[NW];
 #pragma unroll
-                    for (int w = 0; w < NW; ++w) x[w] = B.a_tab[a_e * NW + w];
+                        for (int w = 0; w < NW; ++w) x[w] = B.a_tab[a_e * NW + w];
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        uint32_t neg = 0;
+                        for (int c = 0; c < 4; ++c) {
+                            uint32_t neg = 0;
 #pragma unroll
-                        for (int i = 0; i < 32; ++i) neg |= (__uint_as_float(v[q][i]) >= bound ? 1u : 0u) << i;
-                        while (neg) {
-                            const int i = __ffs(neg) - 1;
-                            neg &= neg - 1;
-                            const unsigned long long b_e = bt * kGN + (unsigned long long)(col0 + 32 * q + i);
-                            if (b_e >= B.b.n) continue;
-                            int w = 0;
+                            for (int i = 0; i < 32; ++i) neg |= (__uint_as_float(v[c][i]) >= bound ? 1u : 0u) << i;
+                            while (neg) {
+                                const int i = __ffs(neg) - 1;
+                                neg &= neg - 1;
+                                const unsigned long long b_e = bt * kGN + (unsigned long long)(col0 + 32 * c + i);
+                                if (b_e >= B.b.n) continue;
+                                int w = 0;
 #pragma unroll
-                            for (int z = 0; z < NW; ++z) w += __popc(x[z] ^ B.b_tab[b_e * NW + z]);
-                            const int weight = w + P.base;
-                            if (weight > (int)(*(volatile unsigned int *)P.U)) continue;
-                            const unsigned long long mask = side_mask(s_bn, B.a, a_e) | side_mask(s_bn, B.b, b_e);
-                            const unsigned long long rank = lexrank64(mask, P.k, P.g, DevBinomG{});
-                            atomicMin(P.U, (unsigned int)weight);
-                            atomicMin(&P.slot->key, ((unsigned long long)weight << kKeyRankBits) | rank);
+                                for (int z = 0; z < NW; ++z) w += __popc(x[z] ^ B.b_tab[b_e * NW + z]);
+                                const int weight = w + P.base;
+                                if (weight > (int)(*(volatile unsigned int *)P.U)) continue;
+                                const unsigned long long mask =
+                                    side_mask(s_bn, B.a, a_e) | side_mask(s_bn, B.b, b_e);
+                                const unsigned long long rank = lexrank64(mask, P.k, P.g, DevBinomG{});
+                                atomicMin(P.U, (unsigned int)weight);
+                                atomicMin(&P.slot->key, ((unsigned long long)weight << kKeyRankBits) | rank);
+                            }
                         }
                     }
-                }
-                tc_fence_before();
-                mbar_arrive(bar(ACC_EMPTY + ab));
-                if (tid == 0) {
-                    const unsigned long long b_left = B.b.n - bt * kGN;
-                    cnt += a_valid_rows * (b_left < (unsigned long long)kGN ? b_left : (unsigned long long)kGN);
+                    tc_fence_before();
+                    mbar_arrive(bar(ACC_EMPTY + ab));
+                    if (tid == 0 && a_lo < B.a.n) {
+                        const unsigned long long a_rows = B.a.n - a_lo < (unsigned long long)kGM
+                                                              ? B.a.n - a_lo
+                                                              : (unsigned long long)kGM;
+                        const unsigned long long b_left = B.b.n - bt * kGN;
+                        cnt += a_rows * (b_left < (unsigned long long)kGN ? b_left : (unsigned long long)kGN);
+                    }
                 }
             }
         }
@@ -372,7 +400,8 @@ __global__ void __launch_bounds__(kGramThreads, 1) gram_kernel(const __grid_cons
 template <int NW>
 size_t gram_smem_bytes() {
     constexpr int KA = gram_ka(NW);
-    const size_t need = 2 * (size_t)kGM * KA + (size_t)gram_b_stages(NW) * kGN * KA + 24 * sizeof(uint64_t) +
+    const size_t need = 2 * (size_t)gram_ma(NW) * kGM * KA + (size_t)gram_b_stages(NW) * kGN * KA +
+                        24 * sizeof(uint64_t) +
                         sizeof(uint32_t) * (size_t)(kBn * kBn);
     return need < (size_t)(120 << 10) ? (size_t)(120 << 10) : need;
 }
@@ -599,7 +628,8 @@ cudaError_t launch_gram_unit(const EnumParams &ep, const GramBlockSpec *blocks, 
             G.a_tab = S.a_tab;
             G.b_tab = S.b_tab;
             G.b_exp = S.b_exp;
-            G.a_tiles = (S.a.n + kGM - 1) / kGM;
+            const unsigned long long rows = (unsigned long long)gram_ma(ep.nwords) * kGM;
+            G.a_tiles = (S.a.n + rows - 1) / rows;
             G.b_tiles = (S.b.n + kGN - 1) / kGN;
             G.b_units = (G.b_tiles + p.tiles_per_unit - 1) / p.tiles_per_unit;
             G.wu_begin = wu;
