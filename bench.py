@@ -54,7 +54,7 @@ FP8_PER_BF16 = 2.0
 # DRAM bytes (read + write) per launch of the dominant kernel (the tensor-core
 # enumerator), from the ncu capture summarised in profiles/ (None until captured for
 # the current kernel)
-TRAFFIC_PER_LAUNCH = {}  # gram_kernel<4>: to be re-captured after the two-A-tile change
+TRAFFIC_PER_LAUNCH = {"192x64": 299398976}  # gram_kernel<4>, average over the 24 launches of a timed step
 
 
 def _env_int(name, default):
