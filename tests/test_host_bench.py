@@ -1,0 +1,46 @@
+"""bench.py's reference arm (the CPU oracle on a bounded sample) on the CPU: the JSON
+line of the contract, the sample's codeword count against its closed form, and the
+other ranks of a multi-rank launch exiting without work."""
+
+import json
+import math
+import os
+import subprocess
+import sys
+
+from conftest import ROOT
+
+
+def _run(extra_env=None, *args):
+    env = dict(os.environ)
+    env.update(extra_env or {})
+    r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", *args], cwd=ROOT, env=env,
+                       capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    return [ln for ln in r.stdout.splitlines() if ln.strip()]
+
+
+def test_reference_arm_line():
+    lines = _run(None, "--steps", "2", "--warmup", "1", "--ref-levels", "5")
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for key in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+                "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e", "gpu_launches"):
+        assert key in d, key
+    assert d["impl"] == "reference" and d["steps"] == 2 and d["warmup"] == 1 and d["n_gpus"] == 1
+    assert d["unit"] == "codewords/s" and d["higher_is_better"] is True and d["vs_baseline"] is None
+    assert d["value"] > 0 and d["ms_per_step"] > 0 and d["gpu_launches"] == 0
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["unit"] == d["unit"]
+    e = d["e2e"]
+    assert e["value"] == d["value"] and e["h2d_bytes_per_step"] == 0 and e["d2h_bytes_per_step"] == 0
+    # [192,64] with three full-rank sets: every unit (g, j), g <= 5, enumerates C(64, g) combinations
+    per_step = 3 * sum(math.comb(64, g) for g in range(1, 6))
+    assert f"({per_step} codewords per step)" in d["config"]["sample"]
+    assert d["config"]["n"] == 192 and d["config"]["k"] == 64
+
+
+def test_reference_arm_other_ranks_exit_quietly():
+    lines = _run({"RANK": "1", "WORLD_SIZE": "2", "LOCAL_RANK": "1"}, "--gpus", "2", "--steps", "1", "--warmup", "1",
+                 "--ref-levels", "3")
+    assert lines == []
