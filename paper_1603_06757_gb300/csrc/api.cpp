@@ -888,7 +888,7 @@ int mdist_state_save(const mdist_code *c, void *buf, size_t *len) {
         return MDIST_EINVAL;
     }
     StateBlob b;
-    std::memset(&b, 0, sizeof b);
+    std::memset(static_cast<void *>(&b), 0, sizeof b);  // padding too: the blob's bytes are deterministic
     b.magic = kMagic;
     b.version = 1;
     b.n = (uint32_t)c->n;
