@@ -3,7 +3,6 @@ equal to the oracle's skip mode, on codes whose partial sets are idle at the low
 levels; the [150,64] config (a rank-22 set, idle below level 42) gives the same d with
 a third less work; the mode is refused with the per-matrix check."""
 
-
 import numpy as np
 import pytest
 
