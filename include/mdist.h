@@ -20,6 +20,8 @@
  *    released by mdist_free().
  *  - Device memory: the library allocates through opts->dev_alloc / dev_free when
  *    given (e.g. a PyTorch caching allocator), else with cudaMalloc / cudaFree.
+ *    dev_alloc must return memory aligned to at least 16 bytes (cudaMalloc and
+ *    PyTorch's allocator give 256 or more) or NULL when it cannot.
  *  - Work is issued on the stream given to mdist_prepare (NULL = legacy default
  *    stream).  Calls return after their results are on the host.
  *  - Return value: MDIST_OK (0) or a negative MDIST_E* code; no exception or signal

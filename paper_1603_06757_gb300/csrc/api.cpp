@@ -164,17 +164,19 @@ uint64_t side_key(int j, const mdist::GramSide &S, bool expanded) {
 }
 
 // Device memory for a table: 256-byte aligned pieces of chunks of at least 64 MiB, so
-// that a run's hundreds of tables cost a handful of allocator calls.
+// that a run's hundreds of tables cost a handful of allocator calls.  The first piece
+// starts at the chunk's first 256-byte boundary, whatever the allocator's alignment
+// (bulk copies and vector stores need 16-byte aligned tables).
 void *table_alloc(mdist_code *c, size_t bytes) {
     constexpr size_t kChunk = 64ull << 20, kAlign = 256;
     bytes = (bytes + kAlign - 1) / kAlign * kAlign;
     if (c->tab_chunks.empty() || c->chunk_used + bytes > c->chunk_size) {
-        const size_t size = bytes > kChunk ? bytes : kChunk;
+        const size_t size = (bytes > kChunk ? bytes : kChunk) + kAlign;
         void *p = dev_alloc(c, size);
         if (!p) return nullptr;
         c->tab_chunks.push_back(p);
         c->chunk_size = size;
-        c->chunk_used = 0;
+        c->chunk_used = (kAlign - (size_t)((uintptr_t)p % kAlign)) % kAlign;
     }
     void *p = (char *)c->tab_chunks.back() + c->chunk_used;
     c->chunk_used += bytes;

@@ -482,8 +482,17 @@ __global__ void side_tables_kernel(const uint32_t *rows, int k, const __grid_con
         add_rows(x, ((unsigned long long)m0 << S.off[0]) | ((unsigned long long)m1 << S.off[1]));
         uint32_t *out = J.out[i];
         for (;;) {
+            // one vector store per entry where the row size allows it (the tables are
+            // 256-byte aligned): a warp's stores are 256 bytes apart, so each store
+            // instruction is one L2 write request per lane however wide it is
+            if constexpr (NW == 4) {
+                *reinterpret_cast<uint4 *>(out + e * 4) = make_uint4(x[0], x[1], x[2], x[3]);
+            } else if constexpr (NW == 2) {
+                *reinterpret_cast<uint2 *>(out + e * 2) = make_uint2(x[0], x[1]);
+            } else {
 #pragma unroll
-            for (int w = 0; w < NW; ++w) out[e * NW + w] = x[w];
+                for (int w = 0; w < NW; ++w) out[e * NW + w] = x[w];
+            }
             if (++e >= e_end) break;
             unsigned long long diff;
             if (e0 + 1 < S.cnt0) {
