@@ -2,14 +2,19 @@
 call, a rank-deficient G is refused on the host, every error code has its message,
 and a valid code on a machine without a device is refused with MDIST_ECUDA (the
 library has no CPU path to fall back to).  The Python binding refuses to run without
-a device or without the built library."""
+a device or without the built library.  The header is plain C: a C99 program
+(`tests/c_abi_example.c`) compiles against it and links with the library."""
 
 import ctypes
+import os
+import shutil
+import subprocess
 
 import numpy as np
 import pytest
 
 import synth
+from conftest import ROOT
 from paper_1603_06757_gb300 import _lib as L
 
 P64 = L.P64
@@ -141,3 +146,31 @@ def test_python_binding_refuses_without_library(monkeypatch, tmp_path):
     monkeypatch.setattr(L, "_lib", None)
     with pytest.raises(ImportError, match="build the CUDA library"):
         L.lib()
+
+
+def _compile_example(tmp_path, compiler, std):
+    cc = shutil.which(compiler)
+    if cc is None:
+        pytest.skip(f"{compiler} not found")
+    exe = tmp_path / f"c_abi_example_{compiler.replace('+', 'x')}"
+    src = os.path.join(ROOT, "tests", "c_abi_example.c")
+    lang = ["-x", "c++"] if compiler.endswith("++") else []
+    cmd = [cc, *lang, f"-std={std}", "-Wall", "-Wextra", "-pedantic", "-Werror", "-I", os.path.join(ROOT, "include"),
+           src, "-x", "none", "-L", os.path.dirname(L.LIB_PATH), "-lmdist",
+           f"-Wl,-rpath,{os.path.dirname(L.LIB_PATH)}", "-o", str(exe)]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    return exe
+
+
+@pytest.mark.parametrize("compiler,std", [("gcc", "c99"), ("g++", "c++17")])
+def test_header_is_plain_c_and_links(lib, tmp_path, compiler, std):
+    """The header compiles as strict C99 (and C++17) and a C program linked against the
+    library runs: without a device it is refused with the CUDA error, with one it
+    computes d = 3 for the [7,4] Hamming code."""
+    exe = _compile_example(tmp_path, compiler, std)
+    r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=120)
+    if _no_device():
+        assert r.returncode == 2 and r.stdout.strip() == lib.mdist_strerror(L.ECUDA).decode()
+    else:
+        assert r.returncode == 0 and r.stdout.startswith("d = 3"), r.stdout
