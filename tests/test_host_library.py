@@ -383,3 +383,29 @@ def test_filter_choice(lib):
     assert _choice(lib, 4, 128, 62) == 0
     # [300,50]-like rows (250 bits, threshold ~67): pairs of words
     assert _choice(lib, 8, 250, 67) in (2, 3)
+
+
+@pytest.mark.parametrize("name,seed,ranks", [
+    ("60x30", 1, None),
+    ("192x64", 8, [64, 64, 64]),
+    ("150x64", 1, [64, 64, 22]),
+    ("300x50", 5, [50] * 6),
+])
+def test_single_code_workloads_seed_rule(lib, name, seed, ranks):
+    """The seed rule of the single-code workloads (first seed whose greedy information
+    sets have the stated ranks) picks the same seed with the library's host partition
+    and with the oracle's, and the ranks are the stated ones."""
+    from synth.configs import single_code
+
+    from paper_1603_06757_gb300 import api
+
+    by_lib = single_code(name, lambda G, n, k: [int(r) for r in api.partition_host(G, n)["ranks"]])
+    by_orc = single_code(name, lambda G, n, k: [int(r) for r in oracle.partition(G, n)["ranks"]])
+    assert by_lib[2] == by_orc[2] == seed
+    assert np.array_equal(by_lib[3], by_orc[3])
+    n, k, _, G = by_lib
+    got = [int(r) for r in oracle.partition(G, n)["ranks"]]
+    if ranks is not None:
+        assert got == ranks
+    else:  # [60,30] takes whatever its sets are: (30, 29, 1)
+        assert got == [30, 29, 1]
