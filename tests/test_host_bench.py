@@ -1,6 +1,7 @@
-"""bench.py's reference arm (the CPU oracle on a bounded sample) on the CPU: the JSON
-line of the contract, the sample's codeword count against its closed form, and the
-other ranks of a multi-rank launch exiting without work."""
+"""bench.py on the CPU: the reference arm (the CPU oracle on a bounded sample) — the
+JSON line of the contract, the sample's codeword count against its closed form, the
+other ranks of a multi-rank launch exiting without work — and the clock record taken
+from nvidia-smi during the timed region."""
 
 import json
 import math
@@ -44,3 +45,39 @@ def test_reference_arm_other_ranks_exit_quietly():
     lines = _run({"RANK": "1", "WORLD_SIZE": "2", "LOCAL_RANK": "1"}, "--gpus", "2", "--steps", "1", "--warmup", "1",
                  "--ref-levels", "3")
     assert lines == []
+
+
+def test_clock_sampler_parses_nvidia_smi(tmp_path, monkeypatch):
+    """The clock record of the bench line from nvidia-smi's CSV (a stand-in script on
+    PATH prints it): median SM clock under load, the maximum, the throttle reasons that
+    were active in any sample."""
+    fake = tmp_path / "nvidia-smi"
+    fake.write_text(
+        "#!/bin/sh\n"
+        "echo '0, 2070, 2070, 900.1, 0x0, Not Active, Not Active, Not Active, Not Active'\n"
+        "echo '0, 1950, 2070, 1390.0, 0x4, Not Active, Not Active, Not Active, Active'\n"
+        "echo '0, 1965, 2070, 1385.2, 0x4, Not Active, Not Active, Not Active, Active'\n"
+        "echo 'garbage line'\n"
+        "exec sleep 30\n")
+    fake.chmod(0o755)
+    monkeypatch.setenv("PATH", f"{tmp_path}{os.pathsep}{os.environ.get('PATH', '')}")
+    import time
+
+    import bench
+
+    s = bench.ClockSampler(None)
+    s.start()
+    deadline = time.time() + 10
+    while len(s.rows) < 3 and time.time() < deadline:
+        time.sleep(0.05)
+    rec = s.stop()
+    assert rec == {"sm_mhz": 1965.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 3}
+
+
+def test_clock_sampler_without_nvidia_smi(tmp_path, monkeypatch):
+    monkeypatch.setenv("PATH", str(tmp_path))
+    import bench
+
+    s = bench.ClockSampler(None)
+    s.start()
+    assert s.stop() is None
