@@ -75,8 +75,8 @@ cudaError_t launch_enum_unit(const EnumParams &p, int nwords, int group, bool hi
 // Tensor-core (tcgen05) enumerator for the large product blocks of a unit (gram.cu).
 // A block goes there directly when both of its sides hold at least kGramMinSide
 // entries and the stored rows are at most kGramMaxWords words; a large block with a
-// smaller side is split into sub-blocks whose sides are all large (the large side's
-// half cut in two quarters).
+// smaller side is split into sub-blocks over the two quarters of its large side's half
+// (gram_block_parts in api.cpp), which gives every sub-block two larger sides.
 constexpr int kGramMinSide = 128;
 constexpr int kGramMaxWords = 7;
 constexpr int kMaxGramBlocks = 128;
@@ -106,7 +106,8 @@ cudaError_t launch_gram_unit(const EnumParams &ep, const GramBlockSpec *blocks, 
 // Tables built together (one launch each for the packed sums and for the expansions).
 constexpr int kMaxTableJobs = 128;
 // for i < n: outs[i][e * nwords ..] = the sum of the rows (rows: all k rows of the set)
-// of entry e of sides[i]
+// of entry e of sides[i]; outs[i] 16-byte aligned (rows of 2 and 4 words are stored
+// as one vector per entry)
 cudaError_t launch_side_tables(const uint32_t *rows, int k, int nwords, const GramSide *sides, uint32_t *const *outs,
                                int n, int sm_count, cudaStream_t stream);
 // bytes of the expanded operand tiles of a packed table of `count` entries
