@@ -74,7 +74,13 @@ __global__ void __launch_bounds__(kCtaThreads, MDIST_ENUM_MIN_BLOCKS) enum_unit_
     uint32_t *s_bn = s_rows + P.k * NW;                  // 33 x 33
     unsigned int *s_hist = s_bn + kBn * kBn;             // histogram mode: n+1 bins
 
-    for (int i = threadIdx.x; i < P.k * NW; i += blockDim.x) s_rows[i] = P.rows[i];
+    // bits past n_bits are cleared while staging, so that no weight exceeds n_bits (the
+    // histogram index stays inside s_hist) whatever the caller's padding holds
+    for (int i = threadIdx.x; i < P.k * NW; i += blockDim.x) {
+        const int vb = P.n_bits - 32 * (i % NW);
+        const uint32_t valid = vb >= 32 ? 0xFFFFFFFFu : (vb <= 0 ? 0u : (1u << vb) - 1u);
+        s_rows[i] = P.rows[i] & valid;
+    }
     for (int i = threadIdx.x; i < kBn * kBn; i += blockDim.x) {
         const unsigned long long v = c_binom.v[i / kBn][i % kBn];
         s_bn[i] = (uint32_t)v;  // C(a, b) <= C(32, 16) < 2^32

@@ -12,13 +12,17 @@
 // counter, and the weight histogram when asked for) lives in the file-scope array
 // `g_noalloc_scratch` below, a fixed 8 KiB that every GPU loading the library keeps
 // until the process exits.  Host code must not use the array's name as a device
-// address: its device address is looked up once per device with
-// cudaGetSymbolAddress (with that device current) on the first call made on that
-// device, so that first call should be made before any stream capture starts.
-// Every call shares the array and it keeps the last call's contents; each call
-// clears what must start at zero before the enumeration runs.  Calls whose work
-// overlaps on the GPU (different streams, or different host threads on one device)
-// race on the array: serialise them.
+// address: its device address is looked up with cudaGetSymbolAddress on the first
+// call made in a CUDA context (the context current on the calling thread, with its
+// device), so that first call should be made before any stream capture starts.  The
+// address belongs to that context: it is cached under the context's unique id, so a
+// context created later (after cudaDeviceReset, or a driver-API context the caller
+// makes current) gets its own lookup.  Every call shares the array and it keeps the
+// last call's contents; each call clears what must start at zero before the
+// enumeration runs.  Calls whose work overlaps on the GPU (different streams, or
+// different host threads on one device) race on the array: serialise them.
+#include <cuda.h>  // driver types only: the two driver calls are fetched at run time
+
 #include <mutex>
 
 #include "internal.h"
@@ -46,6 +50,7 @@ __global__ void noalloc_init(unsigned int U, int bins) {
         s->slot.key = kNoKey;
         s->slot.count = 0;
         s->slot.tile_next = 0;
+        s->slot.tc_cand = 0;
     }
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < bins; i += gridDim.x * blockDim.x) s->hist[i] = 0;
 }
@@ -61,30 +66,85 @@ __global__ void noalloc_finish(unsigned long long *out, int bins) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < bins; i += gridDim.x * blockDim.x) out[3 + i] = s->hist[i];
 }
 
-constexpr int kMaxDevices = 64;
+// Per-context set-up: the scratch array's device address and the SM count, cached
+// under the unique id of the CUDA context current on the calling thread.
+constexpr int kMaxContexts = 64;
+struct ContextEntry {
+    unsigned long long ctx_id;
+    void *addr;
+    int sms;
+};
 std::mutex g_setup_mu;
-void *g_scratch_addr[kMaxDevices];
-int g_sm_count[kMaxDevices];
+ContextEntry g_ctx[kMaxContexts];
+int g_nctx = 0;
+int g_next_evict = 0;
 
-// Per-device set-up: the scratch array's device address and the SM count.
+using CtxGetCurrentFn = CUresult (*)(CUcontext *);
+using CtxGetIdFn = CUresult (*)(CUcontext, unsigned long long *);
+CtxGetCurrentFn g_ctx_get_current = nullptr;
+CtxGetIdFn g_ctx_get_id = nullptr;
+
+constexpr int kNoContext = 1;  // nothing current on this thread yet
+
+// Unique id of the context current on the calling thread.
+int current_context_id(unsigned long long *id) {
+    if (!g_ctx_get_current || !g_ctx_get_id) {
+        void *f0 = nullptr, *f1 = nullptr;
+        cudaDriverEntryPointQueryResult q0, q1;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f0, 12000, cudaEnableDefault, &q0) != cudaSuccess ||
+            cudaGetDriverEntryPointByVersion("cuCtxGetId", &f1, 12000, cudaEnableDefault, &q1) != cudaSuccess ||
+            q0 != cudaDriverEntryPointSuccess || q1 != cudaDriverEntryPointSuccess || !f0 || !f1)
+            return MDIST_ECUDA;
+        g_ctx_get_current = (CtxGetCurrentFn)f0;
+        g_ctx_get_id = (CtxGetIdFn)f1;
+    }
+    CUcontext ctx = nullptr;
+    if (g_ctx_get_current(&ctx) != CUDA_SUCCESS) return MDIST_ECUDA;
+    if (!ctx) return kNoContext;
+    if (g_ctx_get_id(ctx, id) != CUDA_SUCCESS) return MDIST_ECUDA;
+    return MDIST_OK;
+}
+
 int noalloc_setup(int dev, void **addr, int *sms) {
     std::lock_guard<std::mutex> lock(g_setup_mu);
-    if (!g_scratch_addr[dev]) {
-        void *p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
-            cudaGetLastError();
+    unsigned long long id = 0;
+    void *p = nullptr;
+    cudaError_t e = cudaSuccess;
+    int rc = current_context_id(&id);
+    if (rc == kNoContext) {
+        // no context yet: the symbol lookup makes the runtime's context current
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p) {
+            if (e != cudaSuccess) cudaGetLastError();  // this call's own error, not the caller's
             return MDIST_ECUDA;
         }
-        int n = 0;
-        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
-            cudaGetLastError();
-            return MDIST_ECUDA;
-        }
-        g_sm_count[dev] = n;
-        g_scratch_addr[dev] = p;
+        rc = current_context_id(&id);
     }
-    *addr = g_scratch_addr[dev];
-    *sms = g_sm_count[dev];
+    if (rc != MDIST_OK) return MDIST_ECUDA;
+    for (int i = 0; i < g_nctx; ++i)
+        if (g_ctx[i].ctx_id == id) {
+            *addr = g_ctx[i].addr;
+            *sms = g_ctx[i].sms;
+            return MDIST_OK;
+        }
+    if (!p) {
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p) {
+            if (e != cudaSuccess) cudaGetLastError();
+            return MDIST_ECUDA;
+        }
+    }
+    int n = 0;
+    e = cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return MDIST_ECUDA;
+    }
+    // context ids are never reused, so a full table drops its oldest entries
+    const int slot = g_nctx < kMaxContexts ? g_nctx++ : (g_next_evict++ % kMaxContexts);
+    g_ctx[slot] = ContextEntry{id, p, n};
+    *addr = p;
+    *sms = n;
     return MDIST_OK;
 }
 
@@ -102,8 +162,10 @@ extern "C" int mdist_enumerate_unit_noalloc(const uint32_t *rows, int k, int nwo
     if (bins > kNoAllocHistBins) return MDIST_ERANGE;  // histogram larger than the scratch holds
     EnumParams p{};
     if (!plan_level(k, g, nwords, p)) return MDIST_ERANGE;
+    // an error the caller has not collected yet stays theirs: report it, clear nothing
+    if (cudaPeekAtLastError() != cudaSuccess) return MDIST_ECUDA;
     int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+    if (cudaGetDevice(&dev) != cudaSuccess) {
         cudaGetLastError();
         return MDIST_ECUDA;
     }
@@ -120,9 +182,13 @@ extern "C" int mdist_enumerate_unit_noalloc(const uint32_t *rows, int k, int nwo
     p.nwords = nwords;
     p.n_bits = n_bits;
     p.base = base;
+    // nothing was pending on entry, so each error collected below is this call's own
     noalloc_init<<<1, 256, 0, stream>>>((unsigned int)U, bins);
     if (cudaGetLastError() != cudaSuccess) return MDIST_ECUDA;
-    if (launch_enum_unit(p, nwords, 0, want_hist != 0, sms, 0, stream) != cudaSuccess) return MDIST_ECUDA;
+    if (launch_enum_unit(p, nwords, 0, want_hist != 0, sms, 0, stream) != cudaSuccess) {
+        cudaGetLastError();
+        return MDIST_ECUDA;
+    }
     noalloc_finish<<<1, 256, 0, stream>>>(out, bins);
     if (cudaGetLastError() != cudaSuccess) return MDIST_ECUDA;
     return MDIST_OK;

@@ -84,6 +84,43 @@ def test_noalloc_matches_allocating_entry_points(env, n, k, seed, j, g):
     assert key == (1 << 64) - 1 and U == want_U - 1 and cnt == math.comb(k, g)
 
 
+@pytest.mark.parametrize("n,k,seed,j,g", [(150, 40, 4, 0, 3), (300, 50, 5, 2, 3)])
+def test_noalloc_ignores_padding_bits(env, n, k, seed, j, g):
+    """Rows whose padding (bits past n_bits in the last word, and a whole extra word per
+    row) holds ones give the same threshold, key and count as the clean rows.  Only the
+    histogram-free form is run on dirty rows."""
+    torch, L, api = env
+    G = synth.random_systematic(n, k, seed)
+    rows, full, nb, nw = _rows_on_device(torch, G, n, j)
+    clean = _call(torch, L, rows, k, nw, nb, full, g, n, False)
+    host = rows.cpu().numpy().view(np.uint32).reshape(k, nw)
+    dirty = np.full((k, nw + 1), 0xA5A5A5A5, dtype=np.uint32)
+    dirty[:, :nw] = host
+    if nb % 32:
+        dirty[:, nw - 1] |= np.uint32(~((1 << (nb % 32)) - 1) & 0xFFFFFFFF)
+    assert not np.array_equal(dirty[:, :nw], host) or nb % 32 == 0
+    drows = torch.from_numpy(dirty.reshape(-1).view(np.int32).copy()).cuda()
+    for _ in range(2):
+        got = _call(torch, L, drows, k, nw + 1, nb, full, g, n, False)
+        assert got[:3] == clean[:3]
+    assert clean[2] == math.comb(k, g)
+
+
+def test_noalloc_histogram_at_the_size_limit(env):
+    """n = 512 (the library's limit), a full-rank set of a k = 8 code at g = k: the
+    histogram has n_bits + g + 1 = 513 bins, exactly the scratch array's capacity."""
+    torch, L, api = env
+    n, k = 512, 8
+    G = synth.random_systematic(n, k, 3)
+    rows, full, nb, nw = _rows_on_device(torch, G, n, 0)
+    assert full == 1 and nb == n - k and nb + k + 1 == 513
+    with api.Code(G, n) as code:
+        want_hist, want_cnt = code.unit_histogram(k, 0)
+    U, key, cnt, hist = _call(torch, L, rows, k, nw, nb, full, k, n, True)
+    assert hist.size == 513 and cnt == want_cnt == 1
+    assert np.array_equal(hist, want_hist)
+
+
 def test_noalloc_rejects_oversize(env):
     torch, L, api = env
     G = synth.random_systematic(150, 40, 4)
