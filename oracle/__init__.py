@@ -74,6 +74,11 @@ def _load():
                                              ctypes.c_int, ctypes.c_int, ctypes.POINTER(OrcResult)]
             lib.orc_min_distance_skip.argtypes = [P64, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                                   ctypes.c_int, ctypes.POINTER(OrcResult)]
+            lib.orc_partition_overlap.argtypes = [P64, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                                  PI, PI, P64, P64, PI]
+            lib.orc_overlap_bound.argtypes = [ctypes.c_int, PI, ctypes.c_int, PI, ctypes.c_int, PI]
+            lib.orc_min_distance_overlap.argtypes = [P64, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                                     ctypes.c_int, ctypes.c_int, ctypes.POINTER(OrcResult)]
             lib.orc_unrank_lex.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_uint64]
             lib.orc_unrank_lex.restype = ctypes.c_uint64
             lib.orc_binomial.argtypes = [ctypes.c_int, ctypes.c_int]
@@ -162,16 +167,59 @@ def enumerate_unit(gamma, n: int, g: int, nthreads: int | None = None, want_hist
     return {"min_w": int(mw[0]), "min_rank": int(mr[0]), "count": int(cnt[0]), "hist": hist, "xor_all": xa}
 
 
+def partition_overlap(G, n: int, msets: int):
+    """M overlapping full information sets (orc_partition_overlap).  Returns dict with m,
+    ranks[m] (relative ranks), pivcols[m,k] (scan order), gammas[m,k,W],
+    transforms[m,k], cover[n]."""
+    G = _as_matrix(G, n)
+    k, W = G.shape
+    rel = np.zeros(MAX_SETS, dtype=np.int32)
+    piv = np.zeros(MAX_SETS * k, dtype=np.int32)
+    gam = np.zeros(MAX_SETS * k * W, dtype=np.uint64)
+    tr = np.zeros(MAX_SETS * k, dtype=np.uint64)
+    cover = np.zeros(n, dtype=np.int32)
+    rc = _load().orc_partition_overlap(_p64(G), n, k, W, int(msets), _pi(rel), _pi(piv), _p64(gam), _p64(tr),
+                                       _pi(cover))
+    if rc == -2:
+        raise ValueError("rank(G) < k")
+    if rc != 0:
+        raise ValueError(f"orc_partition_overlap failed ({rc})")
+    m = int(msets)
+    return {
+        "m": m,
+        "ranks": rel[:m].copy(),
+        "pivcols": piv.reshape(MAX_SETS, k)[:m].copy(),
+        "gammas": gam.reshape(MAX_SETS, k, W)[:m].copy(),
+        "transforms": tr.reshape(MAX_SETS, k)[:m].copy(),
+        "cover": cover,
+    }
+
+
+def overlap_bound(levels, k: int, rel_ranks, cover) -> int:
+    """orc_overlap_bound: the lower bound once set j has all its levels <= levels[j] done."""
+    h = np.ascontiguousarray(np.asarray(levels, dtype=np.int32))
+    rel = np.ascontiguousarray(np.asarray(rel_ranks, dtype=np.int32))
+    cov = np.ascontiguousarray(np.asarray(cover, dtype=np.int32))
+    return int(_load().orc_overlap_bound(len(h), _pi(h), int(k), _pi(rel), len(cov), _pi(cov)))
+
+
 def min_distance(G, n: int, check_per_matrix: bool = False, max_sets: int = MAX_SETS,
-                 nthreads: int | None = None, skip_idle_sets: bool = False) -> dict:
+                 nthreads: int | None = None, skip_idle_sets: bool = False, overlap_sets: int = 0) -> dict:
     """Alg. 1 (plain Brouwer-Zimmerman).  Returns a dict with d, key (w, g, j, rank),
     message, witness[W], g_final, j_final, m, ranks, counts[g][j], L_final, U_final.
     skip_idle_sets: the sets whose bound term is still 0 are left out until it becomes
-    positive, then catch up (orc_min_distance_skip; level check only)."""
+    positive, then catch up (orc_min_distance_skip; level check only).
+    overlap_sets = M > 0: M overlapping full information sets with the bound of
+    orc_overlap_bound (orc_min_distance_overlap; ranks are the relative ranks)."""
     G = _as_matrix(G, n)
     k, W = G.shape
     res = OrcResult()
-    if skip_idle_sets:
+    if overlap_sets:
+        if skip_idle_sets:
+            raise ValueError("overlap_sets and skip_idle_sets are exclusive")
+        rc = _load().orc_min_distance_overlap(_p64(G), n, k, W, int(overlap_sets), 1 if check_per_matrix else 0,
+                                              nthreads or default_threads(), ctypes.byref(res))
+    elif skip_idle_sets:
         if check_per_matrix:
             raise ValueError("skip_idle_sets works with the level check only")
         rc = _load().orc_min_distance_skip(_p64(G), n, k, W, max_sets, nthreads or default_threads(),

@@ -34,6 +34,24 @@
  *                             of weight <= g.  The key is the least (weight, g, j, rank)
  *                             over the units run.
  *
+ *   orc_partition_overlap  -- the non-disjoint information sets of §2 ("a different
+ *   orc_min_distance_overlap  quantity if the information sets are not disjoint"): M sets,
+ *                             each a full information set found by Gauss-Jordan on the
+ *                             ORIGINAL G scanning the columns least covered by earlier sets
+ *                             first (ties by index).  The paper cites the lower bound
+ *                             without printing it; this oracle takes the larger of two
+ *                             bounds that hold for any family of full information sets
+ *                             S_1..S_M once every message of weight <= h_j has been
+ *                             enumerated in Gamma_j (so a codeword not yet seen has at
+ *                             least h_j + 1 ones inside S_j):
+ *                               relative ranks: sum_j max(0, h_j + 1 - (k - rho_j)), rho_j =
+ *                                 the pivots of S_j no earlier set holds (the ones inside
+ *                                 S_j but outside the new positions number at most k - rho_j);
+ *                               coverage: with cov(i) = number of sets holding position i,
+ *                                 sum_{i in supp} cov(i) = sum_j |supp & S_j| >=
+ *                                 sum_j (h_j + 1), so the weight is at least the least w
+ *                                 whose w largest cov values reach that sum.
+ *
  * Bit layout: an R x n matrix is R rows of W uint64 words, bit i of a row in word i>>6
  * at bit i&63.  Parallelism: POSIX threads over the first element of each combination
  * with a shared counter (the dynamic schedule over the first recursion level of §4.3).
@@ -501,5 +519,139 @@ int orc_min_distance(const u64 *G, int n, int k, int W, int check_per_matrix, in
         if ((msg >> b) & 1)
             for (int w = 0; w < W; w++) out->witness[w] ^= G[(size_t)b * W + w];
     free(ranks); free(piv); free(gam); free(tr);
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------------ */
+/* overlapping information sets (the non-disjoint case of §2)                      */
+/* ------------------------------------------------------------------------------ */
+
+/* M full information sets.  Set j: Gauss-Jordan on a fresh copy of the original G over
+ * ALL n columns, scanned in the order (cover count so far, column index) ascending; a
+ * column is a pivot iff some row at or below the current pivot position has a 1 in it;
+ * the lowest such row is swapped up and the column is cleared in every other row; the
+ * scan stops at rank k.  Outputs per set j < M: rel_ranks[j] (pivots of S_j that no
+ * earlier set holds), pivcols[j*k + i] (the i-th pivot in scan order), gammas and
+ * transforms as orc_partition; cover[0..n-1] = number of sets holding each column. */
+int orc_partition_overlap(const u64 *G, int n, int k, int W, int msets, int *rel_ranks, int *pivcols, u64 *gammas,
+                          u64 *transforms, int *cover) {
+    if (check_shape(G, n, k, W) != ORC_OK || !rel_ranks || !pivcols || !gammas || !transforms || !cover)
+        return ORC_EINVAL;
+    if (msets < 1 || msets > ORC_MAX_SETS) return ORC_EINVAL;
+    u64 M[ORC_MAX_K * ORC_MAX_W];
+    u64 T[ORC_MAX_K];
+    int order[ORC_MAX_N];
+    for (int c = 0; c < n; c++) cover[c] = 0;
+    for (int j = 0; j < msets; j++) {
+        /* scan order: by cover count, then by column */
+        int len = 0;
+        for (int cv = 0; cv <= j; cv++)
+            for (int c = 0; c < n; c++)
+                if (cover[c] == cv) order[len++] = c;
+        memcpy(M, G, sizeof(u64) * (size_t)k * (size_t)W);
+        for (int r = 0; r < k; r++) T[r] = (u64)1 << r;
+        int p = 0;
+        int piv[ORC_MAX_K];
+        for (int q = 0; q < len && p < k; q++) {
+            const int c = order[q];
+            int i = p;
+            while (i < k && !get_bit(M + (size_t)i * W, c)) i++;
+            if (i == k) continue;
+            if (i != p) {
+                for (int w = 0; w < W; w++) { u64 t = M[i * W + w]; M[i * W + w] = M[p * W + w]; M[p * W + w] = t; }
+                u64 t = T[i]; T[i] = T[p]; T[p] = t;
+            }
+            for (int r = 0; r < k; r++) {
+                if (r != p && get_bit(M + (size_t)r * W, c)) {
+                    for (int w = 0; w < W; w++) M[r * W + w] ^= M[p * W + w];
+                    T[r] ^= T[p];
+                }
+            }
+            piv[p++] = c;
+        }
+        if (p < k) return ORC_ERANK;
+        int fresh = 0;
+        for (int i = 0; i < k; i++) fresh += cover[piv[i]] == 0;
+        rel_ranks[j] = fresh;
+        for (int i = 0; i < k; i++) pivcols[j * k + i] = piv[i];
+        memcpy(gammas + (size_t)j * k * W, M, sizeof(u64) * (size_t)k * (size_t)W);
+        memcpy(transforms + (size_t)j * k, T, sizeof(u64) * (size_t)k);
+        for (int i = 0; i < k; i++) cover[piv[i]]++;
+    }
+    return ORC_OK;
+}
+
+/* Lower bound once set j has all of its units of levels <= h[j] enumerated (h[j] = 0:
+ * none), for full information sets with relative ranks rel[] and cover counts cover[]:
+ * the larger of the relative-rank sum and the coverage bound (see the header). */
+int orc_overlap_bound(int m, const int *h, int k, const int *rel, int n, const int *cover) {
+    int Lrel = 0;
+    long demand = 0;
+    for (int j = 0; j < m; j++) {
+        Lrel += set_bound(h[j], k, rel[j]);
+        demand += h[j] + 1;
+    }
+    /* cover counts in decreasing order (counting sort: counts are at most m) */
+    int Lcov = 0;
+    long sum = 0;
+    for (int cv = m; cv >= 1 && sum < demand; cv--)
+        for (int c = 0; c < n && sum < demand; c++)
+            if (cover[c] == cv) { sum += cv; Lcov++; }
+    if (sum < demand) Lcov = n + 1; /* no support of any size carries the demand */
+    return Lrel > Lcov ? Lrel : Lcov;
+}
+
+/* Alg. 1 over M overlapping full information sets: levels g = 1, 2, ... over every set
+ * while g <= k and L < U, with L = orc_overlap_bound after each level (or, with
+ * check_per_matrix, after each unit: sets up to j at level g, the later ones at g - 1).
+ * Key, counts and witness as orc_min_distance; out->ranks holds the relative ranks. */
+int orc_min_distance_overlap(const u64 *G, int n, int k, int W, int msets, int check_per_matrix, int nthreads,
+                             orc_result *out) {
+    if (check_shape(G, n, k, W) != ORC_OK || !out || msets < 1 || msets > ORC_MAX_SETS) return ORC_EINVAL;
+    memset(out, 0, sizeof *out);
+    int *rel = (int *)calloc(ORC_MAX_SETS, sizeof(int));
+    int *piv = (int *)calloc((size_t)ORC_MAX_SETS * k, sizeof(int));
+    u64 *gam = (u64 *)calloc((size_t)ORC_MAX_SETS * k * W, sizeof(u64));
+    u64 *tr = (u64 *)calloc((size_t)ORC_MAX_SETS * k, sizeof(u64));
+    int *cover = (int *)calloc((size_t)n, sizeof(int));
+    int *h = (int *)calloc(ORC_MAX_SETS, sizeof(int));
+    if (!rel || !piv || !gam || !tr || !cover || !h) {
+        free(rel); free(piv); free(gam); free(tr); free(cover); free(h);
+        return ORC_ENOMEM;
+    }
+    int rc = orc_partition_overlap(G, n, k, W, msets, rel, piv, gam, tr, cover);
+    if (rc != ORC_OK) { free(rel); free(piv); free(gam); free(tr); free(cover); free(h); return rc; }
+    const int m = msets;
+    out->m = m;
+    for (int j = 0; j < m; j++) out->ranks[j] = rel[j];
+    int L = 1, U = n - k + 1;
+    int have_key = 0;
+    int g = 1;
+    while (g <= k && L < U) {
+        for (int j = 0; j < m; j++) {
+            int w; u64 rank, cnt;
+            orc_enumerate_unit(gam + (size_t)j * k * W, n, k, W, g, nthreads, &w, &rank, &cnt, NULL, NULL);
+            out->counts[g * ORC_MAX_SETS + j] = cnt;
+            out->g_final = g; out->j_final = j;
+            if (!have_key || w < out->key_w) {
+                out->key_w = w; out->key_g = g; out->key_j = j; out->key_rank = rank;
+                have_key = 1;
+            }
+            if (w < U) U = w;
+            h[j] = g;
+            if (check_per_matrix) {
+                const int Lm = orc_overlap_bound(m, h, k, rel, n, cover);
+                if (Lm > L) L = Lm;
+                if (L >= U) break;
+            }
+        }
+        if (!check_per_matrix) L = orc_overlap_bound(m, h, k, rel, n, cover);
+        if (L >= U) break;
+        g++;
+    }
+    out->d = U;
+    out->L_final = L; out->U_final = U;
+    witness_of_key(G, k, W, tr, out);
+    free(rel); free(piv); free(gam); free(tr); free(cover); free(h);
     return ORC_OK;
 }
