@@ -149,8 +149,17 @@ def weak_value(world: int, units_per_rank: float, max_seconds: float) -> float:
     return world * units_per_rank / max_seconds
 
 
-def workload(name):
+def workload(name, ranks_by="library"):
+    """(n, k, seed, G) of a single-code workload.  The seed rule needs information-set
+    ranks: the library's host partition on the GPU arm, the oracle's own partition on
+    the oracle arm (which then loads nothing of the package).  Both follow the same
+    reading and agree set for set (tested)."""
     import synth.configs as cfg
+
+    if ranks_by == "oracle":
+        import oracle
+
+        return cfg.single_code(name, lambda G, n, k: [int(r) for r in oracle.partition(G, n)["ranks"]])
     from paper_1603_06757_gb300 import api
 
     return cfg.single_code(name, lambda G, n, k: [int(r) for r in api.partition_host(G, n)["ranks"]])
@@ -174,9 +183,7 @@ def run_reference(args):
     rank = _env_int("RANK", 0)
     if rank != 0:
         return 0
-    import oracle
-
-    n, k, seed, G = workload(args.workload)
+    n, k, seed, G = workload(args.workload, ranks_by="oracle")
     threads = os.cpu_count() or 1
     step_vals = []
     for i in range(args.warmup + args.steps):

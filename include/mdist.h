@@ -75,7 +75,12 @@ typedef struct {
                                 32-bit words), exact weight only where the bound does not
                                 already exceed the threshold, 5 = groups of 4, then of 2,
                                 then exact.  Results are identical. */
-    long long timeout_cycles;/* bound for device-side waits (batched / serving); 0 = default */
+    long long timeout_cycles;/* bound of the tensor-core enumerator's pipeline waits, in polls
+                                of an mbarrier (each poll may suspend for a hardware-chosen
+                                time); 0 = default (2e8).  A wait that runs out ends the launch
+                                early (after its own copies and MMAs have drained, which
+                                get at least the default bound) and the call returns
+                                MDIST_ETIMEOUT; the handle stays usable.  Negative: EINVAL. */
     mdist_alloc_fn dev_alloc;/* optional device allocator */
     mdist_free_fn dev_free;
     void *alloc_ctx;
@@ -101,6 +106,20 @@ typedef struct {
                                 single-code handles only (MDIST_EINVAL in batch and
                                 server handles); mdist_run's max_units is rounded up to
                                 whole levels. */
+    int overlap_sets;        /* M > 0: M overlapping full information sets instead of the
+                                disjoint ones (the non-disjoint case of §2, whose bound
+                                the paper cites without printing).  Set j is found by
+                                Gauss-Jordan on the original G scanning the columns held by
+                                the fewest earlier sets first (ties by index) until rank k,
+                                so every Gamma_j is systematic on k positions.  After
+                                set j has all messages of weight <= h_j done, a codeword not
+                                yet seen has >= h_j + 1 ones inside S_j; L is the larger of
+                                sum_j max(0, h_j + 1 - (k - rho_j)), rho_j the relative rank
+                                (pivots of S_j no earlier set holds), and the least w whose
+                                w largest cover counts (sets holding a position) add up to
+                                sum_j (h_j + 1).  Reported ranks are the relative ranks.
+                                Pays off when n < 2k.  Single-code handles only; not with
+                                skip_idle_sets (MDIST_EINVAL). */
 } mdist_options;
 
 /* Witness key: the least (weight, g, j, rank) over the enumerated units (a total
@@ -129,6 +148,8 @@ typedef struct {
     int32_t tc_launches;      /* tensor-core enumerator launches */
     int32_t reserved;
     uint64_t tc_combos;       /* combinations those launches enumerated */
+    uint64_t tc_candidates;   /* pairs of those launches whose accumulator reached the candidate
+                                 bound (n_bits - 2 (U - base)) and were re-weighed exactly */
 } mdist_stats;
 
 typedef struct mdist_code mdist_code; /* opaque */
@@ -160,6 +181,14 @@ int mdist_info_sets(const mdist_code *code, int *m, int *ranks, int32_t *pivcols
  * ([m] for j = -1, else [1]).  Does not change the state used by mdist_run. */
 int mdist_enumerate_level(mdist_code *code, int g, int j, int *U_inout, mdist_key *key_inout,
                           uint64_t *combos_out);
+
+/* Tensor-core counters of the last mdist_enumerate_level call on this handle, summed
+ * over its units: *tc_combos = combinations the tensor-core enumerator covered,
+ * *tc_candidates = those whose accumulator reached the candidate bound and were
+ * re-weighed exactly from the packed rows (the filter's pass count: at a threshold
+ * near the least weight it is a tiny fraction of *tc_combos).  Either pointer may be
+ * NULL. */
+int mdist_level_counters(const mdist_code *code, uint64_t *tc_combos, uint64_t *tc_candidates);
 
 /* Debug / parity form of one unit: the full weight histogram hist[0..n] of the
  * C(k, g) codewords c * Gamma_j (weights over all n columns) and their count. */
@@ -267,6 +296,14 @@ int mdist_server_submit(mdist_server *srv, const uint64_t *G, int n, int k, int 
 int mdist_server_poll(mdist_server *srv, long long request_id, int wait_ms, int *d, uint64_t *witness,
                       uint64_t *message, mdist_key *key, mdist_stats *stats, double *latency_s);
 
+/* Cancel a request.  Still queued: it is dropped at once.  In a slot: it leaves the
+ * batch at the next round boundary (its device slot and rows are freed).  Running on
+ * the single-code path: that run finishes first.  Either way its poll then returns
+ * MDIST_ECANCELLED.  Returns MDIST_OK if the request was queued or in flight,
+ * MDIST_EAGAIN if it had already finished (its result stays available to poll),
+ * MDIST_EINVAL for an unknown id (never submitted, or already polled). */
+int mdist_server_cancel(mdist_server *srv, long long request_id);
+
 /* Counters: requests admitted and completed, rounds run, requests queued and in
  * flight, summed CUDA-event time of the rounds (ms).  Returns the server's sticky
  * error, if any. */
@@ -326,7 +363,9 @@ int mdist_microbench(int which, int iters, double *ops_per_clock_per_sm, double 
 /* ---- one unit without any device allocation ---------------------------------------- */
 
 /* Capacity of the fixed scratch array behind mdist_enumerate_unit_noalloc: histogram
- * bins (n_bits + g + 1 for a full-rank set, n_bits + 1 otherwise). */
+ * bins (n_bits + g + 1 for a full-rank set, n_bits + 1 otherwise).  Both are at most
+ * n + 1 (a full-rank set stores n_bits = n - k bits and g <= k), so every code with
+ * n <= MDIST_MAX_N fits. */
 #define MDIST_NOALLOC_MAX_HIST_BINS 513
 
 /* Enumerate one (g, j) unit, as mdist_enumerate_level / mdist_unit_histogram do, for
@@ -337,7 +376,9 @@ int mdist_microbench(int which, int iters, double *ops_per_clock_per_sm, double 
  *
  * Inputs: `rows` (device) = the set's stored rows, k rows of nwords 32-bit words (the
  * layout mdist_debug_set_rows returns: for a full-rank set the n_bits = n - k
- * non-pivot columns, full_rank = 1; otherwise all n_bits = n columns, full_rank = 0);
+ * non-pivot columns, full_rank = 1; otherwise all n_bits = n columns, full_rank = 0).
+ * Bits at positions >= n_bits of a row (the last word's padding and any whole words
+ * after it) are ignored: the kernel clears them when it stages the rows.
  * level g; candidates are codewords of weight <= U.  Output `out` (device, caller-
  * owned, 3 + bins uint64): out[0] = min(U, least candidate weight), out[1] = least
  * key weight << 54 | lexicographic rank, or 2^64-1 if no candidate, out[2] =
@@ -348,11 +389,17 @@ int mdist_microbench(int which, int iters, double *ops_per_clock_per_sm, double 
  * Memory: no cudaMalloc, cudaFree or other allocating call.  The unit's scratch state
  * (threshold, key, count, work counter, histogram) lives in one fixed 8 KiB device
  * array that every GPU loading the library keeps until the process exits.  The first
- * call on a device looks up that array's device address (so make it before any stream
- * capture starts).  Each call clears the scratch it uses, but all calls share it:
- * calls that may overlap on the GPU (other streams, other host threads) race and must
- * be serialised by the caller.  MDIST_ERANGE if the histogram needs more than
- * MDIST_NOALLOC_MAX_HIST_BINS bins or C(k, g) >= 2^54; MDIST_EINVAL for bad sizes. */
+ * call in a CUDA context (the one current on the calling thread) looks up that array's
+ * device address in that context and caches it under the context's unique id, so make
+ * that first call before any stream capture starts; a new context (after
+ * cudaDeviceReset, or a driver-API context the caller makes current) gets its own
+ * lookup on its first call.  Each call clears the scratch it uses, but all calls share
+ * it: calls that may overlap on the GPU (other streams, other host threads) race and
+ * must be serialised by the caller.  MDIST_ERANGE if the histogram needs more than
+ * MDIST_NOALLOC_MAX_HIST_BINS bins or C(k, g) >= 2^54; MDIST_EINVAL for bad sizes;
+ * MDIST_ECUDA if a CUDA error is already pending when the call starts (the call then
+ * launches nothing and leaves that error for the caller to collect) or if one of its
+ * launches fails. */
 int mdist_enumerate_unit_noalloc(const uint32_t *rows, int k, int nwords, int n_bits, int full_rank, int g, int U,
                                  int want_hist, unsigned long long *out, void *cuda_stream);
 
@@ -369,6 +416,18 @@ int mdist_tc_probe(const uint8_t *A, const uint8_t *B, int N, int K, float *D);
  * MDIST_MAX_SETS.  MDIST_ERANK if rank(G) < k. */
 int mdist_partition_host(const uint64_t *G, int n, int k, int words_per_row, int max_sets, int *m, int *ranks,
                          int32_t *pivcols, uint64_t *gammas, uint64_t *transforms);
+
+/* The overlapping sets of mdist_options.overlap_sets = msets, computed on the host:
+ * ranks[msets] (relative ranks), pivcols[msets*k] (in the order found), gammas,
+ * transforms (as mdist_info_sets) and cover[n] (number of sets holding each column).
+ * Any output may be NULL. */
+int mdist_partition_overlap_host(const uint64_t *G, int n, int k, int words_per_row, int msets, int *ranks,
+                                 int32_t *pivcols, uint64_t *gammas, uint64_t *transforms, int32_t *cover);
+
+/* The lower bound L of that mode once set j has all messages of weight <= levels[j]
+ * done (levels[msets]; 0 = none). */
+int mdist_overlap_bound_host(const uint64_t *G, int n, int k, int words_per_row, int msets, const int *levels,
+                             int *L);
 
 /* Row layout the enumerator reads for set j (0-based): a full-rank set stores its
  * n - k non-pivot columns (every codeword of a weight-g combination has exactly g

@@ -44,6 +44,7 @@ class Options(ctypes.Structure):
         ("wstar_hint", ctypes.c_int),
         ("tensor_cores", ctypes.c_int),
         ("skip_idle_sets", ctypes.c_int),
+        ("overlap_sets", ctypes.c_int),
     ]
 
 
@@ -79,6 +80,7 @@ class Stats(ctypes.Structure):
         ("tc_launches", ctypes.c_int32),
         ("reserved", ctypes.c_int32),
         ("tc_combos", ctypes.c_uint64),
+        ("tc_candidates", ctypes.c_uint64),
     ]
 
 
@@ -104,6 +106,7 @@ SIGNATURES = {
     "mdist_info_sets": (ctypes.c_int, [PCODE, PI, PI, PI32, P64, P64]),
     "mdist_enumerate_level": (ctypes.c_int, [PCODE, ctypes.c_int, ctypes.c_int, PI, ctypes.POINTER(Key), P64]),
     "mdist_unit_histogram": (ctypes.c_int, [PCODE, ctypes.c_int, ctypes.c_int, P64, P64]),
+    "mdist_level_counters": (ctypes.c_int, [PCODE, P64, P64]),
     "mdist_run": (ctypes.c_int, [PCODE, ctypes.c_int, PI]),
     "mdist_reset": (ctypes.c_int, [PCODE]),
     "mdist_result": (ctypes.c_int, [PCODE, PI, P64, P64, ctypes.POINTER(Key), ctypes.POINTER(Stats)]),
@@ -134,6 +137,7 @@ SIGNATURES = {
     "mdist_server_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_longlong),
                                          ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong), PI, PI,
                                          ctypes.POINTER(ctypes.c_double)]),
+    "mdist_server_cancel": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_longlong]),
     "mdist_server_free": (None, [ctypes.c_void_p]),
     "mdist_features": (ctypes.c_int, [P64, ctypes.c_int, ctypes.c_int, ctypes.c_int, PF]),
     "mdist_gv_estimate": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, PI, PI, PI]),
@@ -153,6 +157,9 @@ SIGNATURES = {
     "mdist_tc_probe": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int, PF]),
     "mdist_partition_host": (ctypes.c_int, [P64, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, PI, PI,
                                             PI32, P64, P64]),
+    "mdist_partition_overlap_host": (ctypes.c_int, [P64, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, PI,
+                                                    PI32, P64, P64, PI32]),
+    "mdist_overlap_bound_host": (ctypes.c_int, [P64, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, PI, PI]),
     "mdist_debug_set_rows": (ctypes.c_int, [P64, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, PI, PI, PI,
                                             ctypes.POINTER(ctypes.c_uint32)]),
     "mdist_debug_unrank_colex": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_uint32,

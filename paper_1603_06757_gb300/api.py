@@ -63,14 +63,20 @@ class Code:
 
     def __init__(self, G, n: int, *, check_per_matrix: bool = False, max_sets: int = 0, blocks_per_sm: int = 0,
                  filter_group: int = 0, wstar_hint: int = 0, tensor_cores: int = 0, skip_idle_sets: bool = False,
-                 stream=None, torch_alloc: bool = True):
+                 timeout_cycles: int = 0, overlap_sets: int = 0, stream=None, torch_alloc: bool = True,
+                 allocator=None):
+        """allocator: an object with alloc_cb / free_cb (ctypes callbacks of the
+        library's allocator hooks) used instead of torch's caching allocator."""
         torch = _torch()
         self.n = int(n)
         self.G = as_packed(G, n)
         self.k, self.W = self.G.shape
         self._lib = L.lib()
         self._stream = stream if stream is not None else torch.cuda.current_stream()
-        self._alloc = _TorchAllocator(torch, self._stream.device) if torch_alloc else None
+        if allocator is not None:
+            self._alloc = allocator
+        else:
+            self._alloc = _TorchAllocator(torch, self._stream.device) if torch_alloc else None
         opts = L.Options()
         opts.check_per_matrix = 1 if check_per_matrix else 0
         opts.max_sets = int(max_sets)
@@ -79,6 +85,8 @@ class Code:
         opts.wstar_hint = int(wstar_hint)
         opts.tensor_cores = int(tensor_cores)
         opts.skip_idle_sets = 1 if skip_idle_sets else 0
+        opts.timeout_cycles = int(timeout_cycles)
+        opts.overlap_sets = int(overlap_sets)
         if self._alloc is not None:
             opts.dev_alloc = self._alloc.alloc_cb
             opts.dev_free = self._alloc.free_cb
@@ -145,6 +153,14 @@ class Code:
         L.check(rc, "mdist_enumerate_level")
         kt = k.as_tuple()
         return Uc.value, (None if kt[0] == 2**31 - 1 else kt), [int(c) for c in combos]
+
+    def level_counters(self) -> dict:
+        """Tensor-core counters of the last enumerate_level call: combinations covered
+        and pairs re-weighed exactly (the filter's pass count)."""
+        a = np.zeros(1, dtype=np.uint64)
+        b = np.zeros(1, dtype=np.uint64)
+        L.check(self._lib.mdist_level_counters(self._h, _p64(a), _p64(b)), "mdist_level_counters")
+        return {"tc_combos": int(a[0]), "tc_candidates": int(b[0])}
 
     def unit_histogram(self, g: int, j: int):
         hist = np.zeros(self.n + 1, dtype=np.uint64)
@@ -221,6 +237,7 @@ def _result_dict(d, wit, msg, key, st) -> dict:
         "tc_ms": float(st.tc_ms),
         "tc_launches": int(st.tc_launches),
         "tc_combos": int(st.tc_combos),
+        "tc_candidates": int(st.tc_candidates),
     }
 
 
@@ -293,6 +310,11 @@ class Server:
         out["latency_s"] = lat.value
         return out
 
+    def cancel(self, rid: int) -> int:
+        """mdist_server_cancel: OK (queued or in flight: its poll raises ECANCELLED),
+        EAGAIN (already finished) or EINVAL (unknown id); returns the code."""
+        return int(self._lib.mdist_server_cancel(self._h, int(rid)))
+
     def info(self) -> dict:
         a, c, r = ctypes.c_longlong(), ctypes.c_longlong(), ctypes.c_longlong()
         q, f = ctypes.c_int(), ctypes.c_int()
@@ -341,6 +363,33 @@ def partition_host(G, n: int, max_sets: int = 0) -> dict:
         "gammas": gam.reshape(L.MAX_SETS, k, W)[:mm].copy(),
         "transforms": tr.reshape(L.MAX_SETS, k)[:mm].copy(),
     }
+
+
+def partition_overlap_host(G, n: int, msets: int) -> dict:
+    """The overlapping information sets of overlap_sets = msets, computed on the host."""
+    G = as_packed(G, n)
+    k, W = G.shape
+    ranks = np.zeros(msets, dtype=np.int32)
+    piv = np.zeros(msets * k, dtype=np.int32)
+    gam = np.zeros(msets * k * W, dtype=np.uint64)
+    tr = np.zeros(msets * k, dtype=np.uint64)
+    cover = np.zeros(n, dtype=np.int32)
+    rc = L.lib().mdist_partition_overlap_host(_p64(G), int(n), k, W, int(msets), ranks.ctypes.data_as(L.PI),
+                                              piv.ctypes.data_as(L.PI32), _p64(gam), _p64(tr),
+                                              cover.ctypes.data_as(L.PI32))
+    L.check(rc, "mdist_partition_overlap_host")
+    return {"m": int(msets), "ranks": ranks, "pivcols": piv.reshape(msets, k), "gammas": gam.reshape(msets, k, W),
+            "transforms": tr.reshape(msets, k), "cover": cover}
+
+
+def overlap_bound_host(G, n: int, msets: int, levels) -> int:
+    G = as_packed(G, n)
+    k, W = G.shape
+    lv = np.ascontiguousarray(np.asarray(levels, dtype=np.int32))
+    out = ctypes.c_int()
+    L.check(L.lib().mdist_overlap_bound_host(_p64(G), int(n), k, W, int(msets), lv.ctypes.data_as(L.PI),
+                                             ctypes.byref(out)), "mdist_overlap_bound_host")
+    return out.value
 
 
 def microbench(which: str, iters: int = 20000) -> dict:

@@ -32,6 +32,7 @@ struct RunState {
     double tc_ms = 0.0;
     int tc_launches = 0;
     uint64_t tc_combos = 0;
+    uint64_t tc_cand = 0;            // pairs the tensor-core filter passed to the exact recheck
     double seconds = 0.0;
     uint64_t h2d_bytes = 0, d2h_bytes = 0;
     int last_group = 0;
@@ -78,6 +79,8 @@ struct mdist_code {
     std::vector<const uint32_t *> pend_xpacked;
     std::vector<unsigned long long> pend_xcount;
     std::vector<uint8_t *> pend_xout;
+    // tensor-core counters of the last mdist_enumerate_level call (summed over its units)
+    uint64_t level_tc_combos = 0, level_tc_cand = 0;
     RunState st;
 };
 
@@ -345,11 +348,13 @@ int run_unit(mdist_code *c, int g, int j, int U_thr, bool hist_mode, bool *found
     p.nwords = dr.nwords;
     p.n_bits = dr.n_bits;
     p.base = dr.full_rank ? g : 0;
+    p.wait_polls = c->opt.timeout_cycles;
     c->h_slot->U = (unsigned)(U_thr < 0 ? 0 : U_thr);
     c->h_slot->status = 0;
     c->h_slot->key = mdist::kNoKey;
     c->h_slot->count = 0;
     c->h_slot->tile_next = 0;
+    c->h_slot->tc_cand = 0;
     if (cudaMemcpyAsync(c->d_slot, c->h_slot, sizeof(UnitSlot), cudaMemcpyHostToDevice, c->stream) != cudaSuccess)
         return MDIST_ECUDA;
     c->st.h2d_bytes += sizeof(UnitSlot);
@@ -388,6 +393,9 @@ int run_unit(mdist_code *c, int g, int j, int U_thr, bool hist_mode, bool *found
         c->st.tc_launches += 1;
         c->st.tc_combos += tc_combos;
     }
+    c->st.tc_cand += c->h_slot->tc_cand;
+    c->level_tc_combos += tc_combos;
+    c->level_tc_cand += c->h_slot->tc_cand;
     if (c->h_slot->status) return MDIST_ETIMEOUT;
     const unsigned long long key = c->h_slot->key;
     *found = key != mdist::kNoKey;
@@ -466,7 +474,9 @@ int mdist_prepare(const uint64_t *G, int n, int k, int words_per_row, const mdis
     if (!c) return MDIST_ENOMEM;
     if (opts) c->opt = *opts;
     if (c->opt.filter_group < 0 || c->opt.filter_group > 5 || c->opt.tensor_cores < 0 || c->opt.tensor_cores > 3 ||
-        c->opt.skip_idle_sets < 0 || c->opt.skip_idle_sets > 1 || (c->opt.skip_idle_sets && c->opt.check_per_matrix)) {
+        c->opt.skip_idle_sets < 0 || c->opt.skip_idle_sets > 1 || (c->opt.skip_idle_sets && c->opt.check_per_matrix) ||
+        c->opt.timeout_cycles < 0 || c->opt.overlap_sets < 0 || c->opt.overlap_sets > MDIST_MAX_SETS ||
+        (c->opt.overlap_sets && c->opt.skip_idle_sets)) {
         delete c;
         return MDIST_EINVAL;
     }
@@ -476,7 +486,9 @@ int mdist_prepare(const uint64_t *G, int n, int k, int words_per_row, const mdis
     c->W = words_per_row;
     c->G.assign(G, G + (size_t)k * words_per_row);
     c->stream = (cudaStream_t)cuda_stream;
-    rc = mdist::partition_info_sets(G, n, k, words_per_row, c->opt.max_sets, c->part);
+    rc = c->opt.overlap_sets > 0
+             ? mdist::partition_overlapping_sets(G, n, k, words_per_row, c->opt.overlap_sets, c->part)
+             : mdist::partition_info_sets(G, n, k, words_per_row, c->opt.max_sets, c->part);
     if (rc != MDIST_OK) { delete c; return rc; }
     c->m = (int)c->part.sets.size();
     c->rows.resize((size_t)c->m);
@@ -532,7 +544,7 @@ int mdist_info_sets(const mdist_code *c, int *m, int *ranks, int32_t *pivcols, u
     *m = c->m;
     for (int j = 0; j < c->m; ++j) {
         const mdist::InfoSet &s = c->part.sets[(size_t)j];
-        if (ranks) ranks[j] = s.rank;
+        if (ranks) ranks[j] = s.bound_rank;
         if (pivcols)
             for (int i = 0; i < c->k; ++i) pivcols[(size_t)j * c->k + i] = i < s.rank ? s.pivcols[(size_t)i] : -1;
         if (gammas) std::memcpy(gammas + (size_t)j * c->k * c->W, s.gamma.data(), sizeof(uint64_t) * s.gamma.size());
@@ -545,6 +557,7 @@ int mdist_enumerate_level(mdist_code *c, int g, int j, int *U_inout, mdist_key *
     if (!c || !U_inout || !key_inout || g < 1 || g > c->k || j < -1 || j >= c->m) return MDIST_EINVAL;
     const int j0 = j < 0 ? 0 : j;
     const int j1 = j < 0 ? c->m : j + 1;
+    c->level_tc_combos = c->level_tc_cand = 0;
     for (int jj = j0; jj < j1; ++jj) {
         bool found;
         int w;
@@ -558,6 +571,13 @@ int mdist_enumerate_level(mdist_code *c, int g, int j, int *U_inout, mdist_key *
             if (w < *U_inout) *U_inout = w;
         }
     }
+    return MDIST_OK;
+}
+
+int mdist_level_counters(const mdist_code *c, uint64_t *tc_combos, uint64_t *tc_candidates) {
+    if (!c) return MDIST_EINVAL;
+    if (tc_combos) *tc_combos = c->level_tc_combos;
+    if (tc_candidates) *tc_candidates = c->level_tc_cand;
     return MDIST_OK;
 }
 
@@ -608,11 +628,12 @@ static int launch_units(mdist_code *c, std::vector<UnitRef> &list, int U_thr) {
         c->h_wave[u].key = mdist::kNoKey;
         c->h_wave[u].count = 0;
         c->h_wave[u].tile_next = 0;
+        c->h_wave[u].tc_cand = 0;
     }
     UnitSlot &thr_word = c->h_wave[c->wave_cap];
     thr_word.U = (unsigned)(U_thr < 0 ? 0 : U_thr);
     thr_word.status = 0;
-    thr_word.key = thr_word.count = thr_word.tile_next = 0;
+    thr_word.key = thr_word.count = thr_word.tile_next = thr_word.tc_cand = 0;
     unsigned int *d_U = &c->d_wave[c->wave_cap].U;
     if (cudaMemcpyAsync(c->d_wave, c->h_wave, sizeof(UnitSlot) * (size_t)n_units, cudaMemcpyHostToDevice, c->stream) !=
             cudaSuccess ||
@@ -637,6 +658,7 @@ static int launch_units(mdist_code *c, std::vector<UnitRef> &list, int U_thr) {
         q.nwords = dr.nwords;
         q.n_bits = dr.n_bits;
         q.base = dr.full_rank ? g : 0;
+        q.wait_polls = c->opt.timeout_cycles;
         const int fg = c->opt.filter_group;
         int group = fg == 0 ? mdist::choose_filter_group(dr.nwords, dr.n_bits, U_thr - q.base) : (fg == 1 ? 0 : fg);
         if (!mdist::filter_group_valid(group, dr.nwords)) group = 0;
@@ -666,6 +688,7 @@ static int launch_units(mdist_code *c, std::vector<UnitRef> &list, int U_thr) {
             s.tc_launches += 1;
             s.tc_combos += tc_combos[(size_t)u];
         }
+    for (int u = 0; u < n_units; ++u) s.tc_cand += c->h_wave[u].tc_cand;
     for (int u = 0; u < n_units; ++u)
         if (c->h_wave[u].status) return MDIST_ETIMEOUT;
     return MDIST_OK;
@@ -711,18 +734,19 @@ static int run_wave(mdist_code *c, int g_hi, int max_units, int *units_done) {
             if (w < s.U) s.U = w;
         }
         if (c->opt.check_per_matrix) {
-            int Lm = 0;
-            for (int i = 0; i < c->m; ++i) Lm += set_bound(i <= j ? g : g - 1, c->k, c->part.sets[(size_t)i].rank);
+            int h[MDIST_MAX_SETS];
+            for (int i = 0; i < c->m; ++i) h[i] = i <= j ? g : g - 1;
+            const int Lm = mdist::lower_bound(c->part, h);
             if (Lm > s.L) s.L = Lm;
             if (s.L >= s.U) s.finished = 1;
         }
         s.next_j = j + 1;
         if (s.next_j == c->m) {
             s.next_j = 0;
-            if (!c->opt.check_per_matrix) {  // Alg. 1, line 7
-                int Lg = 0;
-                for (int i = 0; i < c->m; ++i) Lg += set_bound(g, c->k, c->part.sets[(size_t)i].rank);
-                s.L = Lg;
+            if (!c->opt.check_per_matrix) {  // Alg. 1, line 7 (or the overlapping sets' bound)
+                int h[MDIST_MAX_SETS];
+                for (int i = 0; i < c->m; ++i) h[i] = g;
+                s.L = mdist::lower_bound(c->part, h);
                 if (s.L >= s.U) s.finished = 1;
             }
             s.next_g = g + 1;
@@ -836,7 +860,7 @@ int mdist_result(const mdist_code *c, int *d, uint64_t *witness, uint64_t *messa
         stats->L_final = s.L;
         stats->U_final = s.U;
         stats->launches = s.launches;
-        for (int j = 0; j < c->m; ++j) stats->ranks[j] = c->part.sets[(size_t)j].rank;
+        for (int j = 0; j < c->m; ++j) stats->ranks[j] = c->part.sets[(size_t)j].bound_rank;
         uint64_t tot = 0;
         for (int g = 0; g <= MDIST_MAX_K; ++g)
             for (int j = 0; j < MDIST_MAX_SETS; ++j) {
@@ -849,6 +873,7 @@ int mdist_result(const mdist_code *c, int *d, uint64_t *witness, uint64_t *messa
         stats->tc_ms = s.tc_ms;
         stats->tc_launches = s.tc_launches;
         stats->tc_combos = s.tc_combos;
+        stats->tc_candidates = s.tc_cand;
         stats->h2d_bytes = s.h2d_bytes + c->rows_bytes;
         stats->d2h_bytes = s.d2h_bytes;
     }
@@ -872,6 +897,7 @@ struct StateBlob {
     uint32_t version, n, k, m;
     uint64_t code_hash;
     int32_t per_matrix;
+    int32_t overlap_sets;
     RunState st;
 };
 constexpr uint64_t kMagic = 0x6d64697374737431ull;  // "mdistst1"
@@ -892,12 +918,13 @@ int mdist_state_save(const mdist_code *c, void *buf, size_t *len) {
     StateBlob b;
     std::memset(static_cast<void *>(&b), 0, sizeof b);  // padding too: the blob's bytes are deterministic
     b.magic = kMagic;
-    b.version = 1;
+    b.version = 2;
     b.n = (uint32_t)c->n;
     b.k = (uint32_t)c->k;
     b.m = (uint32_t)c->m;
     b.code_hash = code_hash(c);
     b.per_matrix = c->opt.check_per_matrix;
+    b.overlap_sets = c->opt.overlap_sets;
     b.st = c->st;
     std::memcpy(buf, &b, sizeof b);
     *len = sizeof b;
@@ -909,8 +936,9 @@ int mdist_state_load(mdist_code *c, const void *buf, size_t len) {
     if (len != sizeof(StateBlob)) return MDIST_ESTATE;
     StateBlob b;
     std::memcpy(&b, buf, sizeof b);
-    if (b.magic != kMagic || b.version != 1 || (int)b.n != c->n || (int)b.k != c->k || (int)b.m != c->m ||
-        b.code_hash != code_hash(c) || b.per_matrix != c->opt.check_per_matrix)
+    if (b.magic != kMagic || b.version != 2 || (int)b.n != c->n || (int)b.k != c->k || (int)b.m != c->m ||
+        b.code_hash != code_hash(c) || b.per_matrix != c->opt.check_per_matrix ||
+        b.overlap_sets != c->opt.overlap_sets)
         return MDIST_ESTATE;
     if (b.st.next_g < 1 || b.st.next_g > c->k + 1 || b.st.next_j < 0 || b.st.next_j >= c->m) return MDIST_ESTATE;
     c->st = b.st;

@@ -404,7 +404,7 @@ void bfree_all(mdist_batch *b) {
 extern "C" {
 
 int mdist_batch_create(const mdist_options *opts, void *cuda_stream, mdist_batch **out) {
-    if (!out || (opts && opts->skip_idle_sets)) return MDIST_EINVAL;
+    if (!out || (opts && (opts->skip_idle_sets || opts->overlap_sets))) return MDIST_EINVAL;
     *out = nullptr;
     mdist_batch *b = new (std::nothrow) mdist_batch();
     if (!b) return MDIST_ENOMEM;

@@ -49,6 +49,42 @@ int mdist_partition_host(const uint64_t *G, int n, int k, int words_per_row, int
     return MDIST_OK;
 }
 
+int mdist_partition_overlap_host(const uint64_t *G, int n, int k, int words_per_row, int msets, int *ranks,
+                                 int32_t *pivcols, uint64_t *gammas, uint64_t *transforms, int32_t *cover) {
+    if (!G || k < 1 || k > MDIST_MAX_K || n <= k || n > MDIST_MAX_N || words_per_row < (n + 63) / 64 ||
+        msets < 1 || msets > MDIST_MAX_SETS)
+        return MDIST_EINVAL;
+    mdist::Partition p;
+    const int rc = mdist::partition_overlapping_sets(G, n, k, words_per_row, msets, p);
+    if (rc != MDIST_OK) return rc;
+    for (int j = 0; j < msets; ++j) {
+        const mdist::InfoSet &s = p.sets[(size_t)j];
+        if (ranks) ranks[j] = s.bound_rank;
+        if (pivcols)
+            for (int i = 0; i < k; ++i) pivcols[(size_t)j * k + i] = s.pivcols[(size_t)i];
+        if (gammas) std::memcpy(gammas + (size_t)j * k * words_per_row, s.gamma.data(), sizeof(uint64_t) * s.gamma.size());
+        if (transforms) std::memcpy(transforms + (size_t)j * k, s.transform.data(), sizeof(uint64_t) * k);
+    }
+    if (cover) {
+        for (int c = 0; c < n; ++c) cover[c] = 0;
+        for (const mdist::InfoSet &s : p.sets)
+            for (int c : s.pivcols) ++cover[c];
+    }
+    return MDIST_OK;
+}
+
+int mdist_overlap_bound_host(const uint64_t *G, int n, int k, int words_per_row, int msets, const int *levels,
+                             int *L) {
+    if (!G || !levels || !L || k < 1 || k > MDIST_MAX_K || n <= k || n > MDIST_MAX_N ||
+        words_per_row < (n + 63) / 64 || msets < 1 || msets > MDIST_MAX_SETS)
+        return MDIST_EINVAL;
+    mdist::Partition p;
+    const int rc = mdist::partition_overlapping_sets(G, n, k, words_per_row, msets, p);
+    if (rc != MDIST_OK) return rc;
+    *L = mdist::lower_bound(p, levels);
+    return MDIST_OK;
+}
+
 int mdist_debug_set_rows(const uint64_t *G, int n, int k, int words_per_row, int j, int *full_rank, int *n_bits,
                          int *nwords, uint32_t *words /* k * 16 */) {
     if (!G || !full_rank || !n_bits || !nwords || !words) return MDIST_EINVAL;

@@ -68,6 +68,10 @@ constexpr int kTilesPerUnit = 64;      // B tiles per work unit (doubled for lar
 constexpr int kUnitsPerSmForLong = 8;  // work units per SM needed to use the doubled unit
 constexpr int kGramThreads = 352;      // 8 epilogue warps, builder warp, producer warp, MMA warp
 constexpr int kSmemOperandBudget = 200 << 10;
+// Polls of a bounded wait: the default for the pipeline's hand-offs, and the floor of
+// the final drains (a role's own copies and MMAs complete without any other thread, so
+// those waits get at least this many polls whatever the caller's bound).
+constexpr long long kDefaultWaitPolls = 200000000ll;
 
 __host__ __device__ constexpr int gram_ka(int nw) { return 32 * nw; }  // bytes per operand row
 
@@ -101,7 +105,8 @@ struct GramParams {
     int nblocks;
     unsigned int tiles_per_unit;  // B tiles per work unit
     unsigned long long total_wu;
-    long long max_wait;
+    long long max_wait;          // polls per hand-off wait
+    long long drain_wait;        // polls per final drain wait (>= kDefaultWaitPolls)
     GramBlock blocks[kMaxGramBlocks];
 };
 
@@ -254,7 +259,7 @@ __global__ void __launch_bounds__(kGramThreads, 1) gram_kernel(const __grid_cons
             // last copy of every stage
             const unsigned long long first = t > (unsigned long long)S ? t - S : 0;
             for (unsigned long long i = first; i < t; ++i)
-                if (!mbar_wait(bar(B_FULL + (int)(i % S)), (uint32_t)((i / S) & 1), P.max_wait)) fail();
+                if (!mbar_wait(bar(B_FULL + (int)(i % S)), (uint32_t)((i / S) & 1), P.drain_wait)) fail();
         }
     } else if (warp == 10) {
         // ---------------- MMA issue ----------------
@@ -297,16 +302,20 @@ __global__ void __launch_bounds__(kGramThreads, 1) gram_kernel(const __grid_cons
                 if (!ok) { fail(); break; }
             }
             mma_commit(bar(DRAIN));
-            if (!mbar_wait(bar(DRAIN), 0, P.max_wait)) fail();  // every MMA has completed
+            if (!mbar_wait(bar(DRAIN), 0, P.drain_wait)) fail();  // every MMA has completed
         }
     } else {
         // ---------------- epilogue (warps 0-7) ----------------
         const int row = 32 * (warp & 3) + lane;  // TMEM lane = A row
         const int col0 = 128 * (warp >> 2);      // first accumulator column of this warp
         unsigned long long t = 0, q = 0, cnt = 0;  // B tiles, accumulators, codewords counted
+        unsigned long long cand = 0;               // pairs this thread re-weighed exactly
         unsigned int u_next = *(volatile unsigned int *)P.U;
         bool ok = true;
-        for (unsigned long long wu = blockIdx.x; wu < P.total_wu && ok && !*s_abort; wu += gridDim.x) {
+        // the TMEM loads below are warp-collective (.sync.aligned), so every decision to
+        // stop is taken for the whole warp: the abort flag and each wait's outcome
+        for (unsigned long long wu = blockIdx.x; wu < P.total_wu && ok && !__any_sync(0xffffffffu, *s_abort != 0);
+             wu += gridDim.x) {
             int b;
             unsigned long long a_tile, bt0, bt1;
             decode_wu(P, wu, b, a_tile, bt0, bt1);
@@ -318,7 +327,7 @@ __global__ void __launch_bounds__(kGramThreads, 1) gram_kernel(const __grid_cons
 #pragma unroll 1
                 for (int h = 0; h < MA; ++h, ++q) {
                     const int ab = (int)(q & 1);
-                    if (!mbar_wait(bar(ACC_FULL + ab), (uint32_t)((q >> 1) & 1), P.max_wait)) {
+                    if (!__all_sync(0xffffffffu, mbar_wait(bar(ACC_FULL + ab), (uint32_t)((q >> 1) & 1), P.max_wait))) {
                         fail();
                         ok = false;
                         break;
@@ -363,6 +372,7 @@ __global__ void __launch_bounds__(kGramThreads, 1) gram_kernel(const __grid_cons
                                 neg &= neg - 1;
                                 const unsigned long long b_e = bt * kGN + (unsigned long long)(col0 + 32 * c + i);
                                 if (b_e >= B.b.n) continue;
+                                ++cand;
                                 int w = 0;
 #pragma unroll
                                 for (int z = 0; z < NW; ++z) w += __popc(x[z] ^ B.b_tab[b_e * NW + z]);
@@ -389,6 +399,7 @@ __global__ void __launch_bounds__(kGramThreads, 1) gram_kernel(const __grid_cons
             }
         }
         if (tid == 0 && cnt) atomicAdd(&P.slot->count, cnt);
+        if (cand) atomicAdd(&P.slot->tc_cand, cand);  // rare except at loose thresholds
     }
     tc_fence_before();
     __syncthreads();
@@ -620,7 +631,8 @@ cudaError_t launch_gram_unit(const EnumParams &ep, const GramBlockSpec *blocks, 
     p.nwords = ep.nwords;
     p.n_bits = ep.n_bits;
     p.base = ep.base;
-    p.max_wait = 200000000ll;
+    p.max_wait = ep.wait_polls > 0 ? ep.wait_polls : kDefaultWaitPolls;
+    p.drain_wait = p.max_wait > kDefaultWaitPolls ? p.max_wait : kDefaultWaitPolls;
     int nb = 0;
     unsigned long long wu = 0;
     for (int pass = 0; pass < 2; ++pass) {

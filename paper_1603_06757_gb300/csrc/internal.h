@@ -32,8 +32,10 @@ struct UnitSlot {
     unsigned long long key;      // least (weight << 54 | rank) among candidates, or kNoKey
     unsigned long long count;    // combinations enumerated
     unsigned long long tile_next;// work counter of the persistent grid
+    unsigned long long tc_cand;  // pairs the tensor-core filter passed to the exact recheck
+    unsigned long long pad[3];
 };
-static_assert(sizeof(UnitSlot) == 32, "slot layout");
+static_assert(sizeof(UnitSlot) == 64, "slot layout");
 
 // One product block of a level: all i-subsets of the first half H1 of the rows,
 // times all (g-i)-subsets of the second half H2.  The larger side is spread over
@@ -60,6 +62,7 @@ struct EnumParams {
     int base;                    // weight every codeword carries outside the reduced row
     int n_bits;                  // bits per reduced row
     int nblocks;
+    long long wait_polls;        // tensor-core enumerator: polls per bounded wait, 0 = default
     unsigned long long total_tiles;
     ProductBlock blocks[kMaxBlocks];
 };

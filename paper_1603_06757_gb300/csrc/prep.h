@@ -7,7 +7,9 @@
 namespace mdist {
 
 struct InfoSet {
-    int rank = 0;
+    int rank = 0;                   // rank of Gamma_j on S_j (k for a full information set)
+    int bound_rank = 0;             // rank entering the lower bound: rank, or for an
+                                    // overlapping set its relative rank (new positions)
     std::vector<int> pivcols;       // rank entries
     std::vector<uint64_t> gamma;    // k x W words: Gamma_j = T_j * G
     std::vector<uint64_t> transform;// k entries: row r of T_j as a mask over G's rows
@@ -15,11 +17,22 @@ struct InfoSet {
 
 struct Partition {
     int n = 0, k = 0, W = 0;
+    bool overlapping = false;       // full information sets that may share positions
     std::vector<InfoSet> sets;
+    std::vector<int> cover_desc;    // overlapping: per position the number of sets holding
+                                    // it, in decreasing order
 };
 
 // Returns MDIST_OK or MDIST_ERANK.
 int partition_info_sets(const uint64_t *G, int n, int k, int W, int max_sets, Partition &out);
+
+// `msets` overlapping full information sets (every Gamma_j systematic on k positions).
+// Returns MDIST_OK or MDIST_ERANK.
+int partition_overlapping_sets(const uint64_t *G, int n, int k, int W, int msets, Partition &out);
+
+// Lower bound on the weight of every codeword not yet enumerated, once set j has all of
+// its units of levels <= h[j] done (h[j] = 0: none).
+int lower_bound(const Partition &p, const int *h);
 
 struct DeviceRows {
     bool full_rank = false;

@@ -17,6 +17,7 @@
 #include <map>
 #include <mutex>
 #include <new>
+#include <set>
 #include <thread>
 #include <utility>
 #include <vector>
@@ -104,6 +105,8 @@ struct mdist_server {
     std::deque<Request *> queue;
     std::deque<Request *> large_queue;  // requests for the single-code tensor-core path
     std::map<long long, Done> done;
+    std::set<long long> live;        // submitted and not finished
+    std::set<long long> cancel_req;  // cancellation asked while in flight
     long long next_id = 1;
     bool stopping = false;
     // serving-thread state
@@ -207,6 +210,7 @@ void run_large(mdist_server *s, Request *rq) {
     o.check_per_matrix = s->opt.check_per_matrix;
     o.max_sets = s->opt.max_sets > 0 && s->opt.max_sets < kServeMaxSets ? s->opt.max_sets : kServeMaxSets;
     o.wstar_hint = rq->wstar;
+    o.timeout_cycles = s->opt.timeout_cycles;
     o.dev_alloc = chunk_alloc;
     o.dev_free = chunk_free;
     o.alloc_ctx = s;
@@ -223,7 +227,9 @@ void run_large(mdist_server *s, Request *rq) {
     out.queue_wait = std::chrono::duration<double>(rq->t_start - rq->t_submit).count();
     {
         std::lock_guard<std::mutex> lock(s->mu);
+        if (s->cancel_req.erase(rq->id)) out = Done{MDIST_ECANCELLED};
         s->done[rq->id] = std::move(out);
+        s->live.erase(rq->id);
     }
     s->admitted++;
     s->completed++;
@@ -340,9 +346,44 @@ void retire(mdist_server *s, int slot, const BatchCode &S) {
     {
         std::lock_guard<std::mutex> lock(s->mu);
         s->done[rq->id] = std::move(out);
+        s->live.erase(rq->id);
     }
     s->completed++;
     delete rq;
+}
+
+// Requests cancelled while in a slot leave it between two rounds: the device code is
+// made inactive (the next round plans nothing for it), its slot and rows are freed,
+// and its result is MDIST_ECANCELLED.
+void drop_cancelled(mdist_server *s) {
+    std::set<long long> cx;
+    {
+        std::lock_guard<std::mutex> lock(s->mu);
+        if (s->cancel_req.empty()) return;
+        cx = s->cancel_req;
+    }
+    for (int slot = 0; slot < s->slots; ++slot) {
+        Request *rq = s->occupant[(size_t)slot];
+        if (!rq || !cx.count(rq->id)) continue;
+        if (cudaMemsetAsync(&s->D.codes[slot].active, 0, sizeof(int), s->stream) != cudaSuccess) {
+            s->error = MDIST_ECUDA;
+            continue;
+        }
+        s->pool.release(rq->rows_off, rq->rows_words);
+        s->occupant[(size_t)slot] = nullptr;
+        s->free_slots.push_back(slot);
+        {
+            std::lock_guard<std::mutex> lock(s->mu);
+            s->cancel_req.erase(rq->id);
+            s->done[rq->id] = Done{MDIST_ECANCELLED};
+            s->live.erase(rq->id);
+        }
+        s->completed++;
+        delete rq;
+    }
+    std::lock_guard<std::mutex> lock(s->mu);
+    for (long long id : cx)  // finished meanwhile: nothing left to cancel
+        if (!s->live.count(id)) s->cancel_req.erase(id);
 }
 
 void serve_loop(mdist_server *s) {
@@ -416,6 +457,7 @@ void serve_loop(mdist_server *s) {
         s->rounds++;
         for (int slot = 0; slot < s->slots; ++slot)
             if (s->occupant[(size_t)slot] && !s->h_codes[(size_t)slot].active) retire(s, slot, s->h_codes[(size_t)slot]);
+        drop_cancelled(s);
         s->cv_done.notify_all();
     }
     cudaEventDestroy(e0);
@@ -427,7 +469,8 @@ void serve_loop(mdist_server *s) {
 extern "C" {
 
 int mdist_server_create(const mdist_options *opts, int max_slots, size_t rows_pool_bytes, mdist_server **out) {
-    if (!out || max_slots < 1 || max_slots > (1 << 16) || rows_pool_bytes < 4096 || (opts && opts->skip_idle_sets))
+    if (!out || max_slots < 1 || max_slots > (1 << 16) || rows_pool_bytes < 4096 ||
+        (opts && (opts->skip_idle_sets || opts->overlap_sets)))
         return MDIST_EINVAL;
     *out = nullptr;
     mdist_server *s = new (std::nothrow) mdist_server();
@@ -520,6 +563,7 @@ int mdist_server_submit(mdist_server *s, const uint64_t *G, int n, int k, int wo
     if (s->stopping) { delete rq; return MDIST_ECANCELLED; }
     rq->id = s->next_id++;
     *request_id = rq->id;
+    s->live.insert(rq->id);
     if (rq->large) s->large_queue.push_back(rq);
     else s->queue.push_back(rq);
     s->cv_work.notify_one();
@@ -553,6 +597,27 @@ int mdist_server_poll(mdist_server *s, long long request_id, int wait_ms, int *d
         if (wait_ms <= 0 || Clock::now() >= deadline) return MDIST_EAGAIN;
         s->cv_done.wait_until(lock, deadline);
     }
+}
+
+int mdist_server_cancel(mdist_server *s, long long request_id) {
+    if (!s) return MDIST_EINVAL;
+    std::lock_guard<std::mutex> lock(s->mu);
+    for (std::deque<Request *> *q : {&s->queue, &s->large_queue})
+        for (auto it = q->begin(); it != q->end(); ++it)
+            if ((*it)->id == request_id) {
+                delete *it;
+                q->erase(it);
+                s->done[request_id] = Done{MDIST_ECANCELLED};
+                s->live.erase(request_id);
+                s->cv_done.notify_all();
+                return MDIST_OK;
+            }
+    if (s->live.count(request_id)) {
+        s->cancel_req.insert(request_id);
+        s->cv_work.notify_one();
+        return MDIST_OK;
+    }
+    return s->done.count(request_id) ? MDIST_EAGAIN : MDIST_EINVAL;
 }
 
 int mdist_server_info(mdist_server *s, long long *admitted, long long *completed, long long *rounds, int *queued,

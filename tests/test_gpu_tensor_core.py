@@ -35,20 +35,51 @@ CASES = [(30, 12, 1), (48, 24, 2), (100, 40, 3), (150, 40, 4), (170, 41, 5), (19
 @pytest.mark.parametrize("mode", [2, 3])
 @pytest.mark.parametrize("n,k,seed", CASES)
 def test_unit_keys_all_blocks_on_tensor_cores(api, mode, n, k, seed):
+    """Per unit, at four thresholds.  At U = n every pair is a candidate; at U = min
+    (the tie) the threshold never moves during the launch, so the pairs the MMA filter
+    passes to the exact recheck are exactly the codewords of weight min in the blocks it
+    covers: with every block on the tensor cores their count must equal the oracle's
+    histogram there, which a wrong accumulator (too low: pairs missed; too high: extra
+    pairs) cannot match.  At U = min + 2 the key must still be the oracle's and the pass
+    count lies between the weight-min and weight-<=min+2 counts; at U = min - 1 nothing
+    passes the recheck."""
     G = synth.random_systematic(n, k, seed)
     part = oracle.partition(G, n)
+    checked_tie = 0
     with api.Code(G, n, tensor_cores=mode) as c:
         for j in range(part["m"]):
             for g in range(1, k + 1):
-                if math.comb(k, g) > 3_000_000:
+                C = math.comb(k, g)
+                if C > 3_000_000:
                     break
+                want = oracle.enumerate_unit(part["gammas"][j], n, g, want_hist=True)
+                hist = [int(x) for x in want["hist"]]
+                mw = want["min_w"]
                 U, key, combos = c.enumerate_level(g, j, U=n)
-                want = oracle.enumerate_unit(part["gammas"][j], n, g, want_hist=False)
-                assert combos == [math.comb(k, g)]
-                assert key == (want["min_w"], g, j, want["min_rank"]), (g, j)
+                assert combos == [C]
+                assert key == (mw, g, j, want["min_rank"]), (g, j)
+                # the tie: exactly the weight-min codewords pass the filter
+                U1, key1, _ = c.enumerate_level(g, j, U=mw)
+                assert key1 == (mw, g, j, want["min_rank"]) and U1 == mw, (g, j)
+                cnt = c.level_counters()
+                if cnt["tc_combos"] == C:
+                    assert cnt["tc_candidates"] == hist[mw], (g, j, cnt, hist[mw])
+                    checked_tie += 1
+                else:
+                    assert cnt["tc_candidates"] <= hist[mw], (g, j, cnt)
+                # two above the least weight: same key, pass count bounded by the histogram
+                U3, key3, _ = c.enumerate_level(g, j, U=mw + 2)
+                assert key3 == (mw, g, j, want["min_rank"]) and U3 == mw, (g, j)
+                cnt = c.level_counters()
+                if cnt["tc_combos"] == C:
+                    assert hist[mw] <= cnt["tc_candidates"] <= sum(hist[mw:mw + 3]), (g, j, cnt)
+                if C >= 4096:
+                    assert cnt["tc_candidates"] * 16 < C, (g, j, cnt)  # the filter, not the recheck, decides
                 # a threshold just below the least weight: no candidate at all
-                U2, key2, _ = c.enumerate_level(g, j, U=want["min_w"] - 1)
-                assert key2 is None and U2 == want["min_w"] - 1
+                U2, key2, _ = c.enumerate_level(g, j, U=mw - 1)
+                assert key2 is None and U2 == mw - 1
+    if mode == 2:
+        assert checked_tie > 0
 
 
 @pytest.mark.parametrize("mode", [0, 2, 3])

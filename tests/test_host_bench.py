@@ -81,3 +81,21 @@ def test_clock_sampler_without_nvidia_smi(tmp_path, monkeypatch):
     s = bench.ClockSampler(None)
     s.start()
     assert s.stop() is None
+
+
+def test_reference_arm_loads_nothing_of_the_package():
+    """The oracle arm computes with the oracle only: after a whole run the process has
+    not mapped the package's library."""
+    code = ("import runpy, sys\n"
+            "sys.argv = ['bench.py', '--impl', 'reference', '--steps', '1', '--warmup', '0', '--ref-levels', '3']\n"
+            "try:\n"
+            "    runpy.run_path('bench.py', run_name='__main__')\n"
+            "except SystemExit as e:\n"
+            "    assert not e.code, e.code\n"
+            "maps = open('/proc/self/maps').read()\n"
+            "print('MAPPED' if 'libmdist' in maps else 'CLEAN')\n"
+            "print('ORACLE' if 'liboracle' in maps else 'NO-ORACLE')\n")
+    r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    out = r.stdout.split()
+    assert "CLEAN" in out and "ORACLE" in out, r.stdout[-500:]

@@ -103,6 +103,27 @@ def test_partition_matches_oracle_random(lib, seed):
     assert np.array_equal(gam, o["gammas"]) and np.array_equal(tr, o["transforms"])
 
 
+@pytest.mark.parametrize("seed", range(30))
+def test_overlap_partition_and_bound_match_oracle(lib, seed):
+    # the library's overlapping sets (mdist_options.overlap_sets) against the oracle's,
+    # set for set, and its lower bound at random per-set levels
+    from paper_1603_06757_gb300 import api
+
+    rng = synth.SplitMix64(800 + seed)
+    k = rng.uniform_int(2, 40)
+    n = rng.uniform_int(k + 1, min(512, 3 * k))
+    M = rng.uniform_int(1, 6)
+    G = _random_full_rank(n, k, seed) if seed % 2 else synth.random_systematic(n, k, seed)
+    got = api.partition_overlap_host(G, n, M)
+    want = oracle.partition_overlap(G, n, M)
+    for key in ("ranks", "pivcols", "gammas", "transforms", "cover"):
+        assert np.array_equal(got[key], want[key]), key
+    for _ in range(5):
+        levels = [rng.uniform_int(0, k - 1) for _ in range(M)]
+        assert api.overlap_bound_host(G, n, M, levels) == oracle.overlap_bound(levels, k, want["ranks"],
+                                                                                 want["cover"])
+
+
 def test_partition_rank_deficient(lib):
     bits = np.zeros((3, 10), dtype=np.uint8)
     bits[0, :5] = 1
