@@ -235,9 +235,15 @@ int mdist_device_info(int *sm_count, int *max_sm_clock_khz, int *cc_major, int *
 /* Many codes of different n, k through Alg. 1 together on one GPU.  Per round every
  * active code enumerates its next level (all its units); the rounds run as one CUDA
  * graph (persistent enumerator grids per row width, per-code state machines on the
- * device), relaunched only while codes remain active.  Each code's result equals
+ * device), relaunched only while codes remain active.  Large codes — at least 10^9
+ * codewords up to the predicted termination level (the code's hint, else the
+ * Gilbert-Varshamov estimate) — run instead after the graph, one after the other, on
+ * the single-code path with the tensor-core enumerator (opts->tensor_cores: 0 as
+ * described, 1 never, 2 every code); their device memory comes from the caller's
+ * allocator, else from chunks kept for reuse during the run.  Each code's result equals
  * mdist_min_distance's for that code (same d, key, message, witness, counters).
- * Options as for mdist_prepare (check_per_matrix, max_sets, blocks_per_sm, allocator). */
+ * Options as for mdist_prepare (check_per_matrix, max_sets, blocks_per_sm, allocator,
+ * timeout_cycles). */
 typedef struct mdist_batch mdist_batch;
 
 int mdist_batch_create(const mdist_options *opts, void *cuda_stream, mdist_batch **out);
@@ -258,9 +264,10 @@ int mdist_batch_result(const mdist_batch *b, int index, int *d, uint64_t *witnes
                        mdist_key *key, mdist_stats *stats);
 
 /* Run totals: codes, graph launches, rounds, summed CUDA-event time of the graph
- * launches (ms) and host wall time of mdist_batch_run (s). */
+ * launches (ms), host wall time of mdist_batch_run (s), codes run on the single-code
+ * path and the summed kernel time of those runs (ms).  Any output may be NULL. */
 int mdist_batch_info(const mdist_batch *b, int *ncodes, int *graph_launches, int *rounds, double *gpu_ms,
-                     double *seconds);
+                     double *seconds, int *large_codes, double *large_ms);
 
 void mdist_batch_free(mdist_batch *b);
 

@@ -126,7 +126,7 @@ SIGNATURES = {
     "mdist_batch_result": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, PI, P64, P64, ctypes.POINTER(Key),
                                           ctypes.POINTER(Stats)]),
     "mdist_batch_info": (ctypes.c_int, [ctypes.c_void_p, PI, PI, PI, ctypes.POINTER(ctypes.c_double),
-                                        ctypes.POINTER(ctypes.c_double)]),
+                                        ctypes.POINTER(ctypes.c_double), PI, ctypes.POINTER(ctypes.c_double)]),
     "mdist_batch_free": (None, [ctypes.c_void_p]),
     "mdist_server_create": (ctypes.c_int, [ctypes.POINTER(Options), ctypes.c_int, ctypes.c_size_t,
                                            ctypes.POINTER(ctypes.c_void_p)]),

@@ -408,7 +408,9 @@ class Batch:
     """Many codes through Alg. 1 together (mdist_batch_*): one graph of rounds."""
 
     def __init__(self, *, check_per_matrix: bool = False, max_sets: int = 0, blocks_per_sm: int = 0, stream=None,
-                 torch_alloc: bool = True):
+                 torch_alloc: bool = True, tensor_cores: int = 0):
+        """tensor_cores: 0 = codes estimated at >= 10^9 codewords on the single-code
+        tensor-core path, 1 = every code in the graph, 2 = every code on that path."""
         torch = _torch()
         self._lib = L.lib()
         self._stream = stream if stream is not None else torch.cuda.current_stream()
@@ -417,6 +419,7 @@ class Batch:
         opts.check_per_matrix = 1 if check_per_matrix else 0
         opts.max_sets = int(max_sets)
         opts.blocks_per_sm = int(blocks_per_sm)
+        opts.tensor_cores = int(tensor_cores)
         if self._alloc is not None:
             opts.dev_alloc = self._alloc.alloc_cb
             opts.dev_free = self._alloc.free_cb
@@ -440,12 +443,13 @@ class Batch:
         L.check(self._lib.mdist_batch_run(self._h, int(rounds_per_graph)), "mdist_batch_run")
 
     def info(self) -> dict:
-        nc, gl, rd = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
-        ms, sec = ctypes.c_double(), ctypes.c_double()
+        nc, gl, rd, nl = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        ms, sec, lms = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
         L.check(self._lib.mdist_batch_info(self._h, ctypes.byref(nc), ctypes.byref(gl), ctypes.byref(rd),
-                                           ctypes.byref(ms), ctypes.byref(sec)), "mdist_batch_info")
+                                           ctypes.byref(ms), ctypes.byref(sec), ctypes.byref(nl),
+                                           ctypes.byref(lms)), "mdist_batch_info")
         return {"codes": nc.value, "graph_launches": gl.value, "rounds": rd.value, "gpu_ms": ms.value,
-                "seconds": sec.value}
+                "seconds": sec.value, "large_codes": nl.value, "large_ms": lms.value}
 
     def result(self, index: int) -> dict:
         n, k, W = self._shapes[index]

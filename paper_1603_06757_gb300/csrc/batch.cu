@@ -12,6 +12,7 @@
 #include <vector>
 
 #include "batch_kernels.cuh"
+#include "chunk_cache.h"
 #include "prep.h"
 
 namespace mdist {
@@ -347,9 +348,21 @@ namespace {
 
 struct HostCode {
     int n = 0, k = 0, W = 0, wstar = 0;
+    bool large = false;          // run on the single-code path (tensor-core enumerator)
+    int slot = -1;               // index among the batched codes, or among the large ones
     std::vector<uint64_t> G;
     Partition part;
     std::vector<DeviceRows> rows;
+};
+
+// Result of a code run on the single-code path.
+struct LargeResult {
+    int status = MDIST_EAGAIN;
+    int d = 0;
+    uint64_t message = 0;
+    mdist_key key{};
+    std::vector<uint64_t> witness;
+    mdist_stats stats{};
 };
 
 unsigned long long host_unrank_lex(int k, int g, unsigned long long rank) {
@@ -372,9 +385,12 @@ struct mdist_batch {
     int device = 0, sm_count = 0;
     std::vector<HostCode> codes;
     std::vector<void *> allocs;
-    std::vector<BatchCode> res;              // per code, after the run
-    std::vector<unsigned long long> counts;  // all codes
+    std::vector<BatchCode> res;              // per batched code, after the run
+    std::vector<unsigned long long> counts;  // all batched codes
     std::vector<unsigned long long> counts_off;
+    std::vector<LargeResult> large_res;      // per large code
+    int n_large = 0;
+    double large_ms = 0;                     // summed kernel time of the large codes' runs
     bool ran = false;
     int rounds_per_graph = 0, graph_launches = 0, rounds = 0;
     double seconds = 0, gpu_ms = 0;
@@ -399,12 +415,17 @@ void bfree_all(mdist_batch *b) {
     b->allocs.clear();
 }
 
+int batch_run_graph(mdist_batch *b, const std::vector<int> &light, int rounds_per_graph);
+int batch_run_large(mdist_batch *b);
+
 }  // namespace
 
 extern "C" {
 
 int mdist_batch_create(const mdist_options *opts, void *cuda_stream, mdist_batch **out) {
-    if (!out || (opts && (opts->skip_idle_sets || opts->overlap_sets))) return MDIST_EINVAL;
+    if (!out || (opts && (opts->skip_idle_sets || opts->overlap_sets || opts->tensor_cores < 0 ||
+                          opts->tensor_cores > 3)))
+        return MDIST_EINVAL;
     *out = nullptr;
     mdist_batch *b = new (std::nothrow) mdist_batch();
     if (!b) return MDIST_ENOMEM;
@@ -437,6 +458,8 @@ int mdist_batch_add(mdist_batch *b, const uint64_t *G, int n, int k, int words_p
     if (rc != MDIST_OK) return rc;
     hc.rows.resize(hc.part.sets.size());
     for (size_t j = 0; j < hc.part.sets.size(); ++j) build_rows(hc.part, (int)j, hc.rows[j]);
+    const int tc = b->opt.tensor_cores;
+    hc.large = tc == 2 || (tc == 0 && estimated_work(n, k, hc.part, hc.wstar) >= kTensorPathWork);
     if (index) *index = (int)b->codes.size();
     b->codes.push_back(std::move(hc));
     return MDIST_OK;
@@ -445,8 +468,73 @@ int mdist_batch_add(mdist_batch *b, const uint64_t *G, int n, int k, int words_p
 int mdist_batch_run(mdist_batch *b, int rounds_per_graph) {
     if (!b || b->ran) return MDIST_EINVAL;
     const auto t0 = std::chrono::steady_clock::now();
-    const int C = (int)b->codes.size();
     b->ran = true;
+    std::vector<int> light;  // the codes of the graph; the others run on the single-code path
+    for (int c = 0; c < (int)b->codes.size(); ++c) {
+        HostCode &h = b->codes[(size_t)c];
+        if (h.large) {
+            h.slot = b->n_large++;
+        } else {
+            h.slot = (int)light.size();
+            light.push_back(c);
+        }
+    }
+    b->large_res.assign((size_t)b->n_large, LargeResult{});
+    int rc = batch_run_graph(b, light, rounds_per_graph);
+    if (rc == MDIST_OK) rc = batch_run_large(b);
+    b->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    return rc;
+}
+
+}  // extern "C"
+
+namespace {
+
+// The large codes one after the other through the single-code path (mdist_prepare +
+// mdist_min_distance, tensor-core enumerator on), on the batch's stream, their device
+// memory from the caller's allocator or else from chunks kept for reuse.
+int batch_run_large(mdist_batch *b) {
+    if (b->n_large == 0) return MDIST_OK;
+    ChunkCache cache;
+    mdist_options o{};
+    o.check_per_matrix = b->opt.check_per_matrix;
+    o.max_sets = b->opt.max_sets;
+    o.blocks_per_sm = b->opt.blocks_per_sm;
+    o.timeout_cycles = b->opt.timeout_cycles;
+    if (b->opt.dev_alloc) {
+        o.dev_alloc = b->opt.dev_alloc;
+        o.dev_free = b->opt.dev_free;
+        o.alloc_ctx = b->opt.alloc_ctx;
+    } else {
+        o.dev_alloc = ChunkCache::alloc;
+        o.dev_free = ChunkCache::release;
+        o.alloc_ctx = &cache;
+    }
+    int rc = MDIST_OK;
+    for (const HostCode &h : b->codes) {
+        if (!h.large) continue;
+        LargeResult &r = b->large_res[(size_t)h.slot];
+        o.wstar_hint = h.wstar;
+        mdist_code *code = nullptr;
+        r.status = mdist_prepare(h.G.data(), h.n, h.k, h.W, &o, b->stream, &code);
+        if (r.status == MDIST_OK) {
+            r.witness.assign((size_t)h.W, 0);
+            r.status = mdist_min_distance(code, &r.d, r.witness.data(), &r.message, &r.key, &r.stats);
+            b->large_ms += r.stats.kernel_ms;
+        }
+        if (code) mdist_free(code);
+        if (r.status == MDIST_ECUDA) {  // the device is in trouble: stop here
+            rc = MDIST_ECUDA;
+            break;
+        }
+    }
+    cache.clear();
+    return rc;
+}
+
+// The batched codes `light` through the rounds of one captured graph.
+int batch_run_graph(mdist_batch *b, const std::vector<int> &light, int rounds_per_graph) {
+    const int C = (int)light.size();
     if (C == 0) return MDIST_OK;
     // ---- host tables ----
     std::vector<BatchUnit> units;
@@ -460,7 +548,7 @@ int mdist_batch_run(mdist_batch *b, int rounds_per_graph) {
     bool present[kBatchBuckets] = {};
     int max_spec = 1;
     for (int c = 0; c < C; ++c) {
-        const HostCode &h = b->codes[(size_t)c];
+        const HostCode &h = b->codes[(size_t)light[(size_t)c]];
         BatchCode &S = codes[(size_t)c];
         std::memset(&S, 0, sizeof S);
         S.n = h.n;
@@ -632,13 +720,22 @@ int mdist_batch_run(mdist_batch *b, int rounds_per_graph) {
         cudaStreamDestroy(own);
     }
     bfree_all(b);
-    b->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     return rc;
 }
 
+}  // namespace
+
+extern "C" {
+
 int mdist_batch_info(const mdist_batch *b, int *ncodes, int *graph_launches, int *rounds, double *gpu_ms,
-                     double *seconds) {
+                     double *seconds, int *large_codes, double *large_ms) {
     if (!b) return MDIST_EINVAL;
+    if (large_codes) {
+        int n = 0;
+        for (const HostCode &h : b->codes) n += h.large ? 1 : 0;
+        *large_codes = n;
+    }
+    if (large_ms) *large_ms = b->large_ms;
     if (ncodes) *ncodes = (int)b->codes.size();
     if (graph_launches) *graph_launches = b->graph_launches;
     if (rounds) *rounds = b->rounds;
@@ -650,9 +747,20 @@ int mdist_batch_info(const mdist_batch *b, int *ncodes, int *graph_launches, int
 int mdist_batch_result(const mdist_batch *b, int index, int *d, uint64_t *witness, uint64_t *message, mdist_key *key,
                        mdist_stats *stats) {
     if (!b || !d || index < 0 || index >= (int)b->codes.size()) return MDIST_EINVAL;
-    if (!b->ran || b->res.empty()) return MDIST_EAGAIN;
-    const BatchCode &S = b->res[(size_t)index];
+    if (!b->ran) return MDIST_EAGAIN;
     const HostCode &h = b->codes[(size_t)index];
+    if (h.large) {
+        const LargeResult &r = b->large_res[(size_t)h.slot];
+        if (r.status != MDIST_OK) return r.status;
+        *d = r.d;
+        if (witness) std::copy(r.witness.begin(), r.witness.end(), witness);
+        if (message) *message = r.message;
+        if (key) *key = r.key;
+        if (stats) *stats = r.stats;
+        return MDIST_OK;
+    }
+    if (b->res.empty()) return MDIST_EAGAIN;
+    const BatchCode &S = b->res[(size_t)h.slot];
     if (S.status != MDIST_OK) return S.status;
     if (S.active || !S.have_key) return MDIST_EAGAIN;
     *d = S.U;
@@ -678,7 +786,7 @@ int mdist_batch_result(const mdist_batch *b, int index, int *d, uint64_t *witnes
         stats->U_final = S.U;
         stats->launches = S.rounds;
         for (int j = 0; j < S.m && j < MDIST_MAX_SETS; ++j) stats->ranks[j] = h.part.sets[(size_t)j].rank;
-        const unsigned long long off = b->counts_off[(size_t)index];
+        const unsigned long long off = b->counts_off[(size_t)h.slot];
         for (int g = 0; g <= h.k; ++g)
             for (int j = 0; j < S.m && j < MDIST_MAX_SETS; ++j) stats->combos[g][j] = b->counts[off + (size_t)g * S.m + j];
         stats->total_combos = S.combos;

@@ -161,6 +161,20 @@ int lower_bound(const Partition &p, const int *h) {
     return Lcov > L ? Lcov : L;
 }
 
+double estimated_work(int n, int k, const Partition &p, int wstar) {
+    const int m = (int)p.sets.size();
+    int w = wstar;
+    if (w < 1) {
+        std::vector<int> ranks((size_t)m);
+        for (int j = 0; j < m; ++j) ranks[(size_t)j] = p.sets[(size_t)j].bound_rank;
+        int d_gv = 0;
+        if (m < 1 || mdist_gv_estimate(n, k, m, ranks.data(), &d_gv, &w) != MDIST_OK) w = k;
+    }
+    double work = 0;
+    for (int g = 1; g <= w && g <= k; ++g) work += (double)binom_host(k, g);
+    return work * m;
+}
+
 // Row layout read by the enumerator for set j.  For a full-rank set every codeword
 // c * Gamma_j carries exactly wt(c) = g ones on the pivot columns (identity block),
 // so only the n - k other columns are stored and `base` adds g back.  A set of rank

@@ -30,6 +30,15 @@ int partition_info_sets(const uint64_t *G, int n, int k, int W, int max_sets, Pa
 // Returns MDIST_OK or MDIST_ERANK.
 int partition_overlapping_sets(const uint64_t *G, int n, int k, int W, int msets, Partition &out);
 
+// Estimated codewords of a whole run: every set up to the predicted termination level
+// (wstar > 0), else up to the level at which the bound reaches the Gilbert-Varshamov
+// estimate of d.  Sizing and routing only.
+double estimated_work(int n, int k, const Partition &p, int wstar);
+
+// Codes whose estimated work reaches this run on the single-code path with the
+// tensor-core enumerator when the batched engine or the serving loop gets them.
+constexpr double kTensorPathWork = 1e9;
+
 // Lower bound on the weight of every codeword not yet enumerated, once set j has all of
 // its units of levels <= h[j] done (h[j] = 0: none).
 int lower_bound(const Partition &p, const int *h);

@@ -23,6 +23,7 @@
 #include <vector>
 
 #include "batch_kernels.cuh"
+#include "chunk_cache.h"
 #include "prep.h"
 
 using namespace mdist;
@@ -31,9 +32,6 @@ namespace {
 
 constexpr int kServeMaxSets = 8;   // information sets per request
 constexpr int kServeMaxSpec = 16;  // levels a request may take in its first round
-// requests whose estimated work (codewords up to the predicted termination level) is at
-// least this run one at a time on the single-code path with the tensor-core enumerator
-constexpr double kServeTensorWork = 1e9;
 
 using Clock = std::chrono::steady_clock;
 
@@ -119,9 +117,8 @@ struct mdist_server {
     std::atomic<long long> rounds{0}, completed{0}, admitted{0};
     std::atomic<int> error{MDIST_OK};
     double gpu_ms = 0;
-    // device memory of the single-code handles: chunks kept for reuse (size -> free chunks)
-    std::multimap<size_t, void *> chunk_free;
-    std::map<void *, size_t> chunk_size;
+    // device memory of the single-code handles, kept for reuse
+    ChunkCache chunks;
 };
 
 namespace {
@@ -154,52 +151,6 @@ unsigned long long unrank_lex(int k, int g, unsigned long long rank) {
     return mask;
 }
 
-// Allocator of the single-code handles the server runs: chunks rounded up to 2 MiB
-// (64 MiB and up to a power of two) are kept after use and handed out again.
-void *chunk_alloc(size_t bytes, void *ctx) {
-    mdist_server *s = static_cast<mdist_server *>(ctx);
-    size_t size = (bytes + (2u << 20) - 1) / (2u << 20) * (2u << 20);
-    if (size >= (64u << 20)) {
-        size_t p2 = 64u << 20;
-        while (p2 < size) p2 <<= 1;
-        size = p2;
-    }
-    auto it = s->chunk_free.find(size);
-    if (it != s->chunk_free.end()) {
-        void *p = it->second;
-        s->chunk_free.erase(it);
-        return p;
-    }
-    void *p = nullptr;
-    if (cudaMalloc(&p, size) != cudaSuccess) {
-        cudaGetLastError();
-        return nullptr;
-    }
-    s->chunk_size[p] = size;
-    return p;
-}
-
-void chunk_free(void *p, void *ctx) {
-    mdist_server *s = static_cast<mdist_server *>(ctx);
-    auto it = s->chunk_size.find(p);
-    if (it != s->chunk_size.end()) s->chunk_free.emplace(it->second, p);
-}
-
-// Estimated codewords of a request: every set up to the predicted termination level
-// (the hint, else the Gilbert-Varshamov estimate).
-double request_work(const Request &rq) {
-    const int m = (int)rq.part.sets.size();
-    int w = rq.wstar;
-    if (w < 1) {
-        std::vector<int> ranks((size_t)m);
-        for (int j = 0; j < m; ++j) ranks[(size_t)j] = rq.part.sets[(size_t)j].rank;
-        int d_gv = 0;
-        mdist_gv_estimate(rq.n, rq.k, m, ranks.data(), &d_gv, &w);
-    }
-    double work = 0;
-    for (int g = 1; g <= w && g <= rq.k; ++g) work += (double)binom_host(rq.k, g);
-    return work * m;
-}
 
 // A large request on the single-code path (tensor-core enumerator), on the server's
 // stream; the result goes to the done table like a retired slot's.
@@ -211,9 +162,9 @@ void run_large(mdist_server *s, Request *rq) {
     o.max_sets = s->opt.max_sets > 0 && s->opt.max_sets < kServeMaxSets ? s->opt.max_sets : kServeMaxSets;
     o.wstar_hint = rq->wstar;
     o.timeout_cycles = s->opt.timeout_cycles;
-    o.dev_alloc = chunk_alloc;
-    o.dev_free = chunk_free;
-    o.alloc_ctx = s;
+    o.dev_alloc = ChunkCache::alloc;
+    o.dev_free = ChunkCache::release;
+    o.alloc_ctx = &s->chunks;
     mdist_code *h = nullptr;
     out.status = mdist_prepare(rq->G.data(), rq->n, rq->k, rq->W, &o, s->stream, &h);
     if (out.status == MDIST_OK) {
@@ -558,7 +509,7 @@ int mdist_server_submit(mdist_server *s, const uint64_t *G, int n, int k, int wo
     }
     if (rq->rows_words > s->pool_words) { delete rq; return MDIST_ENOMEM; }
     const int tc = s->opt.tensor_cores;
-    rq->large = tc == 2 || (tc == 0 && request_work(*rq) >= kServeTensorWork);
+    rq->large = tc == 2 || (tc == 0 && estimated_work(rq->n, rq->k, rq->part, rq->wstar) >= kTensorPathWork);
     std::lock_guard<std::mutex> lock(s->mu);
     if (s->stopping) { delete rq; return MDIST_ECANCELLED; }
     rq->id = s->next_id++;
@@ -648,7 +599,7 @@ void mdist_server_free(mdist_server *s) {
     for (Request *rq : s->occupant) delete rq;
     cudaStreamSynchronize(s->stream);
     sfree_all(s);
-    for (auto &kv : s->chunk_size) cudaFree(kv.first);
+    s->chunks.clear();
     cudaStreamDestroy(s->stream);
     delete s;
 }

@@ -85,3 +85,24 @@ def test_batch_textbook_and_edges(api):
         got = [b.result(i) for i in range(len(items))]
     for (G, n), r in zip(items, got):
         _same(r, api.min_distance(G, n))
+
+
+@pytest.mark.parametrize("tc", [0, 2])
+def test_batch_routes_large_codes_to_tensor_core_path(api, tc):
+    # a mix with codes of >= 10^9 estimated codewords: those run on the single-code
+    # tensor-core path inside mdist_batch_run (tc = 0), or every code does (tc = 2);
+    # every result is the single-code run's, and the light codes' the oracle's
+    codes = _mix(24, 4, k_lo=10, k_hi=30) + [(n, k, synth.random_systematic(n, k, 900 + i))
+                                             for i, (n, k) in enumerate([(112, 48), (116, 48), (120, 48)])]
+    with api.Batch(tensor_cores=tc) as b:
+        for n, k, G in codes:
+            b.add(G, n)
+        b.run()
+        info = b.info()
+        got = [b.result(i) for i in range(len(codes))]
+    assert info["large_codes"] == (len(codes) if tc == 2 else 3)
+    assert info["large_ms"] > 0
+    for (n, k, G), r in zip(codes, got):
+        _same(r, api.min_distance(G, n))
+        if k <= 30:
+            _same(r, oracle.min_distance(G, n))
