@@ -371,6 +371,14 @@ def run_ours(args):
                "sample": f"Alg. 1 units (g, j), g <= {args.cpu_levels}, of the same code: {cw} codewords "
                          f"in {sec:.1f} s"}
 
+    ext = {}
+    if rank == 0 and world == 1 and not args.no_extensions:
+        # the other half of the metric: batched and served codes/s against plain runs
+        # (outside the timed region of `value`)
+        code.close()
+        ext["batch"] = batch_report(args)
+        ext["serve"] = serve_report(args)
+
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -386,6 +394,7 @@ def run_ours(args):
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": launches,
             "clocks": clocks,
+            **ext,
         }
         print(json.dumps(line), flush=True)
     code.close()
@@ -426,9 +435,18 @@ def run_profile_unit(args):
 # batched codes and the predictor (config: 4096 random codes, k in [24, 56], n in [2k, 3k])
 # ----------------------------------------------------------------------------------
 
-def batch_codes(count, seed, seed_base, cap, k_lo=24, k_hi=56, nmul_hi=3):
-    """Codes of the batched workload whose Gilbert-Varshamov work estimate is <= cap:
-    list of (n, k, G, ranks)."""
+def gv_work(n, k, ranks):
+    """Codewords up to the level at which the bound reaches the Gilbert-Varshamov
+    estimate of d (the library's routing estimate without a hint)."""
+    from paper_1603_06757_gb300 import predict
+
+    _, w = predict.gv_estimate(n, k, ranks)
+    return sum(len(ranks) * math.comb(k, g) for g in range(1, w + 1))
+
+
+def batch_codes(count, seed, seed_base, cap=None, k_lo=24, k_hi=56, nmul_hi=3):
+    """Codes of the batched workload (all of them, or those whose Gilbert-Varshamov work
+    estimate is <= cap): list of (n, k, G, ranks)."""
     import synth
     from paper_1603_06757_gb300 import api, predict
 
@@ -436,9 +454,7 @@ def batch_codes(count, seed, seed_base, cap, k_lo=24, k_hi=56, nmul_hi=3):
     for s in synth.batch_specs(count, k_lo, k_hi, 2, nmul_hi, seed=seed, seed_base=seed_base):
         G = synth.random_systematic(s.n, s.k, s.seed)
         ranks = [int(r) for r in api.partition_host(G, s.n)["ranks"]]
-        _, w = predict.gv_estimate(s.n, s.k, ranks)
-        work = sum(len(ranks) * math.comb(s.k, g) for g in range(1, w + 1))
-        if work <= cap:
+        if cap is None or gv_work(s.n, s.k, ranks) <= cap:
             out.append((s.n, s.k, G, ranks))
     return out
 
@@ -459,15 +475,16 @@ def run_plain(codes, hints=None):
     return len(codes) / (time.perf_counter() - t0), res
 
 
-def run_batched(codes, hints=None, blocks_per_sm=0, rounds_per_graph=0):
-    """All codes in one batched run (rounds captured in one CUDA graph)."""
+def run_batched(codes, hints=None, blocks_per_sm=0, rounds_per_graph=0, tensor_cores=0):
+    """All codes in one batched run (rounds captured in one CUDA graph; large codes on
+    the single-code tensor-core path unless tensor_cores=1)."""
     import torch
 
     from paper_1603_06757_gb300 import api
 
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    with api.Batch(blocks_per_sm=blocks_per_sm) as b:
+    with api.Batch(blocks_per_sm=blocks_per_sm, tensor_cores=tensor_cores) as b:
         for i, (n, k, G, _) in enumerate(codes):
             b.add(G, n, wstar_hint=hints[i] if hints else 0)
         b.run(rounds_per_graph)
@@ -499,6 +516,75 @@ def predictor_report(mlp, test_codes, test_res):
     return p_mlp, p_gv, {"mlp": predict.errors(p_mlp, truth), "gv": predict.errors(p_gv, truth)}
 
 
+def _same_results(a_list, b_list):
+    return all(a["d"] == b["d"] and a["key"] == b["key"] and a["message"] == b["message"] and
+               np.array_equal(a["counts"], b["counts"]) for a, b in zip(a_list, b_list))
+
+
+def batch_report(args, full=False):
+    """Batched vs plain codes/s on the 4096-code workload (every code: the light ones in
+    the batched graph, the large ones on the single-code tensor-core path), with the
+    predictor's hints (MLP, Gilbert-Varshamov, none) deciding the first round's levels and
+    the routing.  full: also the launch-shape autotuner and hinted plain runs."""
+    from paper_1603_06757_gb300 import predict
+
+    codes = batch_codes(args.batch_codes, 2024, 1000)
+    train = batch_codes(args.batch_train, 77, 500000, cap=args.batch_cap)
+    t0 = time.perf_counter()
+    mlp, curve = train_predictor(train)
+    train_s = time.perf_counter() - t0
+    shapes = [(n, k, ranks) for (n, k, G, ranks) in codes]
+    feats = np.stack([predict.features(G, n) for (n, k, G, _) in codes])
+    p_mlp = predict.Predictor(mlp).predict(feats, shapes)
+    p_gv = predict.Predictor(None).predict(feats, shapes)
+    hints = {"mlp": [w for (w, d) in p_mlp], "gv": [w for (w, d) in p_gv], "none": None}
+    run_batched(codes[:64])  # warm-up of both paths
+    run_plain(codes[:16])
+    cps, res, info = {}, {}, {}
+    for name, h in hints.items():
+        cps[name], res[name], info[name] = run_batched(codes, h)
+    cps_plain, res_plain = run_plain(codes)
+    same = all(_same_results(res[name], res_plain) for name in hints)
+    truth = [(r["g_final"], r["d"]) for r in res_plain]
+    errs = {"mlp": predict.errors(p_mlp, truth), "gv": predict.errors(p_gv, truth)}
+    # the light codes alone (those the default routing keeps in the graph)
+    light = [c for c in codes if gv_work(c[0], c[1], c[3]) < 1e9]
+    cps_light_b, res_lb, _ = run_batched(light)
+    cps_light_p, res_lp = run_plain(light)
+    best = max(cps, key=cps.get)
+    out = {
+        "metric": "codes/s, batched vs plain (one code per prepare/run)", "unit": "codes/s",
+        "value": cps[best], "best": f"batched, {best} hints", "higher_is_better": True,
+        "config": {"workload": f"{len(codes)} random codes, k ~ U[24,56], n ~ U[2k,3k], R iid Bernoulli(1/2), "
+                               "seeds 1000+i (every code)",
+                   "codewords": sum(r["total_combos"] for r in res_plain),
+                   "large_codes": info["none"]["large_codes"],
+                   "train_codes": len(train)},
+        "codes_per_s": {"plain": cps_plain, **{f"batched_{k}_hints": v for k, v in cps.items()}},
+        "speedup_vs_plain": cps[best] / cps_plain,
+        "light_codes": {"codes": len(light), "batched": cps_light_b, "plain": cps_light_p,
+                        "speedup": cps_light_b / cps_light_p, "results_identical": _same_results(res_lb, res_lp)},
+        "rounds": {k: v["rounds"] for k, v in info.items()},
+        "large_codes": {k: v["large_codes"] for k, v in info.items()},
+        "gpu_ms": {k: v["gpu_ms"] + v["large_ms"] for k, v in info.items()},
+        "predictor": errs, "predictor_train_s": train_s, "train_loss_last": float(curve[-50:].mean()),
+        "results_identical": bool(same),
+    }
+    if full:
+        from paper_1603_06757_gb300 import tune
+
+        tuned = tune.autotune_batch([(G, n, hh) for (n, k, G, _), hh in zip(light, [0] * len(light))],
+                                    sample=args.tune_sample)
+        shape = {"blocks_per_sm": tuned["blocks_per_sm"], "rounds_per_graph": tuned["rounds_per_graph"]}
+        out["autotune"] = {"chosen": shape, "sample": tuned["sample"], "seconds_best": tuned["seconds_best"],
+                           "seconds_worst": tuned["seconds_worst"], "candidates": len(tuned["table"]),
+                           "codes_per_s_tuned": run_batched(codes, hints[best], **shape)[0]}
+        out["codes_per_s"]["plain_mlp_hints"] = run_plain(codes, hints["mlp"])[0]
+        out["codes_per_s"]["plain_gv_hints"] = run_plain(codes, hints["gv"])[0]
+        out["codes_per_s"]["batched_no_routing"] = run_batched(codes, hints[best], tensor_cores=1)[0]
+    return out
+
+
 def run_batch_bench(args):
     import torch
 
@@ -506,48 +592,8 @@ def run_batch_bench(args):
 
     __graft_entry__.build()
     torch.cuda.set_device(0)
-    cap = args.batch_cap
-    test = batch_codes(args.batch_codes, 2024, 1000, cap)
-    train = batch_codes(args.batch_train, 77, 500000, cap)
-    mlp, curve = train_predictor(train)
-    # warm-up of every path
-    run_batched(test[:64])
-    run_plain(test[:16])
-    cps_batch_untuned, res_b, info_b = run_batched(test)
-    p_mlp, p_gv, errs = predictor_report(mlp, test, res_b)
-    h_mlp = [w for (w, d) in p_mlp]
-    h_gv = [w for (w, d) in p_gv]
-    # launch shapes of the batched engine, tuned on a seeded sample (not timed)
-    from paper_1603_06757_gb300 import tune
-
-    tuned = tune.autotune_batch([(G, n, h) for (n, k, G, _), h in zip(test, h_mlp)], sample=args.tune_sample)
-    shape = {"blocks_per_sm": tuned["blocks_per_sm"], "rounds_per_graph": tuned["rounds_per_graph"]}
-    cps_batch, res_bt, info_bt = run_batched(test, None, **shape)
-    cps_batch_mlp, res_bm, info_bm = run_batched(test, h_mlp, **shape)
-    cps_batch_gv, _, info_bg = run_batched(test, h_gv, **shape)
-    cps_plain, res_p = run_plain(test)
-    cps_plain_mlp, _ = run_plain(test, h_mlp)
-    cps_plain_gv, _ = run_plain(test, h_gv)
-    same = all(a["d"] == b["d"] and a["key"] == b["key"] and np.array_equal(a["counts"], b["counts"])
-               for a, b in zip(res_b, res_p)) and all(a["key"] == b["key"] for a, b in zip(res_b, res_bm)) and \
-        all(a["key"] == b["key"] and np.array_equal(a["counts"], b["counts"]) for a, b in zip(res_b, res_bt))
-    cw = sum(r["total_combos"] for r in res_b)
-    line = {
-        "metric": "codes/s, batched vs plain (one code per prepare/run)", "unit": "codes/s",
-        "value": cps_batch_mlp, "higher_is_better": True, "n_gpus": 1, "data": "synthetic",
-        "config": {"workload": f"{args.batch_codes} random codes, k ~ U[24,56], n ~ U[2k,3k], seeds 1000+i; "
-                               f"kept: GV work estimate <= {cap:.0e} codewords",
-                   "codes": len(test), "codewords": cw, "train_codes": len(train)},
-        "codes_per_s": {"plain": cps_plain, "plain_gv_hint": cps_plain_gv, "plain_mlp_hint": cps_plain_mlp,
-                        "batched_untuned": cps_batch_untuned, "batched": cps_batch, "batched_gv_hint": cps_batch_gv,
-                        "batched_mlp_hint": cps_batch_mlp},
-        "rounds": {"batched": info_bt["rounds"], "batched_mlp_hint": info_bm["rounds"],
-                   "batched_gv_hint": info_bg["rounds"]},
-        "autotune": {"chosen": shape, "sample": tuned["sample"], "seconds_best": tuned["seconds_best"],
-                     "seconds_worst": tuned["seconds_worst"], "candidates": len(tuned["table"])},
-        "predictor": errs, "train_loss_last": float(curve[-50:].mean()),
-        "results_identical": bool(same),
-    }
+    line = batch_report(args, full=True)
+    line.update({"n_gpus": 1, "data": "synthetic"})
     print(json.dumps(line), flush=True)
     return 0
 
@@ -574,17 +620,13 @@ def serve_requests(count, seed, cap):
     return out, rejected
 
 
-def run_serve_bench(args):
+def serve_report(args):
+    """Served capacity vs plain per-code launches on the same seeded sample of the request
+    stream, then the latency of the whole Poisson stream at a fraction of that capacity."""
     import threading as th
 
-    import torch
-
-    import __graft_entry__
     import synth
-
-    __graft_entry__.build()
-    torch.cuda.set_device(0)
-    from paper_1603_06757_gb300 import api, predict
+    from paper_1603_06757_gb300 import api, predict, tune
 
     reqs, rejected = serve_requests(args.serve_requests, 4242, args.serve_cap)
     train = batch_codes(args.batch_train, 77, 500000, args.batch_cap, k_lo=20, k_hi=64, nmul_hi=4)
@@ -597,24 +639,24 @@ def run_serve_bench(args):
         hints = [w for (w, d) in predict.Predictor(None).predict(feats, shapes)]
     else:
         hints = [0] * len(reqs)
-    # capacity of the batched engine alone: the whole stream as one batch
-    cps_batch, _, _ = run_batched([(n, k, G, r) for (n, k, G, r) in reqs], hints)
-    # capacity of the server (batched rounds + large requests on the tensor-core path):
-    # a seeded sample submitted at once
-    from paper_1603_06757_gb300 import tune
-
-    cap_idx = tune.sample_indices(len(reqs), min(len(reqs), args.serve_capacity_sample), 5)
+    idx = tune.sample_indices(len(reqs), min(len(reqs), args.serve_capacity_sample), 5)
+    sample = [reqs[i] for i in idx]
+    run_plain(sample[:16])  # warm-up
+    cps_plain, res_plain = run_plain(sample)
     with api.Server(max_slots=args.serve_slots, rows_pool_bytes=64 << 20) as srv:
         t0 = time.perf_counter()
-        cap_ids = [srv.submit(reqs[i][2], reqs[i][0], wstar_hint=hints[i]) for i in cap_idx]
-        pending = set(cap_ids)
-        while pending:
-            for rid in list(pending):
-                if srv.poll(rid, wait_ms=0) is not None:
-                    pending.discard(rid)
+        ids = [srv.submit(reqs[i][2], reqs[i][0], wstar_hint=hints[i]) for i in idx]
+        got = {}
+        while len(got) < len(ids):
+            for rid in ids:
+                if rid not in got:
+                    r = srv.poll(rid, wait_ms=0)
+                    if r is not None:
+                        got[rid] = r
             time.sleep(0.001)
-        cps_served_cap = len(cap_ids) / (time.perf_counter() - t0)
-    rate = args.serve_rate if args.serve_rate > 0 else args.serve_load * cps_served_cap
+        cps_served = len(ids) / (time.perf_counter() - t0)
+    same = _same_results([got[rid] for rid in ids], res_plain)
+    rate = args.serve_rate if args.serve_rate > 0 else args.serve_load * cps_served
     arrivals = synth.poisson_arrivals(len(reqs), rate, seed=99)
     with api.Server(max_slots=args.serve_slots, rows_pool_bytes=64 << 20) as srv:
         ids = [None] * len(reqs)
@@ -641,23 +683,33 @@ def run_serve_bench(args):
         wall = time.perf_counter() - t0
         info = srv.info()
     lats = np.array([lat[i] for i in range(len(reqs))])
-    sample = reqs[: min(len(reqs), args.serve_plain_sample)]
-    cps_plain, _ = run_plain(sample)
-    line = {
+    return {
         "metric": "served codes/s and latency vs plain per-code launches", "unit": "codes/s",
-        "value": cps_served_cap, "higher_is_better": True, "n_gpus": 1, "data": "synthetic",
-        "config": {"workload": f"Poisson stream of {len(reqs)} requests, k ~ U[20,64], n ~ U[2k,4k]; draws with "
-                               f"GV work estimate > {args.serve_cap:.0e} redrawn ({rejected} redrawn)",
-                   "arrival_rate_per_s": rate, "load": f"{args.serve_load} x served capacity",
-                   "slots": args.serve_slots,
+        "value": cps_served, "higher_is_better": True,
+        "config": {"workload": f"Poisson stream of {len(reqs)} requests, k ~ U[20,64], n ~ U[2k,4k], R iid "
+                               f"Bernoulli(1/2); draws with GV work estimate > {args.serve_cap:.0e} codewords "
+                               f"redrawn ({rejected} redrawn)",
+                   "capacity_sample": len(idx), "arrival_rate_per_s": rate,
+                   "load": f"{args.serve_load} x served capacity", "slots": args.serve_slots,
                    "hints": args.serve_hints},
+        "codes_per_s": {"served": cps_served, "plain": cps_plain, "served_at_load": len(reqs) / wall},
+        "speedup_vs_plain": cps_served / cps_plain,
         "latency_s": {"p50": float(np.percentile(lats, 50)), "p99": float(np.percentile(lats, 99)),
                       "mean": float(lats.mean()), "max": float(lats.max())},
-        "codes_per_s": {"served_capacity": cps_served_cap, "capacity_sample": len(cap_idx),
-                        "served_at_load": len(reqs) / wall, "batched_capacity": cps_batch,
-                        "plain": cps_plain, "plain_sample": len(sample)},
         "rounds": info["rounds"], "gpu_ms": info["gpu_ms"],
+        "results_identical": bool(same),
     }
+
+
+def run_serve_bench(args):
+    import torch
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    torch.cuda.set_device(0)
+    line = serve_report(args)
+    line.update({"n_gpus": 1, "data": "synthetic"})
     print(json.dumps(line), flush=True)
     return 0
 
@@ -672,6 +724,8 @@ def main():
     ap.add_argument("--cpu-levels", type=int, default=8)
     ap.add_argument("--ref-levels", type=int, default=7)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extensions", action="store_true",
+                    help="leave out the batched and served measurements of the default line")
     ap.add_argument("--mode", choices=["single", "batch", "serve"], default="single")
     ap.add_argument("--batch-codes", type=int, default=4096)
     ap.add_argument("--batch-train", type=int, default=1500)

@@ -88,7 +88,7 @@ typedef struct {
                                 levels 1 .. wstar_hint-1 as one wave (one host
                                 synchronisation).  Sizing only: results never depend on it. */
     int tensor_cores;        /* product blocks on the tensor cores (tcgen05 Gram-matrix
-                                enumerator, stored rows of at most 7 words): 0 = blocks
+                                enumerator, stored rows of at most 8 words): 0 = blocks
                                 whose two sides hold >= 128 subsets each, and blocks of
                                 >= 2^24 codewords with a smaller side split into parts
                                 whose sides are large (the large side's half cut in two

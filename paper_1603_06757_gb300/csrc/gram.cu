@@ -9,7 +9,7 @@
 // dense contraction over the n_bits columns.  Operand rows are the signs as E4M3 bytes
 // (+1.0 / -1.0; the B side has zero bytes past n_bits), one kind::f8f6f4 MMA chain
 // with f32 accumulation gives every acc = n_bits - 2 wt(x ^ y) exactly (integers of
-// magnitude <= n_bits <= 224), and a codeword is a candidate iff
+// magnitude <= n_bits <= 256), and a codeword is a candidate iff
 // acc >= n_bits - 2 thr (thr = largest reduced weight still a candidate).  The
 // epilogue reads the accumulators from TMEM with loads that also return their maximum
 // (tcgen05.ld.red .max); only a maximum at or above that bound sends a lane to the
@@ -309,7 +309,7 @@ __global__ void __launch_bounds__(kGramThreads, 1) gram_kernel(const __grid_cons
         const int row = 32 * (warp & 3) + lane;  // TMEM lane = A row
         const int col0 = 128 * (warp >> 2);      // first accumulator column of this warp
         unsigned long long t = 0, q = 0, cnt = 0;  // B tiles, accumulators, codewords counted
-        unsigned long long cand = 0;               // pairs this thread re-weighed exactly
+        unsigned int cand = 0;                     // pairs this thread re-weighed exactly (< 2^32 per launch)
         unsigned int u_next = *(volatile unsigned int *)P.U;
         bool ok = true;
         // the TMEM loads below are warp-collective (.sync.aligned), so every decision to
@@ -327,7 +327,7 @@ __global__ void __launch_bounds__(kGramThreads, 1) gram_kernel(const __grid_cons
 #pragma unroll 1
                 for (int h = 0; h < MA; ++h, ++q) {
                     const int ab = (int)(q & 1);
-                    if (!__all_sync(0xffffffffu, mbar_wait(bar(ACC_FULL + ab), (uint32_t)((q >> 1) & 1), P.max_wait))) {
+                    if (!mbar_wait_warp(bar(ACC_FULL + ab), (uint32_t)((q >> 1) & 1), P.max_wait)) {
                         fail();
                         ok = false;
                         break;
@@ -399,7 +399,7 @@ __global__ void __launch_bounds__(kGramThreads, 1) gram_kernel(const __grid_cons
             }
         }
         if (tid == 0 && cnt) atomicAdd(&P.slot->count, cnt);
-        if (cand) atomicAdd(&P.slot->tc_cand, cand);  // rare except at loose thresholds
+        if (cand) atomicAdd(&P.slot->tc_cand, (unsigned long long)cand);  // rare except at loose thresholds
     }
     tc_fence_before();
     __syncthreads();
@@ -496,7 +496,10 @@ __global__ void side_tables_kernel(const uint32_t *rows, int k, const __grid_con
             // one vector store per entry where the row size allows it (the tables are
             // 256-byte aligned): a warp's stores are 256 bytes apart, so each store
             // instruction is one L2 write request per lane however wide it is
-            if constexpr (NW == 4) {
+            if constexpr (NW == 8) {
+                *reinterpret_cast<uint4 *>(out + e * 8) = make_uint4(x[0], x[1], x[2], x[3]);
+                *reinterpret_cast<uint4 *>(out + e * 8 + 4) = make_uint4(x[4], x[5], x[6], x[7]);
+            } else if constexpr (NW == 4) {
                 *reinterpret_cast<uint4 *>(out + e * 4) = make_uint4(x[0], x[1], x[2], x[3]);
             } else if constexpr (NW == 2) {
                 *reinterpret_cast<uint2 *>(out + e * 2) = make_uint2(x[0], x[1]);
@@ -583,6 +586,7 @@ cudaError_t launch_side_tables(const uint32_t *rows, int k, int nwords, const Gr
         case 5: return side_tables_nw<5>(rows, k, J, sm_count, stream);
         case 6: return side_tables_nw<6>(rows, k, J, sm_count, stream);
         case 7: return side_tables_nw<7>(rows, k, J, sm_count, stream);
+        case 8: return side_tables_nw<8>(rows, k, J, sm_count, stream);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -613,6 +617,7 @@ cudaError_t launch_expand_tables(int nwords, int n_bits, const uint32_t *const *
         case 5: return expand_tables_nw<5>(J, sm_count, stream);
         case 6: return expand_tables_nw<6>(J, sm_count, stream);
         case 7: return expand_tables_nw<7>(J, sm_count, stream);
+        case 8: return expand_tables_nw<8>(J, sm_count, stream);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -669,6 +674,7 @@ cudaError_t launch_gram_unit(const EnumParams &ep, const GramBlockSpec *blocks, 
         case 5: return gram_launch_nw<5>(p, sm_count, stream);
         case 6: return gram_launch_nw<6>(p, sm_count, stream);
         case 7: return gram_launch_nw<7>(p, sm_count, stream);
+        case 8: return gram_launch_nw<8>(p, sm_count, stream);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -81,7 +81,7 @@ cudaError_t launch_enum_unit(const EnumParams &p, int nwords, int group, bool hi
 // smaller side is split into sub-blocks over the two quarters of its large side's half
 // (gram_block_parts in api.cpp), which gives every sub-block two larger sides.
 constexpr int kGramMinSide = 128;
-constexpr int kGramMaxWords = 7;
+constexpr int kGramMaxWords = 8;
 constexpr int kMaxGramBlocks = 128;
 bool gram_eligible(int nwords);
 

@@ -89,6 +89,23 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mbar_smem, uint32_t parity, l
     return false;
 }
 
+// The same wait taken by a whole warp: every lane polls, and the warp stops on the same
+// poll (all lanes have seen the phase complete) or gives up on the same poll, so the
+// outcome is warp-uniform.
+__device__ __forceinline__ bool mbar_wait_warp(uint32_t mbar_smem, uint32_t parity, long long max_iters) {
+    for (long long i = 0; i < max_iters; ++i) {
+        uint32_t ok;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(ok)
+            : "r"(mbar_smem), "r"(parity)
+            : "memory");
+        if (__all_sync(0xffffffffu, ok)) return true;
+    }
+    return false;
+}
+
 // arrive on an mbarrier and raise its expected transaction bytes
 __device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t mbar_smem, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar_smem), "r"(bytes) : "memory");

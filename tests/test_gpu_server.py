@@ -1,12 +1,14 @@
 """Serving loop: requests admitted while others are in flight (continuous batching),
 bounded by slots and rows memory; large requests routed to the single-code tensor-core
-path between rounds; every result equals the code's run alone."""
+path between rounds; every result equals the code's run alone and, for the requests
+the oracle finishes in well under a second (k <= 36), the oracle's."""
 
 import time
 
 import numpy as np
 import pytest
 
+import oracle
 import synth
 
 pytestmark = pytest.mark.gpu
@@ -71,6 +73,7 @@ def test_results_same_alone_and_in_the_mix(api, per_matrix):
     assert info["rounds"] > 0
     for rid, (n, k, G) in zip(ids, reqs):
         _same(res[rid], api.min_distance(G, n, check_per_matrix=per_matrix, max_sets=8))
+        _same(res[rid], oracle.min_distance(G, n, check_per_matrix=per_matrix, max_sets=8))
         assert res[rid]["latency_s"] > 0
 
 
@@ -82,6 +85,7 @@ def test_admission_bounded_by_memory_and_slots(api):
         res = _drain(srv, ids)
     for rid, (n, k, G) in zip(ids, reqs):
         _same(res[rid], api.min_distance(G, n, max_sets=8))
+        _same(res[rid], oracle.min_distance(G, n, max_sets=8))
 
 
 def test_oversize_request_rejected(api):
@@ -110,3 +114,5 @@ def test_large_requests_on_the_tensor_core_path(api, tc):
     assert info["completed"] == len(reqs) and info["queued"] == 0 and info["in_flight"] == 0
     for rid, (n, k, G) in zip(ids, reqs):
         _same(res[rid], api.min_distance(G, n, max_sets=8))
+        if k <= 36:
+            _same(res[rid], oracle.min_distance(G, n, max_sets=8))

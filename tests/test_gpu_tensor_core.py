@@ -27,9 +27,9 @@ def api():
     return a
 
 
-# (n, k, seed): 1 to 7 stored words, odd and even k, partial sets
+# (n, k, seed): 1 to 8 stored words, odd and even k, partial sets
 CASES = [(30, 12, 1), (48, 24, 2), (100, 40, 3), (150, 40, 4), (170, 41, 5), (192, 64, 8), (260, 40, 6),
-         (96, 24, 5), (129, 64, 8)]
+         (96, 24, 5), (129, 64, 8), (290, 40, 7)]
 
 
 @pytest.mark.parametrize("mode", [2, 3])
@@ -83,7 +83,8 @@ def test_unit_keys_all_blocks_on_tensor_cores(api, mode, n, k, seed):
 
 
 @pytest.mark.parametrize("mode", [0, 2, 3])
-@pytest.mark.parametrize("n,k,seed", [(120, 36, 3), (150, 36, 14), (96, 24, 5), (180, 36, 13), (60, 30, 1)])
+@pytest.mark.parametrize("n,k,seed", [(120, 36, 3), (150, 36, 14), (96, 24, 5), (180, 36, 13), (60, 30, 1),
+                                      (260, 30, 9)])
 def test_min_distance_tensor_cores(api, mode, n, k, seed):
     G = synth.random_systematic(n, k, seed)
     with api.Code(G, n, tensor_cores=mode) as c:
