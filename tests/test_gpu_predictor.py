@@ -1,6 +1,9 @@
 """The learned predictor, trained by the library's own kernels on labels from the
 method's own runs, against the analytic Gilbert-Varshamov fallback on held-out codes;
-and the predictions used as hints never change a result."""
+and the predictions used as hints never change a result.  What the hints buy is
+measured by the benchmark (codes/s with MLP, GV and no hints on the 4096-code
+workload: no significant throughput gain); this test asserts the one effect that is
+deterministic, fewer batched rounds (device-host round trips)."""
 
 import numpy as np
 import pytest
