@@ -355,17 +355,6 @@ int mdist_mlp_train(mdist_mlp *mlp, const float *X, const float *T, int N, int s
                     uint64_t seed, float *loss_curve);
 void mdist_mlp_free(mdist_mlp *mlp);
 
-/* Instruction-throughput probe on the current device, for roofline arithmetic:
- * which = 0: 32-bit POPC, 1: 3-input XOR (LOP3), 2: enumerator inner step (XOR + POPC
- * over 4 words, sum, running min), 3 / 4: the lower-bound step of filter groups of 2 /
- * 4 words (threshold never reached), operands in registers; one 1024-thread CTA
- * per SM, `iters` loop trips.  which = 5 / 6 / 7: tcgen05 kind::f8f6f4 MMAs (E4M3,
- * f16 accumulator, 128 x 256 x 32) issued back to back by one thread per SM on
- * shared-memory operands in the no-swizzle / 128-byte swizzle / 32-byte swizzle
- * layout, 4 MMAs per loop trip.  *ops_per_clock_per_sm = operations (codeword steps;
- * multiply-adds for the MMA probes) retired per SM per clock (clock64), *seconds =
- * launch time.  Allocates 64 B + 8 B per SM of device memory for its duration. */
-int mdist_microbench(int which, int iters, double *ops_per_clock_per_sm, double *seconds);
 
 /* ---- one unit without any device allocation ---------------------------------------- */
 
@@ -382,7 +371,7 @@ int mdist_microbench(int which, int iters, double *ops_per_clock_per_sm, double 
  * enumerator.
  *
  * Inputs: `rows` (device) = the set's stored rows, k rows of nwords 32-bit words (the
- * layout mdist_debug_set_rows returns: for a full-rank set the n_bits = n - k
+ * layout mdist_debug_set_rows of mdist_debug.h returns: for a full-rank set the n_bits = n - k
  * non-pivot columns, full_rank = 1; otherwise all n_bits = n columns, full_rank = 0).
  * Bits at positions >= n_bits of a row (the last word's padding and any whole words
  * after it) are ignored: the kernel clears them when it stages the rows.
@@ -410,11 +399,6 @@ int mdist_microbench(int which, int iters, double *ops_per_clock_per_sm, double 
 int mdist_enumerate_unit_noalloc(const uint32_t *rows, int k, int nwords, int n_bits, int full_rank, int g, int U,
                                  int want_hist, unsigned long long *out, void *cuda_stream);
 
-/* Tensor-core check: D = A * B^T for A 128 x K and B N x K of E4M3 bytes (row-major,
- * host), K and N multiples of 32 up to 256, computed by tcgen05 kind::f8f6f4 with f32
- * accumulation in TMEM on one CTA; D 128 x N f32 (host).  Allocates its device buffers
- * for the call.  MDIST_ETIMEOUT if the MMA's completion wait ran out. */
-int mdist_tc_probe(const uint8_t *A, const uint8_t *B, int N, int K, float *D);
 
 /* ---- host-only entry points (no CUDA call; usable without a GPU) ---------------- */
 
@@ -435,49 +419,6 @@ int mdist_partition_overlap_host(const uint64_t *G, int n, int k, int words_per_
  * done (levels[msets]; 0 = none). */
 int mdist_overlap_bound_host(const uint64_t *G, int n, int k, int words_per_row, int msets, const int *levels,
                              int *L);
-
-/* Row layout the enumerator reads for set j (0-based): a full-rank set stores its
- * n - k non-pivot columns (every codeword of a weight-g combination has exactly g
- * ones on the pivots, §2's identity block); a set of rank < k stores all n columns.
- * words[k * *nwords] receives the rows as 32-bit words (capacity k * 16). */
-int mdist_debug_set_rows(const uint64_t *G, int n, int k, int words_per_row, int j, int *full_rank, int *n_bits,
-                         int *nwords, uint32_t *words);
-
-/* The combination indexing the kernels run, evaluated on the host:
- *  unrank_colex: t-subset of {0..kh-1} (kh <= 32) with colex rank `rank`, as a mask;
- *  next_colex:   the next subset of the same size in colex order;
- *  lexrank:      lexicographic rank (§3.1 order) of a g-subset of {0..k-1}. */
-int mdist_debug_unrank_colex(int kh, int t, uint32_t rank, uint32_t *mask);
-int mdist_debug_next_colex(uint32_t m, uint32_t *next);
-int mdist_debug_lexrank(uint64_t mask, int k, int g, uint64_t *rank);
-
-/* Enumerator variant the library picks for a unit (mdist_options.filter_group = 0):
- * 0 = exact count, 2..4 = OR-group size; nwords 32-bit words of n_bits stored bits,
- * thr = largest reduced weight that is still a candidate. */
-int mdist_debug_filter_choice(int nwords, int n_bits, int thr, int *group);
-
-/* Work plan of one level (k rows, level g, nwords 32-bit words per row): the product
- * blocks (i-subsets of rows [0, ceil(k/2)) times (g-i)-subsets of the rest), 7 values
- * per block in blocks[]: lane_half, lane_t, walk_t, lane_n, walk_n, walk_chunks,
- * tile_begin (capacity 34 blocks); the tile count and the tile shape.  MDIST_ERANGE
- * if C(k, g) >= 2^54. */
-int mdist_debug_level_plan(int k, int g, int nwords, int *nblocks, uint64_t *blocks, uint64_t *total_tiles,
-                           int *lane_chunk, int *walk_chunk);
-
-/* Tensor-core plan of one level (same k, g, nwords as mdist_debug_level_plan) under
- * mdist_options.tensor_cores = tensor_cores, before any table is built: the parts the
- * tensor-core enumerator takes, each a product A x B of two sides, and which product
- * blocks of the level plan they cover.  A side is the set of sums of one t0-subset of
- * rows [off0, off0 + kc0) and, when it has two components, one t1-subset of rows
- * [off1, off1 + kc1).  parts[15 * i ..]: block, then for A and for B in turn off0,
- * kc0, t0, off1, kc1, t1 (-1 for an absent second component) and the component count;
- * sizes[2 * i ..]: the entry counts of A and B; covered[b] (34 entries): 1 if block b
- * is split into parts, 0 if it stays on the ALU kernel.  Capacity 128 parts.  The
- * library swaps A and B when B is the larger side; this reports them unswapped.
- * MDIST_EINVAL on a null pointer or a mode outside 0..3, MDIST_ERANGE if
- * C(k, g) >= 2^54.  Host only, no CUDA calls. */
-int mdist_debug_gram_plan(int k, int g, int nwords, int tensor_cores, int *nparts, int *parts, uint64_t *sizes,
-                          int *covered);
 
 #ifdef __cplusplus
 }

@@ -117,8 +117,6 @@ SIGNATURES = {
     "mdist_free": (None, [PCODE]),
     "mdist_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "mdist_device_info": (ctypes.c_int, [PI, PI, PI, PI]),
-    "mdist_microbench": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
-                                        ctypes.POINTER(ctypes.c_double)]),
     "mdist_batch_create": (ctypes.c_int, [ctypes.POINTER(Options), ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]),
     "mdist_batch_add": (ctypes.c_int, [ctypes.c_void_p, P64, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                        PI]),
@@ -154,7 +152,6 @@ SIGNATURES = {
     "mdist_enumerate_unit_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                                     ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                                     ctypes.c_void_p, ctypes.c_void_p]),
-    "mdist_tc_probe": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int, PF]),
     "mdist_partition_host": (ctypes.c_int, [P64, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, PI, PI,
                                             PI32, P64, P64]),
     "mdist_partition_overlap_host": (ctypes.c_int, [P64, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, PI,
@@ -171,6 +168,32 @@ SIGNATURES = {
     "mdist_debug_gram_plan": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, PI, PI, P64,
                                              PI]),
 }
+
+
+# the measurement probes of include/mdist_probe.h, in libmdist_probe.so
+PROBE_LIB_PATH = os.path.join(HERE, "libmdist_probe.so")
+PROBE_SIGNATURES = {
+    "mdist_microbench": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                        ctypes.POINTER(ctypes.c_double)]),
+    "mdist_tc_probe": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int, PF]),
+}
+_probe = None
+
+
+def probe_lib():
+    """The loaded libmdist_probe.so (tests and the benchmark only)."""
+    global _probe
+    with _lock:
+        if _probe is None:
+            if not os.path.exists(PROBE_LIB_PATH):
+                raise ImportError(f"{PROBE_LIB_PATH} is missing: build the CUDA libraries first")
+            handle = ctypes.CDLL(PROBE_LIB_PATH)
+            for name, (res, args) in PROBE_SIGNATURES.items():
+                fn = getattr(handle, name)
+                fn.restype = res
+                fn.argtypes = args
+            _probe = handle
+    return _probe
 
 
 def lib():

@@ -400,7 +400,7 @@ def microbench(which: str, iters: int = 20000) -> dict:
            "mma_sw32": 7}[which]
     v = ctypes.c_double()
     s = ctypes.c_double()
-    L.check(L.lib().mdist_microbench(idx, int(iters), ctypes.byref(v), ctypes.byref(s)), "mdist_microbench")
+    L.check(L.probe_lib().mdist_microbench(idx, int(iters), ctypes.byref(v), ctypes.byref(s)), "mdist_microbench")
     return {"per_clock_per_sm": v.value, "seconds": s.value}
 
 

@@ -12,6 +12,7 @@
 
 #include "internal.h"
 #include "prep.h"
+#include "../../include/mdist_debug.h"
 
 using mdist::DeviceRows;
 using mdist::EnumParams;

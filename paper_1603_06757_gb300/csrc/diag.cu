@@ -7,6 +7,7 @@
 #include "combinatorics.cuh"
 #include "internal.h"
 #include "prep.h"
+#include "../../include/mdist_debug.h"
 
 namespace {
 

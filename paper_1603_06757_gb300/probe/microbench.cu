@@ -5,8 +5,9 @@
 // held in registers (no memory traffic) and times itself with clock64().
 #include <cstdint>
 
-#include "internal.h"
-#include "tc_common.cuh"
+#include "../csrc/internal.h"
+#include "../../include/mdist_probe.h"
+#include "../csrc/tc_common.cuh"
 
 namespace mdist {
 namespace {

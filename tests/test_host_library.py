@@ -27,16 +27,29 @@ def lib():
     return L.lib()
 
 
+def _declared(*headers):
+    out = set()
+    for h in headers:
+        hdr = open(os.path.join(ROOT, "include", h)).read()
+        hdr = re.sub(r"/\*.*?\*/", "", hdr, flags=re.S)
+        out |= set(re.findall(r"\b(mdist_[a-z_0-9]+)\s*\(", hdr))
+    return out - {"mdist_alloc_fn", "mdist_free_fn"}
+
+
 def test_header_symbols_exported(lib):
-    hdr = open(os.path.join(ROOT, "include", "mdist.h")).read()
-    hdr = re.sub(r"/\*.*?\*/", "", hdr, flags=re.S)
-    declared = set(re.findall(r"\b(mdist_[a-z_0-9]+)\s*\(", hdr))
-    declared -= {"mdist_alloc_fn", "mdist_free_fn"}
+    # mdist.h and mdist_debug.h: libmdist.so; mdist_probe.h: libmdist_probe.so only
+    declared = _declared("mdist.h", "mdist_debug.h")
     assert len(declared) >= 19
     for name in declared:
         assert hasattr(lib, name), name
         assert name in L.SIGNATURES, name
     assert set(L.SIGNATURES) == declared
+    probes = _declared("mdist_probe.h")
+    assert probes == set(L.PROBE_SIGNATURES) == {"mdist_microbench", "mdist_tc_probe"}
+    plib = L.probe_lib()
+    for name in probes:
+        assert hasattr(plib, name), name
+        assert not hasattr(lib, name), name
 
 
 def _partition_lib(lib, G, n):
@@ -357,7 +370,7 @@ def test_gram_plan_partitions_level_bruteforce(lib, k, mode):
 def test_gram_plan_counts_large_levels(lib, k, mode):
     """At full code sizes: part sizes multiply out to each covered block's size, blocks
     with both sides >= 128 entries are one part, mode 0 splits exactly the blocks with a
-    smaller side and >= 2^24 codewords, and rows of more than 7 words get no parts."""
+    smaller side and >= 2^24 codewords, and rows of more than 8 words get no parts."""
     for g in range(1, k + 1):
         rc, blocks, _, _, _ = _plan(lib, k, g, 4)
         if rc == L.ERANGE:
@@ -374,7 +387,7 @@ def test_gram_plan_counts_large_levels(lib, k, mode):
                 assert cov[b] == (1 if ln * wn >= 1 << 24 else 0), (k, g, b)
             if cov[b]:
                 assert sum(sz for _, _, sz in per_block[b]) == ln * wn
-        rc, parts, _, cov = _gram_plan(lib, k, g, 8, mode)
+        rc, parts, _, cov = _gram_plan(lib, k, g, 9, mode)
         assert rc == 0 and len(parts) == 0 and not cov.any()
 
 
