@@ -52,9 +52,10 @@ L2_FLUSH_BYTES = 256 << 20
 # dense fp8 / bf16 tensor throughput, nominal (2.25 and 4.5 PFLOP/s per GB300)
 FP8_PER_BF16 = 2.0
 # DRAM bytes (read + write) per launch of the dominant kernel (the tensor-core
-# enumerator), from the ncu capture summarised in profiles/ (None until captured for
-# the current kernel)
-TRAFFIC_PER_LAUNCH = {"192x64": 299398976}  # gram_kernel<4>, average over the 24 launches of a timed step
+# enumerator), from the one-launch ncu captures of levels 8-11 summarised in profiles/
+# (a timed step runs each level once per set: the mean of the four); None until
+# captured for the current kernel
+TRAFFIC_PER_LAUNCH = {"192x64": int((72.44 + 204.32 + 578.59 + 1516.26) / 4 * 1e6)}  # gram_kernel<4>
 
 
 def _env_int(name, default):

@@ -462,13 +462,23 @@ __device__ __forceinline__ int job_of(const unsigned long long (&begin)[N], int 
 // A thread takes kTableChunk consecutive entries: it unranks the first, then steps to
 // the next subset of each component in colex order (Gosper's rule; component 1 steps
 // when component 0 wraps) and XORs only the rows that changed.  J.begin counts chunks.
+// The 32 chunks of a warp are 512 consecutive entries of one table (when they lie in
+// one table and are all full): the lanes stage their sums in shared memory (lane
+// regions padded to an odd word stride, so the stores do not collide on banks) and the
+// warp writes the 2 KB x NW block with coalesced 4-byte stores.  Other warps (a table
+// boundary, the last partial chunk) store entry by entry.
+__host__ __device__ constexpr int kStageStride(int nw) { return kTableChunk * nw + 1; }
+
 template <int NW>
 __global__ void side_tables_kernel(const uint32_t *rows, int k, const __grid_constant__ SideJobs J) {
     __shared__ uint32_t s_bn[kBn * kBn];
     __shared__ uint32_t s_rows[64 * NW];
+    extern __shared__ uint32_t s_stage[];  // warps x 32 lanes x kStageStride(NW) words
     for (int i = threadIdx.x; i < kBn * kBn; i += blockDim.x) s_bn[i] = (uint32_t)c_binom_g.v[i / kBn][i % kBn];
     for (int i = threadIdx.x; i < k * NW; i += blockDim.x) s_rows[i] = rows[i];
     __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t *stage = s_stage + (size_t)warp * 32 * kStageStride(NW);
     auto add_rows = [&](uint32_t (&x)[NW], unsigned long long m) {
         while (m) {
             const int r = __ffsll((long long)m) - 1;
@@ -478,51 +488,62 @@ __global__ void side_tables_kernel(const uint32_t *rows, int k, const __grid_con
         }
     };
     const unsigned long long total = J.begin[J.njobs];
-    for (unsigned long long c = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; c < total;
-         c += (unsigned long long)gridDim.x * blockDim.x) {
-        const int i = job_of(J.begin, J.njobs, c);
+    const unsigned long long step = (unsigned long long)gridDim.x * blockDim.x;
+    // every lane of a warp runs the same trips (the warp-wide votes below need them all)
+    for (unsigned long long cw = blockIdx.x * (unsigned long long)blockDim.x + 32ull * warp; cw < total; cw += step) {
+        const unsigned long long c = cw + lane;
+        const bool active = c < total;
+        const int i = active ? job_of(J.begin, J.njobs, c) : J.njobs - 1;
         const GramSide &S = J.side[i];
-        unsigned long long e = (c - J.begin[i]) * kTableChunk;
-        const unsigned long long e_end = e + kTableChunk < S.n ? e + kTableChunk : S.n;
-        unsigned long long e0 = S.nc == 2 ? e % S.cnt0 : e;
-        uint32_t m0 = unrank_colex(s_bn, S.kc[0], S.t[0], (uint32_t)e0);
-        uint32_t m1 = S.nc == 2 ? unrank_colex(s_bn, S.kc[1], S.t[1], (uint32_t)(e / S.cnt0)) : 0u;
-        uint32_t x[NW];
-#pragma unroll
-        for (int w = 0; w < NW; ++w) x[w] = 0;
-        add_rows(x, ((unsigned long long)m0 << S.off[0]) | ((unsigned long long)m1 << S.off[1]));
+        unsigned long long e = active ? (c - J.begin[i]) * kTableChunk : 0;
+        const unsigned long long e_end = active ? (e + kTableChunk < S.n ? e + kTableChunk : S.n) : 0;
+        const int i0 = __shfl_sync(0xffffffffu, i, 0);
+        const bool staged = __all_sync(0xffffffffu, active && i == i0 && e_end - e == kTableChunk);
         uint32_t *out = J.out[i];
-        for (;;) {
-            // one vector store per entry where the row size allows it (the tables are
-            // 256-byte aligned): a warp's stores are 256 bytes apart, so each store
-            // instruction is one L2 write request per lane however wide it is
-            if constexpr (NW == 8) {
-                *reinterpret_cast<uint4 *>(out + e * 8) = make_uint4(x[0], x[1], x[2], x[3]);
-                *reinterpret_cast<uint4 *>(out + e * 8 + 4) = make_uint4(x[4], x[5], x[6], x[7]);
-            } else if constexpr (NW == 4) {
-                *reinterpret_cast<uint4 *>(out + e * 4) = make_uint4(x[0], x[1], x[2], x[3]);
-            } else if constexpr (NW == 2) {
-                *reinterpret_cast<uint2 *>(out + e * 2) = make_uint2(x[0], x[1]);
-            } else {
+        const unsigned long long e_first = e;
+        if (active) {
+            unsigned long long e0 = S.nc == 2 ? e % S.cnt0 : e;
+            uint32_t m0 = unrank_colex(s_bn, S.kc[0], S.t[0], (uint32_t)e0);
+            uint32_t m1 = S.nc == 2 ? unrank_colex(s_bn, S.kc[1], S.t[1], (uint32_t)(e / S.cnt0)) : 0u;
+            uint32_t x[NW];
 #pragma unroll
-                for (int w = 0; w < NW; ++w) out[e * NW + w] = x[w];
+            for (int w = 0; w < NW; ++w) x[w] = 0;
+            add_rows(x, ((unsigned long long)m0 << S.off[0]) | ((unsigned long long)m1 << S.off[1]));
+            for (int q = 0;; ++q) {
+                if (staged) {
+#pragma unroll
+                    for (int w = 0; w < NW; ++w) stage[lane * kStageStride(NW) + q * NW + w] = x[w];
+                } else {
+#pragma unroll
+                    for (int w = 0; w < NW; ++w) out[e * NW + w] = x[w];
+                }
+                if (++e >= e_end) break;
+                unsigned long long diff;
+                if (e0 + 1 < S.cnt0) {
+                    const uint32_t n0 = next_colex(m0);
+                    diff = (unsigned long long)(m0 ^ n0) << S.off[0];
+                    m0 = n0;
+                    ++e0;
+                } else {  // component 0 wraps to its first subset, component 1 steps
+                    const uint32_t n0 = S.t[0] >= 32 ? 0xFFFFFFFFu : (1u << S.t[0]) - 1u;
+                    const uint32_t n1 = next_colex(m1);
+                    diff = ((unsigned long long)(m0 ^ n0) << S.off[0]) | ((unsigned long long)(m1 ^ n1) << S.off[1]);
+                    m0 = n0;
+                    m1 = n1;
+                    e0 = 0;
+                }
+                add_rows(x, diff);
             }
-            if (++e >= e_end) break;
-            unsigned long long diff;
-            if (e0 + 1 < S.cnt0) {
-                const uint32_t n0 = next_colex(m0);
-                diff = (unsigned long long)(m0 ^ n0) << S.off[0];
-                m0 = n0;
-                ++e0;
-            } else {  // component 0 wraps to its first subset, component 1 steps
-                const uint32_t n0 = S.t[0] >= 32 ? 0xFFFFFFFFu : (1u << S.t[0]) - 1u;
-                const uint32_t n1 = next_colex(m1);
-                diff = ((unsigned long long)(m0 ^ n0) << S.off[0]) | ((unsigned long long)(m1 ^ n1) << S.off[1]);
-                m0 = n0;
-                m1 = n1;
-                e0 = 0;
+        }
+        if (staged) {
+            __syncwarp();
+            // word wd of the warp's block: entry wd / NW (lane (wd / NW) / 16, step % 16)
+            uint32_t *dst = out + __shfl_sync(0xffffffffu, e_first, 0) * NW;
+            for (int wd = lane; wd < 32 * kTableChunk * NW; wd += 32) {
+                const int ent = wd / NW, w = wd - ent * NW;
+                dst[wd] = stage[(ent / kTableChunk) * kStageStride(NW) + (ent % kTableChunk) * NW + w];
             }
-            add_rows(x, diff);
+            __syncwarp();
         }
     }
 }
@@ -555,7 +576,10 @@ unsigned int table_grid(unsigned long long work, int sm_count) {
 
 template <int NW>
 cudaError_t side_tables_nw(const uint32_t *rows, int k, const SideJobs &J, int sm_count, cudaStream_t stream) {
-    side_tables_kernel<NW><<<table_grid(J.begin[J.njobs], sm_count), 256, 0, stream>>>(rows, k, J);
+    const size_t smem = (size_t)(256 / 32) * 32 * kStageStride(NW) * sizeof(uint32_t);
+    cudaError_t e = cudaFuncSetAttribute(side_tables_kernel<NW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    side_tables_kernel<NW><<<table_grid(J.begin[J.njobs], sm_count), 256, smem, stream>>>(rows, k, J);
     return cudaGetLastError();
 }
 
