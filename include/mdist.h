@@ -254,7 +254,11 @@ int mdist_batch_create(const mdist_options *opts, void *cuda_stream, mdist_batch
  * Codes cannot be added after mdist_batch_run. */
 int mdist_batch_add(mdist_batch *b, const uint64_t *G, int n, int k, int words_per_row, int wstar_hint, int *index);
 
-/* Run every code to completion.  rounds_per_graph <= 0: chosen from the hints.
+/* Run every code to completion.  rounds_per_graph <= 0: the batched codes' rounds are
+ * ONE launch of a CUDA graph whose conditional WHILE node runs a round per iteration
+ * until no code is active (a device-side counter caps it at MDIST_MAX_K + 2 rounds);
+ * rounds_per_graph > 0: that many rounds captured back to back and the graph
+ * relaunched while codes remain.  Then the large codes run on the single-code path.
  * Device buffers are allocated for the run and released before returning. */
 int mdist_batch_run(mdist_batch *b, int rounds_per_graph);
 

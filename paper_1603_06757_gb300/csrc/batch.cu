@@ -326,6 +326,16 @@ cudaError_t batch_bucket_grids(const bool present[kBatchBuckets], int sm_count, 
     return cudaSuccess;
 }
 
+// One thread, after a round's fold: the run's graph loops (a conditional WHILE node
+// around one round) while codes remain active, for at most max_rounds rounds; the
+// device-side round counter bounds the loop whatever the codes do.
+__global__ void batch_continue(const int *active_ctr, int *rounds_done, int max_rounds, cudaGraphConditionalHandle h) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        const int r = ++*rounds_done;
+        cudaGraphSetConditional(h, (*active_ctr > 0 && r < max_rounds) ? 1u : 0u);
+    }
+}
+
 void batch_launch_round(const BatchDev &D, const bool present[kBatchBuckets], const int grid[kBatchBuckets],
                         cudaStream_t st) {
     const int tb = 128, cb = (D.ncodes + tb - 1) / tb;
@@ -417,6 +427,44 @@ void bfree_all(mdist_batch *b) {
 
 int batch_run_graph(mdist_batch *b, const std::vector<int> &light, int rounds_per_graph);
 int batch_run_large(mdist_batch *b);
+
+// The loop graph of a run: a conditional WHILE node (launch value 1) whose body is one
+// round followed by batch_continue.  False if the toolkit or driver cannot build it.
+bool build_loop_graph(const BatchDev &D, const bool present[kBatchBuckets], const int grid[kBatchBuckets],
+                      cudaStream_t st, int *d_rounds, int max_rounds, cudaGraph_t *out) {
+    *out = nullptr;
+    cudaGraph_t g = nullptr;
+    if (cudaGraphCreate(&g, 0) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    cudaGraphConditionalHandle h;
+    cudaGraphNodeParams np{};
+    cudaGraphNode_t node;
+    bool ok = cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault) == cudaSuccess;
+    if (ok) {
+        np.type = cudaGraphNodeTypeConditional;
+        np.conditional.handle = h;
+        np.conditional.type = cudaGraphCondTypeWhile;
+        np.conditional.size = 1;
+        ok = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np) == cudaSuccess;
+    }
+    if (ok) ok = cudaStreamBeginCaptureToGraph(st, np.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                               cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+    if (ok) {
+        batch_launch_round(D, present, grid, st);
+        batch_continue<<<1, 32, 0, st>>>(D.active_ctr, d_rounds, max_rounds, h);
+        cudaGraph_t body = nullptr;
+        ok = cudaStreamEndCapture(st, &body) == cudaSuccess;
+    }
+    if (!ok) {
+        cudaGetLastError();
+        cudaGraphDestroy(g);
+        return false;
+    }
+    *out = g;
+    return true;
+}
 
 }  // namespace
 
@@ -609,7 +657,7 @@ int batch_run_graph(mdist_batch *b, const std::vector<int> &light, int rounds_pe
     BucketEntry *d_bucket = (BucketEntry *)balloc(b, (size_t)kBatchBuckets * cap * sizeof(BucketEntry));
     unsigned long long *d_packed = (unsigned long long *)balloc(b, 2 * kBatchBuckets * sizeof(unsigned long long));
     unsigned int *d_codeU = (unsigned int *)balloc(b, (size_t)C * sizeof(unsigned int));
-    int *d_ctr = (int *)balloc(b, 2 * sizeof(int));
+    int *d_ctr = (int *)balloc(b, 4 * sizeof(int));  // items, active codes, rounds run
     if (!d_rows || !d_units || !d_gs || !d_codes || !d_counts || !d_items || !d_slots || !d_plans || !d_bucket ||
         !d_packed || !d_codeU || !d_ctr) {
         bfree_all(b);
@@ -663,19 +711,29 @@ int batch_run_graph(mdist_batch *b, const std::vector<int> &light, int rounds_pe
         bfree_all(b);
         return MDIST_ECUDA;
     }
-    // ---- capture the rounds into one graph ----
-    const int R = rounds_per_graph > 0 ? rounds_per_graph : std::max(4, std::min(16, max_spec + 2));
-    b->rounds_per_graph = R;
+    // ---- the rounds as one graph ----
+    // Default: ONE launch of a graph whose conditional WHILE node runs a round per
+    // iteration until no code is active (batch_continue; at most kMaxRounds rounds).
+    // rounds_per_graph > 0: that many rounds captured back to back, the graph relaunched
+    // while codes remain.  Where the loop graph cannot be built, rounds of 4.
+    constexpr int kMaxRounds = MDIST_MAX_K + 2;  // a code ends within k + 1 levels
+    int *d_rounds = d_ctr + 2;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
-    if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
-        cudaGetLastError();
-        if (own) cudaStreamDestroy(own);
-        bfree_all(b);
-        return MDIST_ECUDA;
+    bool looped = rounds_per_graph <= 0 && build_loop_graph(D, present, grid, st, d_rounds, kMaxRounds, &graph);
+    const int R = looped ? 0 : (rounds_per_graph > 0 ? rounds_per_graph : 4);
+    b->rounds_per_graph = R;
+    if (!looped) {
+        if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+            cudaGetLastError();
+            if (own) cudaStreamDestroy(own);
+            bfree_all(b);
+            return MDIST_ECUDA;
+        }
+        for (int r = 0; r < R; ++r) batch_launch_round(D, present, grid, st);
+        if (cudaStreamEndCapture(st, &graph) != cudaSuccess) graph = nullptr;
     }
-    for (int r = 0; r < R; ++r) batch_launch_round(D, present, grid, st);
-    if (cudaStreamEndCapture(st, &graph) != cudaSuccess || cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) {
+    if (!graph || cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) {
         if (graph) cudaGraphDestroy(graph);
         cudaGetLastError();
         if (own) cudaStreamDestroy(own);
@@ -687,21 +745,24 @@ int batch_run_graph(mdist_batch *b, const std::vector<int> &light, int rounds_pe
     cudaEventCreate(&e1);
     int rc = MDIST_OK;
     int *h_active = nullptr;
-    cudaMallocHost((void **)&h_active, sizeof(int));
-    const int max_launches = 65 / (R > 0 ? R : 1) + 2;
-    for (int launch = 0; launch < max_launches; ++launch) {
+    cudaMallocHost((void **)&h_active, 2 * sizeof(int));
+    const int max_launches = looped ? 1 : kMaxRounds / R + 2;
+    if (cudaMemsetAsync(d_rounds, 0, sizeof(int), st) != cudaSuccess) rc = MDIST_ECUDA;
+    for (int launch = 0; launch < max_launches && rc == MDIST_OK; ++launch) {
         cudaEventRecord(e0, st);
         if (cudaGraphLaunch(exec, st) != cudaSuccess) { rc = MDIST_ECUDA; break; }
         cudaEventRecord(e1, st);
-        cudaMemcpyAsync(h_active, D.active_ctr, sizeof(int), cudaMemcpyDeviceToHost, st);
+        cudaMemcpyAsync(h_active, D.active_ctr, 2 * sizeof(int), cudaMemcpyDeviceToHost, st);  // active, rounds
         if (cudaStreamSynchronize(st) != cudaSuccess) { rc = MDIST_ECUDA; break; }
         float ms = 0.f;
         cudaEventElapsedTime(&ms, e0, e1);
         b->gpu_ms += ms;
         b->graph_launches += 1;
-        b->rounds += R;
-        if (*h_active == 0) break;
+        b->rounds = looped ? h_active[1] : b->rounds + R;
+        if (h_active[0] == 0) break;
     }
+    // codes still active here ran into the round cap, which no code reaches (their
+    // results stay MDIST_EAGAIN)
     if (rc == MDIST_OK) {
         b->res.resize((size_t)C);
         b->counts.resize(ncounts);
