@@ -194,6 +194,35 @@ int mdist_level_counters(const mdist_code *code, uint64_t *tc_combos, uint64_t *
  * C(k, g) codewords c * Gamma_j (weights over all n columns) and their count. */
 int mdist_unit_histogram(mdist_code *code, int g, int j, uint64_t *hist, uint64_t *combos_out);
 
+/* One slice of unit(s) (g, j), for a unit split over several ranks: the unit's work —
+ * the tensor-core enumerator's work units and the ALU enumerator's tiles, each in its
+ * own order — is cut into nparts near-equal contiguous slices and slice `part` is
+ * enumerated, otherwise as mdist_enumerate_level (candidates weight <= *U_inout, key
+ * min, combos_out the slice's combinations).  The slices of a unit partition its
+ * combinations: their counts add up to C(k, g) and the least of their keys is the
+ * unit's.  part in [0, nparts), else MDIST_EINVAL. */
+int mdist_enumerate_level_part(mdist_code *code, int g, int j, int part, int nparts, int *U_inout,
+                               mdist_key *key_inout, uint64_t *combos_out);
+
+/* Exchange of one unit's results among the ranks of a sharded run: on entry *key (the
+ * device key weight << 54 | lexicographic rank of this rank's least candidate, or
+ * UINT64_MAX for none) and *count (this rank's combinations); on return the least key
+ * and the summed count over all ranks.  Returns 0, or nonzero when the exchange failed
+ * (a rank left). */
+typedef int (*mdist_exchange_fn)(uint64_t *key, uint64_t *count, void *ctx);
+
+/* Alg. 1 with every unit split over nparts ranks (one GPU each, or several handles of
+ * one GPU): this rank enumerates slice `part` of each unit (mdist_enumerate_level_part),
+ * `exchange` combines the unit's slices over the ranks, and the combined unit is folded
+ * exactly as mdist_run folds it (U, key, counters, L after each level or, with
+ * check_per_matrix, after each unit), so every rank stops at the same unit and
+ * mdist_result then gives every rank mdist_min_distance's result.  Every rank calls this
+ * with the same G, options and nparts; the exchange is on the host (no kernel waits for
+ * another rank).  MDIST_ECANCELLED if an exchange fails (the run stops before folding
+ * that unit).  Not with skip_idle_sets (MDIST_EINVAL). */
+int mdist_run_sharded(mdist_code *code, int part, int nparts, mdist_exchange_fn exchange, void *ctx,
+                      int *finished);
+
 /* Advance Alg. 1 by at most max_units (g, j) units (max_units <= 0: until the end).
  * *finished = 1 once L >= U or every level is done. */
 int mdist_run(mdist_code *code, int max_units, int *finished);

@@ -28,6 +28,8 @@ ESTATE = -8
 EAGAIN = -9
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+EXCHANGE_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64),
+                               ctypes.c_void_p)
 FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
 
 
@@ -108,6 +110,9 @@ SIGNATURES = {
     "mdist_unit_histogram": (ctypes.c_int, [PCODE, ctypes.c_int, ctypes.c_int, P64, P64]),
     "mdist_level_counters": (ctypes.c_int, [PCODE, P64, P64]),
     "mdist_run": (ctypes.c_int, [PCODE, ctypes.c_int, PI]),
+    "mdist_enumerate_level_part": (ctypes.c_int, [PCODE, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, PI,
+                                                  ctypes.POINTER(Key), P64]),
+    "mdist_run_sharded": (ctypes.c_int, [PCODE, ctypes.c_int, ctypes.c_int, EXCHANGE_FN, ctypes.c_void_p, PI]),
     "mdist_reset": (ctypes.c_int, [PCODE]),
     "mdist_result": (ctypes.c_int, [PCODE, PI, P64, P64, ctypes.POINTER(Key), ctypes.POINTER(Stats)]),
     "mdist_min_distance": (ctypes.c_int, [PCODE, PI, P64, P64, ctypes.POINTER(Key), ctypes.POINTER(Stats)]),

@@ -154,6 +154,37 @@ class Code:
         kt = k.as_tuple()
         return Uc.value, (None if kt[0] == 2**31 - 1 else kt), [int(c) for c in combos]
 
+    def enumerate_level_part(self, g: int, j: int, part: int, nparts: int, U: int | None = None):
+        """Slice `part` of `nparts` of unit (g, j) (j = -1: every set).  Returns (U, key tuple
+        or None, combos list) as enumerate_level."""
+        Uc = ctypes.c_int(self.n if U is None else int(U))
+        k = L.Key(2**31 - 1, 0, 0, 0, 0)
+        nunits = self.m if j < 0 else 1
+        combos = np.zeros(nunits, dtype=np.uint64)
+        rc = self._lib.mdist_enumerate_level_part(self._h, int(g), int(j), int(part), int(nparts), ctypes.byref(Uc),
+                                                  ctypes.byref(k), _p64(combos))
+        L.check(rc, "mdist_enumerate_level_part")
+        kt = k.as_tuple()
+        return Uc.value, (None if kt[0] == 2**31 - 1 else kt), [int(c) for c in combos]
+
+    def run_sharded(self, part: int, nparts: int, exchange) -> bool:
+        """mdist_run_sharded: this handle runs slice `part` of every unit; exchange(key, count)
+        returns the (least key, summed count) over all ranks.  An exception inside it ends
+        the run with MDIST_ECANCELLED."""
+        def cb(kp, cp, _ctx):
+            try:
+                kk, cc = exchange(int(kp[0]), int(cp[0]))
+                kp[0], cp[0] = int(kk), int(cc)
+                return 0
+            except Exception:  # noqa: BLE001 - reported to C as a failed exchange
+                return 1
+
+        fn = L.EXCHANGE_FN(cb)
+        fin = ctypes.c_int()
+        L.check(self._lib.mdist_run_sharded(self._h, int(part), int(nparts), fn, None, ctypes.byref(fin)),
+                "mdist_run_sharded")
+        return bool(fin.value)
+
     def level_counters(self) -> dict:
         """Tensor-core counters of the last enumerate_level call: combinations covered
         and pairs re-weighed exactly (the filter's pass count)."""

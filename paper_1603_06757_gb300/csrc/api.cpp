@@ -337,8 +337,9 @@ int gram_plan(mdist_code *c, int j, const EnumParams &p, std::vector<mdist::Gram
 }
 
 // One (g, j) unit on the GPU.  Candidates: codewords of weight <= U_thr.
+// part / nparts: only that slice of the unit's work (a unit split over ranks).
 int run_unit(mdist_code *c, int g, int j, int U_thr, bool hist_mode, bool *found, int *w_out, uint64_t *rank_out,
-             uint64_t *count_out) {
+             uint64_t *count_out, int part = 0, int nparts = 1) {
     const DeviceRows &dr = c->rows[(size_t)j];
     EnumParams p{};
     if (!mdist::plan_level(c->k, g, dr.nwords, p)) return MDIST_ERANGE;
@@ -379,7 +380,7 @@ int run_unit(mdist_code *c, int g, int j, int U_thr, bool hist_mode, bool *found
     int kernels = 0;
     if (mdist::launch_unit_split(p, dr.nwords, group, hist_mode, c->sm_count, c->opt.blocks_per_sm,
                                  gspecs.data(), (int)gspecs.size(), covered, c->stream, c->tc_ev[0], c->tc_ev[1],
-                                 &tc_combos, &kernels) != cudaSuccess)
+                                 &tc_combos, &kernels, part, nparts) != cudaSuccess)
         return MDIST_ECUDA;
     if (cudaEventRecord(c->ev1, c->stream) != cudaSuccess) return MDIST_ECUDA;
     if (cudaMemcpyAsync(c->h_slot, c->d_slot, sizeof(UnitSlot), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess)
@@ -695,6 +696,46 @@ static int launch_units(mdist_code *c, std::vector<UnitRef> &list, int U_thr) {
     return MDIST_OK;
 }
 
+// Fold the result of unit (g, j) — the least device key (weight << 54 | rank) among its
+// candidates, or kNoKey, and its combination count — into the Alg. 1 state, then check
+// the bound after the unit (per-matrix mode) or after its level (Alg. 1, line 7, or the
+// overlapping sets' bound) and advance to the next unit.
+static void fold_unit(mdist_code *c, int g, int j, unsigned long long key, unsigned long long count,
+                      int *units_done) {
+    RunState &s = c->st;
+    s.counts[g][j] = count;
+    s.g_last = g;
+    s.j_last = j;
+    ++*units_done;
+    if (key != mdist::kNoKey) {
+        const int w = (int)(key >> mdist::kKeyRankBits);
+        if (!s.have_key || w < s.key.weight) {
+            s.key = mdist_key{w, g, j, 0, key & ((1ull << mdist::kKeyRankBits) - 1)};
+            s.have_key = 1;
+        }
+        if (w < s.U) s.U = w;
+    }
+    if (c->opt.check_per_matrix) {
+        int h[MDIST_MAX_SETS];
+        for (int i = 0; i < c->m; ++i) h[i] = i <= j ? g : g - 1;
+        const int Lm = mdist::lower_bound(c->part, h);
+        if (Lm > s.L) s.L = Lm;
+        if (s.L >= s.U) s.finished = 1;
+    }
+    s.next_j = j + 1;
+    if (s.next_j == c->m) {
+        s.next_j = 0;
+        if (!c->opt.check_per_matrix) {  // Alg. 1, line 7 (or the overlapping sets' bound)
+            int h[MDIST_MAX_SETS];
+            for (int i = 0; i < c->m; ++i) h[i] = g;
+            s.L = mdist::lower_bound(c->part, h);
+            if (s.L >= s.U) s.finished = 1;
+        }
+        s.next_g = g + 1;
+        if (s.next_g > c->k) s.finished = 1;
+    }
+}
+
 // One wave: the units from (next_g, next_j) through the end of level g_hi (at most
 // max_units of them) are launched back to back, each with its own slot, sharing one
 // candidate threshold (the current best weight, ties kept); one host synchronisation;
@@ -719,41 +760,8 @@ static int run_wave(mdist_code *c, int g_hi, int max_units, int *units_done) {
     if (rc != MDIST_OK) return rc;
     const int n_units = (int)list.size();
     // fold in (g, j) order
-    for (int u = 0; u < n_units && !s.finished; ++u) {
-        const int g = list[(size_t)u].g, j = list[(size_t)u].j;
-        const UnitSlot &r = c->h_wave[u];
-        s.counts[g][j] = r.count;
-        s.g_last = g;
-        s.j_last = j;
-        ++*units_done;
-        if (r.key != mdist::kNoKey) {
-            const int w = (int)(r.key >> mdist::kKeyRankBits);
-            if (!s.have_key || w < s.key.weight) {
-                s.key = mdist_key{w, g, j, 0, r.key & ((1ull << mdist::kKeyRankBits) - 1)};
-                s.have_key = 1;
-            }
-            if (w < s.U) s.U = w;
-        }
-        if (c->opt.check_per_matrix) {
-            int h[MDIST_MAX_SETS];
-            for (int i = 0; i < c->m; ++i) h[i] = i <= j ? g : g - 1;
-            const int Lm = mdist::lower_bound(c->part, h);
-            if (Lm > s.L) s.L = Lm;
-            if (s.L >= s.U) s.finished = 1;
-        }
-        s.next_j = j + 1;
-        if (s.next_j == c->m) {
-            s.next_j = 0;
-            if (!c->opt.check_per_matrix) {  // Alg. 1, line 7 (or the overlapping sets' bound)
-                int h[MDIST_MAX_SETS];
-                for (int i = 0; i < c->m; ++i) h[i] = g;
-                s.L = mdist::lower_bound(c->part, h);
-                if (s.L >= s.U) s.finished = 1;
-            }
-            s.next_g = g + 1;
-            if (s.next_g > c->k) s.finished = 1;
-        }
-    }
+    for (int u = 0; u < n_units && !s.finished; ++u)
+        fold_unit(c, list[(size_t)u].g, list[(size_t)u].j, c->h_wave[u].key, c->h_wave[u].count, units_done);
     return MDIST_OK;
 }
 
@@ -828,6 +836,58 @@ int mdist_run(mdist_code *c, int max_units, int *finished) {
         if (g_hi < s.next_g) g_hi = s.next_g;
         rc = run_wave(c, g_hi, max_units > 0 ? max_units - units : 0, &units);
         if (rc != MDIST_OK) break;
+    }
+    s.seconds += std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (finished) *finished = s.finished;
+    return rc;
+}
+
+int mdist_enumerate_level_part(mdist_code *c, int g, int j, int part, int nparts, int *U_inout, mdist_key *key_inout,
+                               uint64_t *combos_out) {
+    if (!c || !U_inout || !key_inout || g < 1 || g > c->k || j < -1 || j >= c->m || nparts < 1 || part < 0 ||
+        part >= nparts)
+        return MDIST_EINVAL;
+    const int j0 = j < 0 ? 0 : j;
+    const int j1 = j < 0 ? c->m : j + 1;
+    c->level_tc_combos = c->level_tc_cand = 0;
+    for (int jj = j0; jj < j1; ++jj) {
+        bool found;
+        int w;
+        uint64_t rank, cnt;
+        const int rc = run_unit(c, g, jj, *U_inout, false, &found, &w, &rank, &cnt, part, nparts);
+        if (rc != MDIST_OK) return rc;
+        if (combos_out) combos_out[jj - j0] = cnt;
+        if (found) {
+            const mdist_key cand{w, g, jj, 0, rank};
+            if (key_less(cand, *key_inout)) *key_inout = cand;
+            if (w < *U_inout) *U_inout = w;
+        }
+    }
+    return MDIST_OK;
+}
+
+int mdist_run_sharded(mdist_code *c, int part, int nparts, mdist_exchange_fn exchange, void *ctx, int *finished) {
+    if (!c || !exchange || nparts < 1 || part < 0 || part >= nparts || c->opt.skip_idle_sets) return MDIST_EINVAL;
+    RunState &s = c->st;
+    const auto t0 = std::chrono::steady_clock::now();
+    int rc = MDIST_OK, units = 0;
+    while (!s.finished) {
+        const int g = s.next_g, j = s.next_j;
+        // every unit after the key's only counts strictly lighter codewords; before a key
+        // exists ties with U = n - k + 1 count (the same thresholds on every rank)
+        const int thr = s.have_key ? s.key.weight - 1 : s.U;
+        bool found;
+        int w;
+        uint64_t rank, cnt;
+        rc = run_unit(c, g, j, thr, false, &found, &w, &rank, &cnt, part, nparts);
+        if (rc != MDIST_OK) break;
+        uint64_t key = found ? (((uint64_t)w << mdist::kKeyRankBits) | rank) : mdist::kNoKey;
+        uint64_t count = cnt;
+        if (exchange(&key, &count, ctx) != 0) {  // the ranks did not all deliver: stop here
+            rc = MDIST_ECANCELLED;
+            break;
+        }
+        fold_unit(c, g, j, key, count, &units);
     }
     s.seconds += std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     if (finished) *finished = s.finished;

@@ -99,7 +99,7 @@ __global__ void __launch_bounds__(kCtaThreads, MDIST_ENUM_MIN_BLOCKS) enum_unit_
 
     for (;;) {
         unsigned long long tile = 0;
-        if (lane == 0) tile = atomicAdd(&slot->tile_next, 1ull);
+        if (lane == 0) tile = P.tile_lo + atomicAdd(&slot->tile_next, 1ull);
         tile = __shfl_sync(0xffffffffu, tile, 0);
         if (tile >= P.total_tiles) break;
         int b = 0;
@@ -184,7 +184,7 @@ cudaError_t launch_variant(const EnumParams &p, int sm_count, int blocks_per_sm,
     if (e != cudaSuccess) return e;
     if (occ < 1) return cudaErrorInvalidConfiguration;
     const int per_sm = blocks_per_sm > 0 && blocks_per_sm < occ ? blocks_per_sm : occ;
-    unsigned long long want = (p.total_tiles + kWarpsPerCta - 1) / kWarpsPerCta;
+    unsigned long long want = (p.total_tiles - p.tile_lo + kWarpsPerCta - 1) / kWarpsPerCta;
     unsigned long long grid = (unsigned long long)sm_count * (unsigned long long)per_sm;
     if (want < grid) grid = want;
     if (grid < 1) grid = 1;

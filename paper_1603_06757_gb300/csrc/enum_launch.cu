@@ -151,19 +151,21 @@ size_t enum_smem_bytes(int k, int nwords) {
 cudaError_t launch_unit_split(const EnumParams &p, int nwords, int group, bool hist_mode, int sm_count,
                               int blocks_per_sm, const GramBlockSpec *gblocks, int ngblocks, const bool *covered,
                               cudaStream_t stream, cudaEvent_t tc_ev0, cudaEvent_t tc_ev1,
-                              unsigned long long *tc_combos, int *kernels) {
+                              unsigned long long *tc_combos, int *kernels, int part, int nparts) {
+    if (nparts < 1 || part < 0 || part >= nparts) return cudaErrorInvalidValue;
     if (hist_mode) {
         ngblocks = 0;
         covered = nullptr;
     }
     unsigned long long combos = 0;
     for (int i = 0; i < ngblocks; ++i) combos += gblocks[i].a.n * gblocks[i].b.n;
-    if (tc_combos) *tc_combos = combos;
+    if (tc_combos) *tc_combos = nparts == 1 ? combos : (unsigned long long)((double)combos / nparts);
     if (kernels) *kernels = 0;
     if (ngblocks > 0) {
         if (tc_ev0 && cudaEventRecord(tc_ev0, stream) != cudaSuccess) return cudaErrorUnknown;
         const cudaError_t e = launch_gram_unit(p, gblocks, ngblocks, p.U, p.slot,
-                                               reinterpret_cast<int *>(&p.slot->status), sm_count, stream);
+                                               reinterpret_cast<int *>(&p.slot->status), sm_count, stream, part,
+                                               nparts);
         if (e != cudaSuccess) return e;
         if (tc_ev1 && cudaEventRecord(tc_ev1, stream) != cudaSuccess) return cudaErrorUnknown;
         if (kernels) *kernels += 1;
@@ -181,7 +183,9 @@ cudaError_t launch_unit_split(const EnumParams &p, int nwords, int group, bool h
     }
     if (nb == 0) return cudaSuccess;
     q.nblocks = nb;
-    q.total_tiles = tiles;
+    q.tile_lo = tiles * (unsigned long long)part / (unsigned long long)nparts;
+    q.total_tiles = tiles * (unsigned long long)(part + 1) / (unsigned long long)nparts;
+    if (q.total_tiles <= q.tile_lo) return cudaSuccess;
     const cudaError_t e = launch_enum_unit(q, nwords, group, hist_mode, sm_count, blocks_per_sm, stream);
     if (e == cudaSuccess && kernels) *kernels += 1;
     return e;

@@ -104,6 +104,7 @@ struct GramParams {
     int k, g, nwords, n_bits, base;
     int nblocks;
     unsigned int tiles_per_unit;  // B tiles per work unit
+    unsigned long long wu_lo;     // this launch's work units: [wu_lo, total_wu)
     unsigned long long total_wu;
     long long max_wait;          // polls per hand-off wait
     long long drain_wait;        // polls per final drain wait (>= kDefaultWaitPolls)
@@ -213,7 +214,7 @@ __global__ void __launch_bounds__(kGramThreads, 1) gram_kernel(const __grid_cons
     if (warp == 8) {
         // ---------------- A builder ----------------
         unsigned long long u = 0;
-        for (unsigned long long wu = blockIdx.x; wu < P.total_wu && !*s_abort; wu += gridDim.x, ++u) {
+        for (unsigned long long wu = P.wu_lo + blockIdx.x; wu < P.total_wu && !*s_abort; wu += gridDim.x, ++u) {
             int b;
             unsigned long long a_tile, bt0, bt1;
             decode_wu(P, wu, b, a_tile, bt0, bt1);
@@ -237,7 +238,7 @@ __global__ void __launch_bounds__(kGramThreads, 1) gram_kernel(const __grid_cons
         // ---------------- B producer ----------------
         if (lane == 0) {
             unsigned long long t = 0;
-            for (unsigned long long wu = blockIdx.x; wu < P.total_wu && !*s_abort; wu += gridDim.x) {
+            for (unsigned long long wu = P.wu_lo + blockIdx.x; wu < P.total_wu && !*s_abort; wu += gridDim.x) {
                 int b;
                 unsigned long long a_tile, bt0, bt1;
                 decode_wu(P, wu, b, a_tile, bt0, bt1);
@@ -267,7 +268,7 @@ __global__ void __launch_bounds__(kGramThreads, 1) gram_kernel(const __grid_cons
             const uint32_t idesc = idesc_f8f6f4_e4m3_f32(kGM, kGN);
             const uint32_t sbo = (uint32_t)(KA / 16) * 128u;
             unsigned long long t = 0, u = 0, q = 0;  // B tiles, work units, accumulators
-            for (unsigned long long wu = blockIdx.x; wu < P.total_wu && !*s_abort; wu += gridDim.x, ++u) {
+            for (unsigned long long wu = P.wu_lo + blockIdx.x; wu < P.total_wu && !*s_abort; wu += gridDim.x, ++u) {
                 int b;
                 unsigned long long a_tile, bt0, bt1;
                 decode_wu(P, wu, b, a_tile, bt0, bt1);
@@ -314,7 +315,7 @@ __global__ void __launch_bounds__(kGramThreads, 1) gram_kernel(const __grid_cons
         bool ok = true;
         // the TMEM loads below are warp-collective (.sync.aligned), so every decision to
         // stop is taken for the whole warp: the abort flag and each wait's outcome
-        for (unsigned long long wu = blockIdx.x; wu < P.total_wu && ok && !__any_sync(0xffffffffu, *s_abort != 0);
+        for (unsigned long long wu = P.wu_lo + blockIdx.x; wu < P.total_wu && ok && !__any_sync(0xffffffffu, *s_abort != 0);
              wu += gridDim.x) {
             int b;
             unsigned long long a_tile, bt0, bt1;
@@ -423,7 +424,7 @@ cudaError_t gram_launch_nw(const GramParams &p, int sm_count, cudaStream_t strea
     cudaError_t e = cudaFuncSetAttribute(gram_kernel<NW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     unsigned long long grid = (unsigned long long)sm_count;
-    if (p.total_wu < grid) grid = p.total_wu;
+    if (p.total_wu - p.wu_lo < grid) grid = p.total_wu - p.wu_lo;
     if (grid < 1) return cudaSuccess;
     gram_kernel<NW><<<(unsigned int)grid, kGramThreads, smem, stream>>>(p);
     return cudaGetLastError();
@@ -649,7 +650,7 @@ cudaError_t launch_expand_tables(int nwords, int n_bits, const uint32_t *const *
 bool gram_eligible(int nwords) { return nwords >= 1 && nwords <= kGramMaxWords; }
 
 cudaError_t launch_gram_unit(const EnumParams &ep, const GramBlockSpec *blocks, int nblocks, unsigned int *U,
-                             UnitSlot *slot, int *status, int sm_count, cudaStream_t stream) {
+                             UnitSlot *slot, int *status, int sm_count, cudaStream_t stream, int part, int nparts) {
     if (nblocks > kMaxGramBlocks) return cudaErrorInvalidValue;
     GramParams p{};
     p.U = U;
@@ -688,8 +689,10 @@ cudaError_t launch_gram_unit(const EnumParams &ep, const GramBlockSpec *blocks, 
         if (wu >= (unsigned long long)kUnitsPerSmForLong * (unsigned long long)sm_count) break;
     }
     p.nblocks = nb;
-    p.total_wu = wu;
-    if (nb == 0) return cudaSuccess;
+    if (nparts < 1 || part < 0 || part >= nparts) return cudaErrorInvalidValue;
+    p.wu_lo = wu * (unsigned long long)part / (unsigned long long)nparts;
+    p.total_wu = wu * (unsigned long long)(part + 1) / (unsigned long long)nparts;
+    if (nb == 0 || p.total_wu <= p.wu_lo) return cudaSuccess;
     switch (ep.nwords) {
         case 1: return gram_launch_nw<1>(p, sm_count, stream);
         case 2: return gram_launch_nw<2>(p, sm_count, stream);

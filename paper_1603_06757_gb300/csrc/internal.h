@@ -63,6 +63,7 @@ struct EnumParams {
     int n_bits;                  // bits per reduced row
     int nblocks;
     long long wait_polls;        // tensor-core enumerator: polls per bounded wait, 0 = default
+    unsigned long long tile_lo;  // first tile of this launch (a slice of the unit: [tile_lo, total_tiles))
     unsigned long long total_tiles;
     ProductBlock blocks[kMaxBlocks];
 };
@@ -104,8 +105,11 @@ struct GramBlockSpec {
     const uint32_t *b_tab = nullptr;
     const uint8_t *b_exp = nullptr;
 };
+// part / nparts: enumerate the part-th of nparts near-equal contiguous slices of the
+// launch's work units (a unit split over several ranks)
 cudaError_t launch_gram_unit(const EnumParams &ep, const GramBlockSpec *blocks, int nblocks, unsigned int *U,
-                             UnitSlot *slot, int *status, int sm_count, cudaStream_t stream);
+                             UnitSlot *slot, int *status, int sm_count, cudaStream_t stream, int part = 0,
+                             int nparts = 1);
 // Tables built together (one launch each for the packed sums and for the expansions).
 constexpr int kMaxTableJobs = 128;
 // for i < n: outs[i][e * nwords ..] = the sum of the rows (rows: all k rows of the set)
@@ -124,10 +128,14 @@ cudaError_t launch_expand_tables(int nwords, int n_bits, const uint32_t *const *
 // kernel is launched and tc_ev0 / tc_ev1 are given they are recorded around it,
 // *tc_combos (may be null) receives the combinations it enumerates (else 0) and
 // *kernels (may be null) the number of kernels launched (0 to 2).
+// part / nparts: only the part-th of nparts near-equal contiguous slices of each kernel's
+// work (tensor-core work units, ALU tiles); the slices of a unit partition its
+// combinations.  *tc_combos is then the slice's share of the tensor-core combinations.
 cudaError_t launch_unit_split(const EnumParams &p, int nwords, int group, bool hist_mode, int sm_count,
                               int blocks_per_sm, const GramBlockSpec *gblocks, int ngblocks, const bool *covered,
                               cudaStream_t stream, cudaEvent_t tc_ev0 = nullptr, cudaEvent_t tc_ev1 = nullptr,
-                              unsigned long long *tc_combos = nullptr, int *kernels = nullptr);
+                              unsigned long long *tc_combos = nullptr, int *kernels = nullptr, int part = 0,
+                              int nparts = 1);
 
 // Filter variant for a unit: 0 (exact count for every codeword) or the OR-group size
 // 2, 3, 4 whose expected cost is least for this row width and threshold.
