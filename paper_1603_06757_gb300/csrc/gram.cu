@@ -473,7 +473,7 @@ __host__ __device__ constexpr int kStageStride(int nw) { return kTableChunk * nw
 template <int NW>
 __global__ void side_tables_kernel(const uint32_t *rows, int k, const __grid_constant__ SideJobs J) {
     __shared__ uint32_t s_bn[kBn * kBn];
-    __shared__ uint32_t s_rows[64 * NW];
+    __shared__ __align__(16) uint32_t s_rows[64 * NW];
     extern __shared__ uint32_t s_stage[];  // warps x 32 lanes x kStageStride(NW) words
     for (int i = threadIdx.x; i < kBn * kBn; i += blockDim.x) s_bn[i] = (uint32_t)c_binom_g.v[i / kBn][i % kBn];
     for (int i = threadIdx.x; i < k * NW; i += blockDim.x) s_rows[i] = rows[i];
@@ -484,8 +484,19 @@ __global__ void side_tables_kernel(const uint32_t *rows, int k, const __grid_con
         while (m) {
             const int r = __ffsll((long long)m) - 1;
             m &= m - 1;
+            if constexpr (NW % 4 == 0) {  // 16-byte loads of the row
 #pragma unroll
-            for (int w = 0; w < NW; ++w) x[w] ^= s_rows[r * NW + w];
+                for (int v = 0; v < NW / 4; ++v) {
+                    const uint4 t = reinterpret_cast<const uint4 *>(s_rows + r * NW)[v];
+                    x[4 * v] ^= t.x;
+                    x[4 * v + 1] ^= t.y;
+                    x[4 * v + 2] ^= t.z;
+                    x[4 * v + 3] ^= t.w;
+                }
+            } else {
+#pragma unroll
+                for (int w = 0; w < NW; ++w) x[w] ^= s_rows[r * NW + w];
+            }
         }
     };
     const unsigned long long total = J.begin[J.njobs];
@@ -538,12 +549,14 @@ __global__ void side_tables_kernel(const uint32_t *rows, int k, const __grid_con
         }
         if (staged) {
             __syncwarp();
-            // word wd of the warp's block: entry wd / NW (lane (wd / NW) / 16, step % 16)
+            // lane r's 16 entries are words r * 16 NW .. of the warp's block, and they sit
+            // contiguously in its staging region: copy run after run, 32 words at a time
             uint32_t *dst = out + __shfl_sync(0xffffffffu, e_first, 0) * NW;
-            for (int wd = lane; wd < 32 * kTableChunk * NW; wd += 32) {
-                const int ent = wd / NW, w = wd - ent * NW;
-                dst[wd] = stage[(ent / kTableChunk) * kStageStride(NW) + (ent % kTableChunk) * NW + w];
-            }
+#pragma unroll 4
+            for (int r = 0; r < 32; ++r)
+#pragma unroll
+                for (int i = lane; i < kTableChunk * NW; i += 32)
+                    dst[r * kTableChunk * NW + i] = stage[r * kStageStride(NW) + i];
             __syncwarp();
         }
     }
