@@ -219,7 +219,9 @@ typedef int (*mdist_exchange_fn)(uint64_t *key, uint64_t *count, void *ctx);
  * mdist_result then gives every rank mdist_min_distance's result.  Every rank calls this
  * with the same G, options and nparts; the exchange is on the host (no kernel waits for
  * another rank).  MDIST_ECANCELLED if an exchange fails (the run stops before folding
- * that unit).  Not with skip_idle_sets (MDIST_EINVAL). */
+ * that unit).  Not with skip_idle_sets (MDIST_EINVAL).  In the stats, the combination
+ * counters are the whole units' (the exchanged sums); the tensor-core counters
+ * (tc_combos, tc_ms, ...) are this rank's, tc_combos as its proportional share. */
 int mdist_run_sharded(mdist_code *code, int part, int nparts, mdist_exchange_fn exchange, void *ctx,
                       int *finished);
 
