@@ -445,6 +445,26 @@ def run_profile_unit(args):
     return 0
 
 
+def run_profile_batch(args):
+    """The batched engine on the first N codes of the batched workload whose work estimate
+    is below 10^8 codewords (all in the graph, none routed), run twice (the first is a
+    warm-up).  Small, self-contained command for profiler captures of batch_enum."""
+    import torch
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    torch.cuda.set_device(0)
+    codes = batch_codes(args.profile_batch, 2024, 1000, cap=1e8)
+    out = []
+    for _ in range(2):
+        cps, res, info = run_batched(codes)
+        out.append({"codes_per_s": cps, "rounds": info["rounds"], "gpu_ms": info["gpu_ms"]})
+    print(json.dumps({"codes": len(codes), "codewords": sum(r["total_combos"] for r in res), "runs": out}),
+          flush=True)
+    return 0
+
+
 # ----------------------------------------------------------------------------------
 # batched codes and the predictor (config: 4096 random codes, k in [24, 56], n in [2k, 3k])
 # ----------------------------------------------------------------------------------
@@ -489,7 +509,7 @@ def run_plain(codes, hints=None):
     return len(codes) / (time.perf_counter() - t0), res
 
 
-def run_batched(codes, hints=None, blocks_per_sm=0, rounds_per_graph=0, tensor_cores=0):
+def run_batched(codes, hints=None, blocks_per_sm=0, rounds_per_graph=0, tensor_cores=0, route_work_log10=0):
     """All codes in one batched run (rounds captured in one CUDA graph; large codes on
     the single-code tensor-core path unless tensor_cores=1)."""
     import torch
@@ -498,7 +518,7 @@ def run_batched(codes, hints=None, blocks_per_sm=0, rounds_per_graph=0, tensor_c
 
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    with api.Batch(blocks_per_sm=blocks_per_sm, tensor_cores=tensor_cores) as b:
+    with api.Batch(blocks_per_sm=blocks_per_sm, tensor_cores=tensor_cores, route_work_log10=route_work_log10) as b:
         for i, (n, k, G, _) in enumerate(codes):
             b.add(G, n, wstar_hint=hints[i] if hints else 0)
         b.run(rounds_per_graph)
@@ -587,9 +607,10 @@ def batch_report(args, full=False):
     if full:
         from paper_1603_06757_gb300 import tune
 
-        tuned = tune.autotune_batch([(G, n, hh) for (n, k, G, _), hh in zip(light, [0] * len(light))],
+        best_hints = hints[best] or [0] * len(codes)
+        tuned = tune.autotune_batch([(G, n, hh) for (n, k, G, _), hh in zip(codes, best_hints)],
                                     sample=args.tune_sample)
-        shape = {"blocks_per_sm": tuned["blocks_per_sm"], "rounds_per_graph": tuned["rounds_per_graph"]}
+        shape = {"blocks_per_sm": tuned["blocks_per_sm"], "route_work_log10": tuned["route_work_log10"]}
         out["autotune"] = {"chosen": shape, "sample": tuned["sample"], "seconds_best": tuned["seconds_best"],
                            "seconds_worst": tuned["seconds_worst"], "candidates": len(tuned["table"]),
                            "codes_per_s_tuned": run_batched(codes, hints[best], **shape)[0]}
@@ -759,9 +780,12 @@ def main():
                     help="0: large product blocks on the tcgen05 enumerator, 1: ALU enumerator only, 2: all blocks")
     ap.add_argument("--profile-unit", type=int, default=0, help="run one unit of this level (profiling)")
     ap.add_argument("--profile-d", type=int, default=0, help="d of the workload if known (skips the full run)")
+    ap.add_argument("--profile-batch", type=int, default=0, help="run the batched engine on this many light codes")
     args = ap.parse_args()
     if args.profile_unit:
         return run_profile_unit(args)
+    if args.profile_batch:
+        return run_profile_batch(args)
     if args.mode == "batch":
         return run_batch_bench(args)
     if args.mode == "serve":

@@ -120,6 +120,11 @@ typedef struct {
                                 sum_j (h_j + 1).  Reported ranks are the relative ranks.
                                 Pays off when n < 2k.  Single-code handles only; not with
                                 skip_idle_sets (MDIST_EINVAL). */
+    int route_work_log10;    /* batched engine and server: a code whose estimated work (every
+                                set up to the predicted termination level: the hint, else
+                                the Gilbert-Varshamov estimate) reaches 10^route_work_log10
+                                codewords runs on the single-code tensor-core path; 0 = 9
+                                (10^9), else 1..18 (MDIST_EINVAL otherwise). */
 } mdist_options;
 
 /* Witness key: the least (weight, g, j, rank) over the enumerated units (a total

@@ -47,6 +47,7 @@ class Options(ctypes.Structure):
         ("tensor_cores", ctypes.c_int),
         ("skip_idle_sets", ctypes.c_int),
         ("overlap_sets", ctypes.c_int),
+        ("route_work_log10", ctypes.c_int),
     ]
 
 

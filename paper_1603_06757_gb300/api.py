@@ -439,9 +439,10 @@ class Batch:
     """Many codes through Alg. 1 together (mdist_batch_*): one graph of rounds."""
 
     def __init__(self, *, check_per_matrix: bool = False, max_sets: int = 0, blocks_per_sm: int = 0, stream=None,
-                 torch_alloc: bool = True, tensor_cores: int = 0):
-        """tensor_cores: 0 = codes estimated at >= 10^9 codewords on the single-code
-        tensor-core path, 1 = every code in the graph, 2 = every code on that path."""
+                 torch_alloc: bool = True, tensor_cores: int = 0, route_work_log10: int = 0):
+        """tensor_cores: 0 = codes estimated at >= 10^route_work_log10 (0: 10^9) codewords
+        on the single-code tensor-core path, 1 = every code in the graph, 2 = every code on
+        that path."""
         torch = _torch()
         self._lib = L.lib()
         self._stream = stream if stream is not None else torch.cuda.current_stream()
@@ -451,6 +452,7 @@ class Batch:
         opts.max_sets = int(max_sets)
         opts.blocks_per_sm = int(blocks_per_sm)
         opts.tensor_cores = int(tensor_cores)
+        opts.route_work_log10 = int(route_work_log10)
         if self._alloc is not None:
             opts.dev_alloc = self._alloc.alloc_cb
             opts.dev_free = self._alloc.free_cb

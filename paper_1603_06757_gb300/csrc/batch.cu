@@ -472,7 +472,7 @@ extern "C" {
 
 int mdist_batch_create(const mdist_options *opts, void *cuda_stream, mdist_batch **out) {
     if (!out || (opts && (opts->skip_idle_sets || opts->overlap_sets || opts->tensor_cores < 0 ||
-                          opts->tensor_cores > 3)))
+                          opts->tensor_cores > 3 || opts->route_work_log10 < 0 || opts->route_work_log10 > 18)))
         return MDIST_EINVAL;
     *out = nullptr;
     mdist_batch *b = new (std::nothrow) mdist_batch();
@@ -507,7 +507,8 @@ int mdist_batch_add(mdist_batch *b, const uint64_t *G, int n, int k, int words_p
     hc.rows.resize(hc.part.sets.size());
     for (size_t j = 0; j < hc.part.sets.size(); ++j) build_rows(hc.part, (int)j, hc.rows[j]);
     const int tc = b->opt.tensor_cores;
-    hc.large = tc == 2 || (tc == 0 && estimated_work(n, k, hc.part, hc.wstar) >= kTensorPathWork);
+    hc.large = tc == 2 ||
+               (tc == 0 && estimated_work(n, k, hc.part, hc.wstar) >= tensor_path_work(b->opt.route_work_log10));
     if (index) *index = (int)b->codes.size();
     b->codes.push_back(std::move(hc));
     return MDIST_OK;

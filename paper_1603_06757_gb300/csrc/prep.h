@@ -36,8 +36,15 @@ int partition_overlapping_sets(const uint64_t *G, int n, int k, int W, int msets
 double estimated_work(int n, int k, const Partition &p, int wstar);
 
 // Codes whose estimated work reaches this run on the single-code path with the
-// tensor-core enumerator when the batched engine or the serving loop gets them.
+// tensor-core enumerator when the batched engine or the serving loop gets them
+// (mdist_options.route_work_log10 = 0; otherwise 10^route_work_log10).
 constexpr double kTensorPathWork = 1e9;
+inline double tensor_path_work(int route_work_log10) {
+    if (route_work_log10 <= 0) return kTensorPathWork;
+    double w = 1.0;
+    for (int i = 0; i < route_work_log10; ++i) w *= 10.0;
+    return w;
+}
 
 // Lower bound on the weight of every codeword not yet enumerated, once set j has all of
 // its units of levels <= h[j] done (h[j] = 0: none).

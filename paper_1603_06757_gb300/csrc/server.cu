@@ -421,7 +421,8 @@ extern "C" {
 
 int mdist_server_create(const mdist_options *opts, int max_slots, size_t rows_pool_bytes, mdist_server **out) {
     if (!out || max_slots < 1 || max_slots > (1 << 16) || rows_pool_bytes < 4096 ||
-        (opts && (opts->skip_idle_sets || opts->overlap_sets)))
+        (opts && (opts->skip_idle_sets || opts->overlap_sets || opts->route_work_log10 < 0 ||
+                  opts->route_work_log10 > 18)))
         return MDIST_EINVAL;
     *out = nullptr;
     mdist_server *s = new (std::nothrow) mdist_server();
@@ -509,7 +510,8 @@ int mdist_server_submit(mdist_server *s, const uint64_t *G, int n, int k, int wo
     }
     if (rq->rows_words > s->pool_words) { delete rq; return MDIST_ENOMEM; }
     const int tc = s->opt.tensor_cores;
-    rq->large = tc == 2 || (tc == 0 && estimated_work(rq->n, rq->k, rq->part, rq->wstar) >= kTensorPathWork);
+    rq->large = tc == 2 || (tc == 0 && estimated_work(rq->n, rq->k, rq->part, rq->wstar) >=
+                                           tensor_path_work(s->opt.route_work_log10));
     std::lock_guard<std::mutex> lock(s->mu);
     if (s->stopping) { delete rq; return MDIST_ECANCELLED; }
     rq->id = s->next_id++;

@@ -17,14 +17,14 @@ def test_sample_indices_are_distinct_sorted_and_seeded():
 def test_autotune_picks_the_fastest_shape_and_times_every_candidate():
     calls = []
 
-    def fake(sample, bps, rpg):
-        calls.append((len(sample), bps, rpg))
-        return 1.0 + abs(bps - 2) + abs(rpg - 8) / 8.0
+    def fake(sample, bps, rw):
+        calls.append((len(sample), bps, rw))
+        return 1.0 + abs(bps - 2) + abs(rw - 8) / 8.0
 
     codes = [(None, 10 + i) for i in range(500)]
-    r = tune.autotune_batch(codes, sample=100, blocks_per_sm=(0, 1, 2, 3), rounds_per_graph=(0, 4, 8, 16),
+    r = tune.autotune_batch(codes, sample=100, blocks_per_sm=(0, 1, 2, 3), route_work_log10=(7, 8, 9, 10),
                             runner=fake)
-    assert (r["blocks_per_sm"], r["rounds_per_graph"]) == (2, 8)
+    assert (r["blocks_per_sm"], r["route_work_log10"]) == (2, 8)
     assert r["sample"] == 100 and len(r["table"]) == 16
     assert len(calls) == 17 and all(c[0] == 100 for c in calls)  # one warm-up + 16 timed
     assert r["seconds_best"] == 1.0 and r["seconds_worst"] == max(t["seconds"] for t in r["table"])
