@@ -576,7 +576,7 @@ def batch_report(args, full=False):
     run_plain(codes[:16])
     cps, res, info = {}, {}, {}
     for name, h in hints.items():
-        cps[name], res[name], info[name] = run_batched(codes, h)
+        cps[name], res[name], info[name] = run_batched(codes, h, route_work_log10=args.route_work_log10)
     cps_plain, res_plain = run_plain(codes)
     same = all(_same_results(res[name], res_plain) for name in hints)
     truth = [(r["g_final"], r["d"]) for r in res_plain]
@@ -593,6 +593,9 @@ def batch_report(args, full=False):
                                "seeds 1000+i (every code)",
                    "codewords": sum(r["total_combos"] for r in res_plain),
                    "large_codes": info["none"]["large_codes"],
+                   "route_work_log10": args.route_work_log10,
+                   "route_basis": "codes estimated at >= 10^route_work_log10 codewords run on the single-code "
+                                  "tensor-core path; 10 = tune.py's choice on a 256-code sample of this workload",
                    "train_codes": len(train)},
         "codes_per_s": {"plain": cps_plain, **{f"batched_{k}_hints": v for k, v in cps.items()}},
         "speedup_vs_plain": cps[best] / cps_plain,
@@ -767,6 +770,8 @@ def main():
     ap.add_argument("--batch-codes", type=int, default=4096)
     ap.add_argument("--batch-train", type=int, default=1500)
     ap.add_argument("--batch-cap", type=float, default=1e10)
+    ap.add_argument("--route-work-log10", type=int, default=10,
+                    help="batched engine: routing threshold of the tensor-core path (10^x codewords)")
     ap.add_argument("--tune-sample", type=int, default=256, help="codes the batched launch-shape autotuner times")
     ap.add_argument("--serve-requests", type=int, default=20000)
     ap.add_argument("--serve-cap", type=float, default=1e11)
