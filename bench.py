@@ -582,8 +582,8 @@ def batch_report(args, full=False):
     truth = [(r["g_final"], r["d"]) for r in res_plain]
     errs = {"mlp": predict.errors(p_mlp, truth), "gv": predict.errors(p_gv, truth)}
     # the light codes alone (those the default routing keeps in the graph)
-    light = [c for c in codes if gv_work(c[0], c[1], c[3]) < 1e9]
-    cps_light_b, res_lb, _ = run_batched(light)
+    light = [c for c in codes if gv_work(c[0], c[1], c[3]) < 10.0 ** args.route_work_log10]
+    cps_light_b, res_lb, _ = run_batched(light, route_work_log10=args.route_work_log10)
     cps_light_p, res_lp = run_plain(light)
     best = max(cps, key=cps.get)
     out = {
