@@ -41,6 +41,8 @@ WORKLOADS = {
     "150x64": "single random [150,64] code (ranks 64,64,22)",
     "300x50": "single random [300,50] code (six rank-50 sets)",
     "60x30": "single random [60,30] code, seed 1",
+    "96x64": "single random [96,64] code, seed 1 (n < 2k: disjoint sets of ranks 64, 32; see --overlap-sets)",
+    "112x64": "single random [112,64] code, seed 1 (n < 2k: disjoint sets of ranks 64, 48; see --overlap-sets)",
 }
 # POPC retired per SM per clock on compute capability 7.0-10.x (CUDA C++ Programming
 # Guide, arithmetic-instruction throughput table: "population count" 16)
@@ -230,7 +232,7 @@ def run_ours(args):
 
     n, k, seed, G = workload(args.workload)
     stream = torch.cuda.current_stream()
-    code = api.Code(G, n, tensor_cores=args.tensor_cores)
+    code = api.Code(G, n, tensor_cores=args.tensor_cores, overlap_sets=args.overlap_sets)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
 
     sharded = args.shard and world > 1
@@ -293,7 +295,7 @@ def run_ours(args):
     e2e_cw = 0
     h2d = d2h = 0
     for _ in range(e2e_steps):
-        r = api.min_distance(G, n)
+        r = api.min_distance(G, n, overlap_sets=args.overlap_sets)
         e2e_cw += r["total_combos"]
         h2d, d2h = r["h2d_bytes"], r["d2h_bytes"]
     torch.cuda.synchronize()
@@ -302,7 +304,7 @@ def run_ours(args):
 
     # ---- the same runs on the ALU enumerator alone (XOR / POPC, no tensor cores) ----
     alu_steps = 2
-    code_alu = api.Code(G, n, tensor_cores=1)
+    code_alu = api.Code(G, n, tensor_cores=1, overlap_sets=args.overlap_sets)
     code_alu.reset()
     code_alu.run()
     torch.cuda.synchronize()
@@ -331,7 +333,7 @@ def run_ours(args):
     peaks = _peaks()
     sm_mhz = float(peaks.get("sm_max_mhz") or info["max_sm_clock_khz"] / 1e3)
     part = api.partition_host(G, n)
-    full = all(int(r) == k for r in part["ranks"])
+    full = args.overlap_sets > 0 or all(int(r) == k for r in part["ranks"])
     n_bits = (n - k) if full else n
     nwords = max(1, math.ceil(n_bits / 32))
     try:
@@ -399,7 +401,7 @@ def run_ours(args):
             "data": "synthetic",
             "config": {"workload": WORKLOADS[args.workload], "n": n, "k": k, "seed": seed, "d": res["d"],
                        "g_final": res["g_final"], "ranks": res["ranks"], "codewords_per_step": res["total_combos"],
-                       "launches_per_step": res["launches"],
+                       "launches_per_step": res["launches"], "overlap_sets": args.overlap_sets,
                        "parallelism": f"one code split over {world} ranks" if sharded else f"replicas x{world}",
                        "l2": "flushed (256 MiB write) before every timed step; inputs ~2 KB"},
             "roofline": roofline,
@@ -762,6 +764,8 @@ def main():
     ap.add_argument("--cpu-levels", type=int, default=8)
     ap.add_argument("--ref-levels", type=int, default=7)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--overlap-sets", type=int, default=0,
+                    help="M > 0: M overlapping information sets (the non-disjoint bound) instead of disjoint ones")
     ap.add_argument("--shard", action="store_true",
                     help="N > 1: split one code's units over the ranks (strong scaling) instead of N replicas")
     ap.add_argument("--no-extensions", action="store_true",

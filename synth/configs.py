@@ -11,6 +11,8 @@ SINGLE = {
     "192x64": (192, 64, [64, 64, 64], 1),
     "150x64": (150, 64, [64, 64, 22], 1),
     "300x50": (300, 50, [50] * 6, 1),
+    "96x64": (96, 64, None, 1),
+    "112x64": (112, 64, None, 1),
 }
 
 
