@@ -290,6 +290,9 @@ def run_ours(args):
 
     # ---- end to end through the C-ABI from host buffers ----
     e2e_steps = max(1, min(args.steps, 3))
+    # one untimed call first: the caching allocator grows once per process to hold a
+    # second handle's tables beside the timed handle's (a warm-up, like the steps')
+    api.min_distance(G, n, overlap_sets=args.overlap_sets)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     e2e_cw = 0

@@ -3,7 +3,9 @@
  * the enumerators read and the combination indexing and work plans they run, evaluated
  * on the host (no CUDA call; usable without a GPU).  The tests check them against
  * independent computations; mdist_enumerate_unit_noalloc callers use
- * mdist_debug_set_rows to lay out a set's rows.  Conventions as in mdist.h.
+ * mdist_debug_set_rows to lay out a set's rows.  One entry point, mdist_debug_side_tables,
+ * runs on the device: the table kernel of the tensor-core enumerator, so that the GPU
+ * tests can check its tables entry by entry.  Conventions as in mdist.h.
  */
 #ifndef MDIST_DEBUG_H
 #define MDIST_DEBUG_H
@@ -56,6 +58,27 @@ int mdist_debug_level_plan(int k, int g, int nwords, int *nblocks, uint64_t *blo
  * C(k, g) >= 2^54.  Host only, no CUDA calls. */
 int mdist_debug_gram_plan(int k, int g, int nwords, int tensor_cores, int *nparts, int *parts, uint64_t *sizes,
                           int *covered);
+
+/* The subset-sum tables of tensor-core sides (the one device entry point here; it
+ * launches the kernel the enumerator uses).  rows: device pointer to k rows of nwords
+ * 32-bit words (4-byte aligned; a set's layout as mdist_debug_set_rows gives it).
+ * sides[6 * i ..] for i < n: off0, kc0, t0, off1, kc1, t1 as in mdist_debug_gram_plan
+ * (t1 = -1: one component).  outs[i]: device buffer, 16-byte aligned, of
+ * C(kc0, t0) x C(kc1, t1) x nwords words; entry e, whose component-0 subset has colex
+ * rank e mod C(kc0, t0) and component-1 subset colex rank e div C(kc0, t0), receives
+ * the XOR of the rows of both subsets (component c: rows off_c + its elements) at
+ * words e * nwords ...  lows (may be NULL) and low_t: where lows[i] is not NULL it is
+ * the finished table (from an earlier call, 16-byte aligned) of the one-component side
+ * (off0, kc0, low_t[i]) on the same rows, 0 < low_t[i] < t0, which the kernel reads
+ * instead of building the low-subset sums in shared memory (the library passes the
+ * tables of earlier levels this way).  The caller owns every buffer.  Queued on `stream`
+ * (a cudaStream_t; NULL: the legacy default stream); the call returns without waiting.
+ * MDIST_EINVAL on a null or misaligned pointer, n outside 1..128, nwords outside 1..8,
+ * k outside 1..64, a component of 0 or more than 32 rows, past row k or with t > kc,
+ * two components that share a row, or a low_t[i] outside (0, t0); MDIST_ECUDA if the
+ * launch fails. */
+int mdist_debug_side_tables(const uint32_t *rows, int k, int nwords, int n, const int *sides, uint32_t *const *outs,
+                            const uint32_t *const *lows, const int *low_t, void *stream);
 
 #ifdef __cplusplus
 }

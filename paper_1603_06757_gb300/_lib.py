@@ -173,6 +173,9 @@ SIGNATURES = {
     "mdist_debug_level_plan": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, PI, P64, P64, PI, PI]),
     "mdist_debug_gram_plan": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, PI, PI, P64,
                                              PI]),
+    "mdist_debug_side_tables": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, PI,
+                                                ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p), PI,
+                                                ctypes.c_void_p]),
 }
 
 

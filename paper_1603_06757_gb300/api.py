@@ -423,6 +423,45 @@ def overlap_bound_host(G, n: int, msets: int, levels) -> int:
     return out.value
 
 
+def side_tables(rows, sides, lows=None) -> list:
+    """The tensor-core enumerator's subset-sum tables (mdist_debug_side_tables), built on
+    the current device: rows (k, nwords) uint32; sides: tuples (off0, kc0, t0, off1, kc1,
+    t1), t1 = -1 for one component; lows: per side None or the index of an earlier side of
+    the same list, a one-component side (off0, kc0, u), 0 < u < t0, whose table is built
+    first (a separate launch) and read as the low-subset sums.  Returns one
+    (entries, nwords) uint32 array per side."""
+    import math
+
+    torch = _torch()
+    rows = np.ascontiguousarray(np.asarray(rows, dtype=np.uint32))
+    k, nw = rows.shape
+    d_rows = torch.from_numpy(rows.view(np.int32).copy()).cuda()
+    lows = list(lows) if lows is not None else [None] * len(sides)
+    outs = []
+    for (off0, kc0, t0, off1, kc1, t1) in sides:
+        cnt = math.comb(kc0, t0) * (math.comb(kc1, t1) if t1 >= 0 else 1)
+        outs.append((torch.empty(max(cnt * nw, 4), dtype=torch.int32, device=d_rows.device), cnt))
+    stream = torch.cuda.current_stream()
+
+    def launch(idx):
+        flat = np.ascontiguousarray(np.asarray([sides[i] for i in idx], dtype=np.int32).reshape(-1))
+        parr = (ctypes.c_void_p * len(idx))(*[outs[i][0].data_ptr() for i in idx])
+        larr = (ctypes.c_void_p * len(idx))(*[outs[lows[i]][0].data_ptr() if lows[i] is not None else None
+                                              for i in idx])
+        lt = np.asarray([sides[lows[i]][2] if lows[i] is not None else 0 for i in idx], dtype=np.int32)
+        L.check(L.lib().mdist_debug_side_tables(ctypes.c_void_p(d_rows.data_ptr()), k, nw, len(idx),
+                                                flat.ctypes.data_as(L.PI), parr, larr, lt.ctypes.data_as(L.PI),
+                                                ctypes.c_void_p(stream.cuda_stream)), "mdist_debug_side_tables")
+
+    first = [i for i in range(len(sides)) if lows[i] is None]
+    second = [i for i in range(len(sides)) if lows[i] is not None]
+    for part in (first, second):
+        for a in range(0, len(part), 128):
+            launch(part[a:a + 128])
+    stream.synchronize()
+    return [t[: cnt * nw].cpu().numpy().view(np.uint32).reshape(cnt, nw) for t, cnt in outs]
+
+
 def microbench(which: str, iters: int = 20000) -> dict:
     """Per-SM-per-clock throughput of 'popc', 'lop3', 'step4', 'step4_or2', 'step4_or4' or
     of the fp8 tensor-core MMA ('mma' no swizzle, 'mma_sw128', 'mma_sw32': multiply-adds)

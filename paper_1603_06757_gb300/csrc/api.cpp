@@ -8,6 +8,7 @@
 #include <cstring>
 #include <new>
 #include <map>
+#include <mutex>
 #include <vector>
 
 #include "internal.h"
@@ -59,7 +60,8 @@ struct mdist_code {
     int device = 0, sm_count = 0;
     std::vector<uint32_t *> d_rows;
     UnitSlot *d_slot = nullptr;
-    UnitSlot *h_slot = nullptr;          // pinned
+    UnitSlot *h_slot = nullptr;          // pinned (pinned_get)
+    unsigned long long pinned_ctx = 0;   // context the pinned blocks belong to (0: unknown)
     unsigned long long *d_hist = nullptr;// n+1 bins, on demand
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     std::vector<cudaEvent_t> tc_ev;      // event pairs around tensor-core launches, one pair per unit of a wave
@@ -86,6 +88,53 @@ struct mdist_code {
 };
 
 namespace {
+
+// Page-locked host blocks kept after a handle is freed and handed to the next handle
+// made in the same CUDA context: cudaMallocHost and cudaFreeHost cost tens of
+// microseconds each and cudaFreeHost waits for the device.  A block belongs to the
+// context that allocated it (its pages go with the context), so it is filed under that
+// context's unique id and only reused there; at most kPinnedKeep blocks are kept.
+struct PinnedBlock {
+    unsigned long long ctx;
+    size_t bytes;
+    void *p;
+};
+constexpr size_t kPinnedKeep = 32;
+std::mutex g_pinned_mu;
+std::vector<PinnedBlock> g_pinned;
+
+void *pinned_get(size_t bytes, unsigned long long *ctx) {
+    unsigned long long id = 0;
+    if (mdist::current_context_id(&id) == MDIST_OK) {
+        std::lock_guard<std::mutex> lock(g_pinned_mu);
+        for (size_t i = 0; i < g_pinned.size(); ++i)
+            if (g_pinned[i].ctx == id && g_pinned[i].bytes == bytes) {
+                void *p = g_pinned[i].p;
+                g_pinned.erase(g_pinned.begin() + (long)i);
+                *ctx = id;
+                return p;
+            }
+    }
+    void *p = nullptr;
+    if (cudaMallocHost(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    *ctx = mdist::current_context_id(&id) == MDIST_OK ? id : 0;  // the context exists now
+    return p;
+}
+
+void pinned_put(void *p, size_t bytes, unsigned long long ctx) {
+    if (!p) return;
+    if (ctx) {
+        std::lock_guard<std::mutex> lock(g_pinned_mu);
+        if (g_pinned.size() < kPinnedKeep) {
+            g_pinned.push_back({ctx, bytes, p});
+            return;
+        }
+    }
+    if (cudaFreeHost(p) != cudaSuccess) cudaGetLastError();  // e.g. its context is gone
+}
 
 void *dev_alloc(mdist_code *c, size_t bytes) {
     if (c->opt.dev_alloc) return c->opt.dev_alloc(bytes, c->opt.alloc_ctx);
@@ -167,15 +216,17 @@ uint64_t side_key(int j, const mdist::GramSide &S, bool expanded) {
     return key;
 }
 
-// Device memory for a table: 256-byte aligned pieces of chunks of at least 64 MiB, so
-// that a run's hundreds of tables cost a handful of allocator calls.  The first piece
-// starts at the chunk's first 256-byte boundary, whatever the allocator's alignment
-// (bulk copies and vector stores need 16-byte aligned tables).
+// Device memory for a table: 256-byte aligned pieces of chunks that start at 64 MiB and
+// double with every chunk up to 1 GiB, so that a run's hundreds of tables (several GB
+// on the large codes) cost a handful of allocator calls while a small code holds one
+// small chunk.  The first piece starts at the chunk's first 256-byte boundary, whatever
+// the allocator's alignment (bulk copies and vector stores need 16-byte aligned tables).
 void *table_alloc(mdist_code *c, size_t bytes) {
-    constexpr size_t kChunk = 64ull << 20, kAlign = 256;
+    constexpr size_t kChunk = 64ull << 20, kChunkMax = 1ull << 30, kAlign = 256;
     bytes = (bytes + kAlign - 1) / kAlign * kAlign;
     if (c->tab_chunks.empty() || c->chunk_used + bytes > c->chunk_size) {
-        const size_t size = (bytes > kChunk ? bytes : kChunk) + kAlign;
+        const size_t grown = c->tab_chunks.size() < 5 ? kChunk << c->tab_chunks.size() : kChunkMax;
+        const size_t size = (bytes > grown ? bytes : grown) + kAlign;
         void *p = dev_alloc(c, size);
         if (!p) return nullptr;
         c->tab_chunks.push_back(p);
@@ -187,17 +238,74 @@ void *table_alloc(mdist_code *c, size_t bytes) {
     return p;
 }
 
-// Build the pending tables of set c->pend_j: one launch for the packed sums, one for
-// the expansions (after them, on the same stream).
+int side_table(mdist_code *c, int j, const mdist::GramSide &S, bool expanded, const void **out);
+
+// Low tables: the packed table of the one-component side (off0, kc0, u) of set j, built
+// by an earlier flush, with the largest u in [3, t0) whose table fits in kLowTableBytes
+// (it stays in the L2 while the new table streams past); 0 when there is none.
+constexpr size_t kLowTableBytes = 32ull << 20;
+
+int low_table(const mdist_code *c, int j, const mdist::GramSide &S, int nwords, const uint32_t **out) {
+    *out = nullptr;
+    for (int u = (int)S.t[0] - 1; u >= 3; --u) {
+        if ((size_t)mdist::binom_host(S.kc[0], u) * (size_t)nwords * sizeof(uint32_t) > kLowTableBytes) continue;
+        auto it = c->tabs.find(side_key(j, make_side(S.off[0], S.kc[0], u), false));
+        if (it == c->tabs.end()) continue;
+        if (std::find(c->pend_outs.begin(), c->pend_outs.end(), (uint32_t *)it->second) != c->pend_outs.end())
+            continue;  // not written yet
+        *out = (const uint32_t *)it->second;
+        return u;
+    }
+    return 0;
+}
+
+// Build the pending tables of set c->pend_j.  First launch: the sides of t0 <= 3 (their
+// low-subset sums built in shared memory) and those with a low table from an earlier
+// flush; second launch: the other sides, reading the table of the 3-subsets of their
+// component-0 rows written by the first (allocated here when no block needs it).  Then
+// one launch for the expansions, all on the same stream.
 int flush_tables(mdist_code *c) {
     if (c->pend_j < 0) return MDIST_OK;
-    const DeviceRows &dr = c->rows[(size_t)c->pend_j];
+    const int j = c->pend_j;
+    const DeviceRows &dr = c->rows[(size_t)j];
+    const size_t np = c->pend_sides.size();
+    std::vector<const uint32_t *> lows(np);
+    std::vector<int> low_t(np), wave(np);
+    for (size_t i = 0; i < np; ++i) {
+        const mdist::GramSide S = c->pend_sides[i];
+        low_t[i] = low_table(c, j, S, dr.nwords, &lows[i]);
+        if (low_t[i] || S.t[0] <= 3) continue;
+        const void *t3 = nullptr;  // may append a pending table of t0 = 3 (built first)
+        const int rc = side_table(c, j, make_side(S.off[0], S.kc[0], 3), false, &t3);
+        if (rc != MDIST_OK) return rc;
+        if (t3) {
+            lows[i] = (const uint32_t *)t3;
+            low_t[i] = 3;
+            wave[i] = 1;
+        }
+    }
+    lows.resize(c->pend_sides.size());
+    low_t.resize(c->pend_sides.size());
+    wave.resize(c->pend_sides.size());
     cudaError_t e = cudaSuccess;
-    for (size_t i = 0; i < c->pend_sides.size() && e == cudaSuccess; i += mdist::kMaxTableJobs) {
-        const int n = (int)std::min<size_t>(mdist::kMaxTableJobs, c->pend_sides.size() - i);
-        e = mdist::launch_side_tables(c->d_rows[(size_t)c->pend_j], c->k, dr.nwords, &c->pend_sides[i],
-                                      &c->pend_outs[i], n, c->sm_count, c->stream);
-        c->st.launches += 1;
+    for (int w = 0; w < 2 && e == cudaSuccess; ++w) {
+        std::vector<mdist::GramSide> sides;
+        std::vector<uint32_t *> outs;
+        std::vector<const uint32_t *> lw;
+        std::vector<int> lt;
+        for (size_t i = 0; i < c->pend_sides.size(); ++i) {
+            if (wave[i] != w) continue;
+            sides.push_back(c->pend_sides[i]);
+            outs.push_back(c->pend_outs[i]);
+            lw.push_back(lows[i]);
+            lt.push_back(low_t[i]);
+        }
+        for (size_t i = 0; i < sides.size() && e == cudaSuccess; i += mdist::kMaxTableJobs) {
+            const int n = (int)std::min<size_t>(mdist::kMaxTableJobs, sides.size() - i);
+            e = mdist::launch_side_tables(c->d_rows[(size_t)j], c->k, dr.nwords, &sides[i], &outs[i], &lw[i], &lt[i],
+                                          n, c->sm_count, c->stream);
+            c->st.launches += 1;
+        }
     }
     for (size_t i = 0; i < c->pend_xout.size() && e == cudaSuccess; i += mdist::kMaxTableJobs) {
         const int n = (int)std::min<size_t>(mdist::kMaxTableJobs, c->pend_xout.size() - i);
@@ -313,6 +421,45 @@ int gram_block_parts(int mode, int k1, int k2, const mdist::ProductBlock &B, int
     return i1 - i0 + 1;
 }
 
+// Tables of the levels after g (set j), requested with level g's own while their sum
+// stays within kPrefetchBytes, so that the small early levels share one flush (one pair
+// of table launches) instead of a flush each.  Requests only: a table over budget is
+// left out here as it is at its own level.
+constexpr size_t kPrefetchBytes = 64ull << 20;
+
+int prefetch_tables(mdist_code *c, int j, int g) {
+    const DeviceRows &dr = c->rows[(size_t)j];
+    size_t total = 0;
+    for (int g2 = g + 1; g2 <= c->k; ++g2) {
+        EnumParams q{};
+        if (!mdist::plan_level(c->k, g2, dr.nwords, q)) return MDIST_OK;
+        std::vector<std::pair<mdist::GramSide, mdist::GramSide>> parts;
+        size_t bytes = 0;
+        mdist::GramSide A[mdist::kMaxGramBlocks], Bs[mdist::kMaxGramBlocks];
+        for (int b = 0; b < q.nblocks; ++b) {
+            const int np = gram_block_parts(c->opt.tensor_cores, q.k1, q.k2, q.blocks[b],
+                                            mdist::kMaxGramBlocks - (int)parts.size(), A, Bs);
+            for (int i = 0; i < np; ++i) {
+                mdist::GramSide a = A[i], bs = Bs[i];
+                if (bs.n > a.n) std::swap(a, bs);  // as add_gram_block: B is the smaller side
+                bytes += (size_t)(a.n + bs.n) * (size_t)dr.nwords * sizeof(uint32_t) +
+                         mdist::gram_expanded_bytes(dr.nwords, bs.n);
+                parts.push_back({a, bs});
+            }
+        }
+        if (total + bytes > kPrefetchBytes) return MDIST_OK;
+        total += bytes;
+        for (const auto &pr : parts) {
+            const void *t = nullptr;
+            int rc = side_table(c, j, pr.first, false, &t);
+            if (rc == MDIST_OK) rc = side_table(c, j, pr.second, false, &t);
+            if (rc == MDIST_OK && t) rc = side_table(c, j, pr.second, true, &t);
+            if (rc != MDIST_OK) return rc;
+        }
+    }
+    return MDIST_OK;
+}
+
 // The tensor-core part of unit p (set j): gram_block_parts of every product block,
 // with its tables; a block any of whose tables is over budget stays on the ALU kernel
 // as a whole.  covered[b] marks the blocks handled there.
@@ -332,6 +479,10 @@ int gram_plan(mdist_code *c, int j, const EnumParams &p, std::vector<mdist::Gram
         }
         if (all) covered[b] = true;
         else out.resize(mark);  // a table over budget: the whole block stays on the ALU kernel
+    }
+    if (c->pend_j == j) {  // tables are built for this level: add the next levels' small ones
+        const int rc = prefetch_tables(c, j, p.g);
+        if (rc != MDIST_OK) return rc;
     }
     return flush_tables(c);
 }
@@ -458,8 +609,8 @@ void mdist_free(mdist_code *c) {
     dev_release(c, c->d_slot);
     dev_release(c, c->d_hist);
     dev_release(c, c->d_wave);
-    if (c->h_wave) cudaFreeHost(c->h_wave);
-    if (c->h_slot) cudaFreeHost(c->h_slot);
+    pinned_put(c->h_wave, sizeof(UnitSlot) * ((size_t)c->wave_cap + 1), c->pinned_ctx);
+    pinned_put(c->h_slot, sizeof(UnitSlot), c->pinned_ctx);
     for (cudaEvent_t e : c->tc_ev) cudaEventDestroy(e);
     if (c->ev0) cudaEventDestroy(c->ev0);
     if (c->ev1) cudaEventDestroy(c->ev1);
@@ -502,7 +653,7 @@ int mdist_prepare(const uint64_t *G, int n, int k, int words_per_row, const mdis
         return MDIST_ECUDA;
     }
     if (cudaEventCreate(&c->ev0) != cudaSuccess || cudaEventCreate(&c->ev1) != cudaSuccess ||
-        cudaMallocHost((void **)&c->h_slot, sizeof(UnitSlot)) != cudaSuccess) {
+        !(c->h_slot = (UnitSlot *)pinned_get(sizeof(UnitSlot), &c->pinned_ctx))) {
         mdist_free(c);
         return MDIST_ECUDA;
     }
@@ -511,10 +662,13 @@ int mdist_prepare(const uint64_t *G, int n, int k, int words_per_row, const mdis
     c->wave_cap = c->m * (k + 1);
     c->d_wave = (UnitSlot *)dev_alloc(c, sizeof(UnitSlot) * ((size_t)c->wave_cap + 1));
     if (!c->d_wave) { mdist_free(c); return MDIST_ENOMEM; }
-    if (cudaMallocHost((void **)&c->h_wave, sizeof(UnitSlot) * ((size_t)c->wave_cap + 1)) != cudaSuccess) {
+    unsigned long long wave_ctx = 0;
+    c->h_wave = (UnitSlot *)pinned_get(sizeof(UnitSlot) * ((size_t)c->wave_cap + 1), &wave_ctx);
+    if (!c->h_wave) {
         mdist_free(c);
         return MDIST_ECUDA;
     }
+    if (wave_ctx != c->pinned_ctx) c->pinned_ctx = 0;  // both blocks must belong to one context
     c->d_rows.assign((size_t)c->m, nullptr);
     for (int j = 0; j < c->m; ++j) {
         const DeviceRows &dr = c->rows[(size_t)j];
@@ -1061,6 +1215,31 @@ int mdist_debug_gram_plan(int k, int g, int nwords, int tensor_cores, int *npart
     }
     *nparts = n;
     return MDIST_OK;
+}
+
+int mdist_debug_side_tables(const uint32_t *rows, int k, int nwords, int n, const int *sides, uint32_t *const *outs,
+                            const uint32_t *const *lows, const int *low_t, void *stream) {
+    if (!rows || !sides || !outs || n < 1 || n > mdist::kMaxTableJobs || nwords < 1 ||
+        nwords > mdist::kGramMaxWords || k < 1 || k > 64 || (uintptr_t)rows % 4 != 0)
+        return MDIST_EINVAL;
+    std::vector<mdist::GramSide> S((size_t)n);
+    auto bad = [&](int off, int kc, int t) { return off < 0 || kc < 1 || kc > 32 || t < 0 || t > kc || off + kc > k; };
+    for (int i = 0; i < n; ++i) {
+        const int *q = sides + 6 * i;
+        if (!outs[i] || (uintptr_t)outs[i] % 16 != 0 || bad(q[0], q[1], q[2]) || (q[5] >= 0 && bad(q[3], q[4], q[5])))
+            return MDIST_EINVAL;
+        if (q[5] >= 0 && q[0] < q[3] + q[4] && q[3] < q[0] + q[1]) return MDIST_EINVAL;  // shared rows
+        if (lows && lows[i] && (!low_t || low_t[i] < 1 || low_t[i] >= q[2] || (uintptr_t)lows[i] % 16 != 0))
+            return MDIST_EINVAL;
+        S[(size_t)i] = make_side(q[0], q[1], q[2], q[3], q[4], q[5]);
+    }
+    int dev = 0, sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return MDIST_ECUDA;
+    const cudaError_t e =
+        mdist::launch_side_tables(rows, k, nwords, S.data(), outs, lows, low_t, n, sm, (cudaStream_t)stream);
+    return e == cudaSuccess ? MDIST_OK : MDIST_ECUDA;
 }
 
 }  // extern "C"

@@ -280,9 +280,9 @@ size_t batch_smem_bytes() {
 template <int NW>
 cudaError_t batch_enum_prepare(int *grid_per_sm) {
     const size_t smem = batch_smem_bytes<NW>();
-    cudaError_t e = cudaFuncSetAttribute(batch_enum<NW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = allow_dynamic_smem((const void *)batch_enum<NW>, smem);
     if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(grid_per_sm, batch_enum<NW>, kCtaThreads, smem);
+    return blocks_per_sm((const void *)batch_enum<NW>, kCtaThreads, smem, grid_per_sm);
 }
 
 template <int NW>

@@ -177,10 +177,10 @@ cudaError_t launch_variant(const EnumParams &p, int sm_count, int blocks_per_sm,
     const int hist_bins = HIST ? p.n_bits + p.base + 1 : 0;
     const size_t smem = enum_smem_bytes_nw(p.k, NW, hist_bins);
     auto kern = enum_unit_kernel<NW, GS, HIST>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = allow_dynamic_smem((const void *)kern, smem);
     if (e != cudaSuccess) return e;
     int occ = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kCtaThreads, smem);
+    e = mdist::blocks_per_sm((const void *)kern, kCtaThreads, smem, &occ);
     if (e != cudaSuccess) return e;
     if (occ < 1) return cudaErrorInvalidConfiguration;
     const int per_sm = blocks_per_sm > 0 && blocks_per_sm < occ ? blocks_per_sm : occ;

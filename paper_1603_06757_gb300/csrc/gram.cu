@@ -45,6 +45,7 @@
 // arrived).  Every wait is bounded; a timeout sets the status word, and the kernel
 // ends after its copies and MMAs have drained.
 //
+#include <algorithm>
 #include <cstdint>
 
 #include "combinatorics.cuh"
@@ -421,7 +422,7 @@ size_t gram_smem_bytes() {
 template <int NW>
 cudaError_t gram_launch_nw(const GramParams &p, int sm_count, cudaStream_t stream) {
     const size_t smem = gram_smem_bytes<NW>();
-    cudaError_t e = cudaFuncSetAttribute(gram_kernel<NW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = allow_dynamic_smem((const void *)gram_kernel<NW>, smem);
     if (e != cudaSuccess) return e;
     unsigned long long grid = (unsigned long long)sm_count;
     if (p.total_wu - p.wu_lo < grid) grid = p.total_wu - p.wu_lo;
@@ -430,14 +431,36 @@ cudaError_t gram_launch_nw(const GramParams &p, int sm_count, cudaStream_t strea
     return cudaGetLastError();
 }
 
-// Several tables in one launch: job i covers the global entries [begin[i], begin[i+1]).
-constexpr int kTableChunk = 16;  // consecutive entries a thread builds
+// Several tables in one launch.  Entry e of a side is the sum of the rows of a subset;
+// the colex rank of a t0-subset c_0 < ... < c_(t0-1) is the sum of C(c_i, i + 1), so
+// the entries whose component-0 subsets share every element but the lowest u (the
+// "top", least element c_u) and share the component-1 subset form one contiguous run
+// of C(c_u, u) entries (all C(kc0, u) when the top is empty), and entry j of a run is
+// the run's top sum XOR T[j], T the sums of the u-subsets of the component's rows in
+// colex order.  T is a table built by an earlier launch (the one-component side of
+// t = u on the same rows, read through the L2) or, with u = min(t0, 1), the
+// component's rows themselves (the 1-subsets; for t0 = 0 a zero entry), staged in
+// shared memory.  A warp task is a piece of `piece` consecutive entries: the warp
+// unranks the first, then walks the runs (tops stepped by Gosper's rule, component 1
+// stepping when the top wraps), writing each run's span with coalesced vector stores
+// of T[j] ^ top.
+constexpr int kTableThreads = 512;
+constexpr int kTableWarps = kTableThreads / 32;
+
+struct SideJob {
+    GramSide side;
+    uint32_t *out;
+    const uint32_t *low;       // T in global memory, or null: the rows (u <= 1)
+    int u;                     // elements of an entry's subset taken from T
+    uint32_t first_mod;        // the job's first task in the launch-wide numbering, mod warps
+    unsigned long long piece;  // entries per task
+    unsigned long long ntasks;
+};
 
 struct SideJobs {
     int njobs;
-    unsigned long long begin[kMaxTableJobs + 1];  // chunks of kTableChunk entries
-    GramSide side[kMaxTableJobs];
-    uint32_t *out[kMaxTableJobs];
+    uint32_t warps;  // warps of the launch
+    SideJob job[kMaxTableJobs];
 };
 
 struct ExpandJobs {
@@ -459,105 +482,189 @@ __device__ __forceinline__ int job_of(const unsigned long long (&begin)[N], int 
     return lo;
 }
 
-// out_i[e * NW ..] = the sum of the rows of entry e of side i (rows: the k rows of the set).
-// A thread takes kTableChunk consecutive entries: it unranks the first, then steps to
-// the next subset of each component in colex order (Gosper's rule; component 1 steps
-// when component 0 wraps) and XORs only the rows that changed.  J.begin counts chunks.
-// The 32 chunks of a warp are 512 consecutive entries of one table (when they lie in
-// one table and are all full): the lanes stage their sums in shared memory (lane
-// regions padded to an odd word stride, so the stores do not collide on banks) and the
-// warp writes the 2 KB x NW block with coalesced 4-byte stores.  Other warps (a table
-// boundary, the last partial chunk) store entry by entry.
-__host__ __device__ constexpr int kStageStride(int nw) { return kTableChunk * nw + 1; }
+// C(a, b) for a, b <= 32 in global memory (the table kernels stage it with coalesced
+// loads; a constant-memory copy would serialise the lanes' different addresses)
+struct Binom32 {
+    uint32_t v[kBn * kBn];
+};
+constexpr Binom32 make_binom32() {
+    Binom32 t{};
+    for (int a = 0; a < kBn; ++a) {
+        t.v[a * kBn] = 1;
+        for (int b = 1; b <= a; ++b) t.v[a * kBn + b] = t.v[(a - 1) * kBn + b - 1] + (b <= a - 1 ? t.v[(a - 1) * kBn + b] : 0u);
+    }
+    return t;
+}
+static __device__ Binom32 g_binom32 = make_binom32();
 
+// x ^= the rows of mask m (rows of NW words in shared memory)
 template <int NW>
-__global__ void side_tables_kernel(const uint32_t *rows, int k, const __grid_constant__ SideJobs J) {
+__device__ __forceinline__ void xor_rows(uint32_t (&x)[NW], const uint32_t *s_rows, unsigned long long m) {
+    while (m) {
+        const int r = __ffsll((long long)m) - 1;
+        m &= m - 1;
+        if constexpr (NW % 4 == 0) {  // 16-byte loads of the row
+#pragma unroll
+            for (int v = 0; v < NW / 4; ++v) {
+                const uint4 t = reinterpret_cast<const uint4 *>(s_rows + r * NW)[v];
+                x[4 * v] ^= t.x;
+                x[4 * v + 1] ^= t.y;
+                x[4 * v + 2] ^= t.z;
+                x[4 * v + 3] ^= t.w;
+            }
+        } else {
+#pragma unroll
+            for (int w = 0; w < NW; ++w) x[w] ^= s_rows[r * NW + w];
+        }
+    }
+}
+
+// y = the entry at src (NW words; G: read-only global memory, else shared memory)
+template <int NW, bool G>
+__device__ __forceinline__ void load_entry(uint32_t (&y)[NW], const uint32_t *src) {
+    if constexpr (NW % 4 == 0) {
+#pragma unroll
+        for (int v = 0; v < NW / 4; ++v) {
+            const uint4 t = G ? __ldg(reinterpret_cast<const uint4 *>(src) + v) : reinterpret_cast<const uint4 *>(src)[v];
+            y[4 * v] = t.x;
+            y[4 * v + 1] = t.y;
+            y[4 * v + 2] = t.z;
+            y[4 * v + 3] = t.w;
+        }
+    } else if constexpr (NW % 2 == 0) {
+#pragma unroll
+        for (int v = 0; v < NW / 2; ++v) {
+            const uint2 t = G ? __ldg(reinterpret_cast<const uint2 *>(src) + v) : reinterpret_cast<const uint2 *>(src)[v];
+            y[2 * v] = t.x;
+            y[2 * v + 1] = t.y;
+        }
+    } else {
+#pragma unroll
+        for (int w = 0; w < NW; ++w) y[w] = G ? __ldg(src + w) : src[w];
+    }
+}
+
+// dst = y ^ x (one entry of NW words, vector stores where the width allows)
+template <int NW>
+__device__ __forceinline__ void store_entry(uint32_t *dst, const uint32_t (&y)[NW], const uint32_t (&x)[NW]) {
+    if constexpr (NW % 4 == 0) {
+#pragma unroll
+        for (int v = 0; v < NW / 4; ++v)
+            reinterpret_cast<uint4 *>(dst)[v] =
+                make_uint4(y[4 * v] ^ x[4 * v], y[4 * v + 1] ^ x[4 * v + 1], y[4 * v + 2] ^ x[4 * v + 2],
+                           y[4 * v + 3] ^ x[4 * v + 3]);
+    } else if constexpr (NW % 2 == 0) {
+#pragma unroll
+        for (int v = 0; v < NW / 2; ++v)
+            reinterpret_cast<uint2 *>(dst)[v] = make_uint2(y[2 * v] ^ x[2 * v], y[2 * v + 1] ^ x[2 * v + 1]);
+    } else {
+#pragma unroll
+        for (int w = 0; w < NW; ++w) dst[w] = y[w] ^ x[w];
+    }
+}
+
+// dst[i] = src[i] ^ x for i < cnt (entries of NW words), lane-strided, four entries per
+// lane in flight while they last
+template <int NW, bool G>
+__device__ __forceinline__ void put_span(uint32_t *dst, const uint32_t *src, const uint32_t (&x)[NW], uint32_t cnt,
+                                         int lane) {
+    uint32_t i = lane;
+    for (; i + 96 < cnt; i += 128) {
+        uint32_t y0[NW], y1[NW], y2[NW], y3[NW];
+        load_entry<NW, G>(y0, src + (size_t)i * NW);
+        load_entry<NW, G>(y1, src + (size_t)(i + 32) * NW);
+        load_entry<NW, G>(y2, src + (size_t)(i + 64) * NW);
+        load_entry<NW, G>(y3, src + (size_t)(i + 96) * NW);
+        store_entry<NW>(dst + (size_t)i * NW, y0, x);
+        store_entry<NW>(dst + (size_t)(i + 32) * NW, y1, x);
+        store_entry<NW>(dst + (size_t)(i + 64) * NW, y2, x);
+        store_entry<NW>(dst + (size_t)(i + 96) * NW, y3, x);
+    }
+    for (; i < cnt; i += 32) {
+        uint32_t y[NW];
+        load_entry<NW, G>(y, src + (size_t)i * NW);
+        store_entry<NW>(dst + (size_t)i * NW, y, x);
+    }
+}
+
+// Task `task` of job R: entries [task * piece, min((task + 1) * piece, n)).  T: the u-subset
+// sums (global memory when G).  Every T index stays below C(c_u, u) <= C(kc0, u), the
+// entries of T.
+template <int NW, bool G>
+__device__ __forceinline__ void walk_task(const SideJob &R, unsigned long long task, const uint32_t *s_bn,
+                                          const uint32_t *s_rows, const uint32_t *T, int lane) {
+    const GramSide &S = R.side;
+    const int u = R.u, t0 = S.t[0], kc0 = S.kc[0], off0 = S.off[0], off1 = S.off[1];
+    const int tt = t0 - u;  // elements of a top, at positions 0 .. kc0 - u - 1 (element - u)
+    const uint32_t first_top = (1u << tt) - 1u;                // tt <= 31 (u >= 1 once t0 > 3)
+    const uint32_t last_top = first_top << (kc0 - u - tt);     // the colex-last top
+    const uint32_t whole = s_bn[kc0 * kBn + u];                // run length with an empty top
+    unsigned long long e = task * R.piece;
+    const unsigned long long e_end = e + R.piece < S.n ? e + R.piece : S.n;
+    unsigned long long e1 = S.nc == 2 ? e / S.cnt0 : 0ull;
+    // the t0-subset of entry e: its lowest u elements have rank j in T, the rest is the top
+    const uint32_t M = unrank_colex(s_bn, kc0, t0, (uint32_t)(e - e1 * S.cnt0));
+    uint32_t j = 0, lowm = 0;
+    {
+        uint32_t m = M;
+        for (int i = 0; i < u; ++i) {
+            const int c = __ffs((int)m) - 1;
+            j += s_bn[c * kBn + i + 1];
+            lowm |= 1u << c;
+            m &= m - 1;
+        }
+    }
+    uint32_t top = (M ^ lowm) >> u;
+    uint32_t m1 = S.nc == 2 ? unrank_colex(s_bn, S.kc[1], S.t[1], (uint32_t)e1) : 0u;
+    uint32_t x[NW];
+#pragma unroll
+    for (int w = 0; w < NW; ++w) x[w] = 0;
+    xor_rows<NW>(x, s_rows, ((unsigned long long)top << (u + off0)) | ((unsigned long long)m1 << off1));
+    uint32_t len = tt > 0 ? s_bn[(__ffs((int)top) - 1 + u) * kBn + u] : whole;
+    for (;;) {
+        const unsigned long long left = e_end - e;
+        const uint32_t cnt = (unsigned long long)(len - j) < left ? len - j : (uint32_t)left;
+        put_span<NW, G>(R.out + e * NW, T + (size_t)j * NW, x, cnt, lane);
+        e += cnt;
+        if (e >= e_end) break;
+        j = 0;
+        unsigned long long diff;
+        if (top != last_top) {  // the next top (tt > 0: the only top of tt = 0 is the last)
+            const uint32_t nt = next_colex(top);
+            diff = (unsigned long long)(top ^ nt) << (u + off0);
+            top = nt;
+        } else {  // the top returns to its first subset and component 1 steps
+            const uint32_t n1 = next_colex(m1);
+            diff = ((unsigned long long)(top ^ first_top) << (u + off0)) | ((unsigned long long)(m1 ^ n1) << off1);
+            top = first_top;
+            m1 = n1;
+        }
+        xor_rows<NW>(x, s_rows, diff);
+        len = tt > 0 ? s_bn[(__ffs((int)top) - 1 + u) * kBn + u] : whole;
+    }
+}
+
+// out_i[e * NW ..] = the sum of the rows of entry e of side i (rows: the k rows of the set).
+// Warp w of the launch (W warps) takes the tasks t of job i with t = w - first_i mod W.
+template <int NW>
+__global__ void __launch_bounds__(kTableThreads) side_tables_kernel(const uint32_t *rows, int k,
+                                                                      const __grid_constant__ SideJobs J) {
     __shared__ uint32_t s_bn[kBn * kBn];
     __shared__ __align__(16) uint32_t s_rows[64 * NW];
-    extern __shared__ uint32_t s_stage[];  // warps x 32 lanes x kStageStride(NW) words
-    for (int i = threadIdx.x; i < kBn * kBn; i += blockDim.x) s_bn[i] = (uint32_t)c_binom_g.v[i / kBn][i % kBn];
+    __shared__ __align__(16) uint32_t s_zero[NW];  // T of t0 = 0: the empty sum
+    for (int i = threadIdx.x; i < kBn * kBn; i += blockDim.x) s_bn[i] = g_binom32.v[i];
     for (int i = threadIdx.x; i < k * NW; i += blockDim.x) s_rows[i] = rows[i];
+    if (threadIdx.x < NW) s_zero[threadIdx.x] = 0;
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    uint32_t *stage = s_stage + (size_t)warp * 32 * kStageStride(NW);
-    auto add_rows = [&](uint32_t (&x)[NW], unsigned long long m) {
-        while (m) {
-            const int r = __ffsll((long long)m) - 1;
-            m &= m - 1;
-            if constexpr (NW % 4 == 0) {  // 16-byte loads of the row
-#pragma unroll
-                for (int v = 0; v < NW / 4; ++v) {
-                    const uint4 t = reinterpret_cast<const uint4 *>(s_rows + r * NW)[v];
-                    x[4 * v] ^= t.x;
-                    x[4 * v + 1] ^= t.y;
-                    x[4 * v + 2] ^= t.z;
-                    x[4 * v + 3] ^= t.w;
-                }
-            } else {
-#pragma unroll
-                for (int w = 0; w < NW; ++w) x[w] ^= s_rows[r * NW + w];
-            }
-        }
-    };
-    const unsigned long long total = J.begin[J.njobs];
-    const unsigned long long step = (unsigned long long)gridDim.x * blockDim.x;
-    // every lane of a warp runs the same trips (the warp-wide votes below need them all)
-    for (unsigned long long cw = blockIdx.x * (unsigned long long)blockDim.x + 32ull * warp; cw < total; cw += step) {
-        const unsigned long long c = cw + lane;
-        const bool active = c < total;
-        const int i = active ? job_of(J.begin, J.njobs, c) : J.njobs - 1;
-        const GramSide &S = J.side[i];
-        unsigned long long e = active ? (c - J.begin[i]) * kTableChunk : 0;
-        const unsigned long long e_end = active ? (e + kTableChunk < S.n ? e + kTableChunk : S.n) : 0;
-        const int i0 = __shfl_sync(0xffffffffu, i, 0);
-        const bool staged = __all_sync(0xffffffffu, active && i == i0 && e_end - e == kTableChunk);
-        uint32_t *out = J.out[i];
-        const unsigned long long e_first = e;
-        if (active) {
-            unsigned long long e0 = S.nc == 2 ? e % S.cnt0 : e;
-            uint32_t m0 = unrank_colex(s_bn, S.kc[0], S.t[0], (uint32_t)e0);
-            uint32_t m1 = S.nc == 2 ? unrank_colex(s_bn, S.kc[1], S.t[1], (uint32_t)(e / S.cnt0)) : 0u;
-            uint32_t x[NW];
-#pragma unroll
-            for (int w = 0; w < NW; ++w) x[w] = 0;
-            add_rows(x, ((unsigned long long)m0 << S.off[0]) | ((unsigned long long)m1 << S.off[1]));
-            for (int q = 0;; ++q) {
-                if (staged) {
-#pragma unroll
-                    for (int w = 0; w < NW; ++w) stage[lane * kStageStride(NW) + q * NW + w] = x[w];
-                } else {
-#pragma unroll
-                    for (int w = 0; w < NW; ++w) out[e * NW + w] = x[w];
-                }
-                if (++e >= e_end) break;
-                unsigned long long diff;
-                if (e0 + 1 < S.cnt0) {
-                    const uint32_t n0 = next_colex(m0);
-                    diff = (unsigned long long)(m0 ^ n0) << S.off[0];
-                    m0 = n0;
-                    ++e0;
-                } else {  // component 0 wraps to its first subset, component 1 steps
-                    const uint32_t n0 = S.t[0] >= 32 ? 0xFFFFFFFFu : (1u << S.t[0]) - 1u;
-                    const uint32_t n1 = next_colex(m1);
-                    diff = ((unsigned long long)(m0 ^ n0) << S.off[0]) | ((unsigned long long)(m1 ^ n1) << S.off[1]);
-                    m0 = n0;
-                    m1 = n1;
-                    e0 = 0;
-                }
-                add_rows(x, diff);
-            }
-        }
-        if (staged) {
-            __syncwarp();
-            // lane r's 16 entries are words r * 16 NW .. of the warp's block, and they sit
-            // contiguously in its staging region: copy run after run, 32 words at a time
-            uint32_t *dst = out + __shfl_sync(0xffffffffu, e_first, 0) * NW;
-#pragma unroll 4
-            for (int r = 0; r < 32; ++r)
-#pragma unroll
-                for (int i = lane; i < kTableChunk * NW; i += 32)
-                    dst[r * kTableChunk * NW + i] = stage[r * kStageStride(NW) + i];
-            __syncwarp();
+    const uint32_t W = J.warps;
+    const uint32_t w = blockIdx.x * kTableWarps + (uint32_t)warp;
+    for (int i = 0; i < J.njobs; ++i) {
+        const SideJob &R = J.job[i];
+        // this warp's first task of the job: (w - first) mod W, w < W
+        for (unsigned long long t = w >= R.first_mod ? w - R.first_mod : w + W - R.first_mod; t < R.ntasks; t += W) {
+            if (R.low) walk_task<NW, true>(R, t, s_bn, s_rows, R.low, lane);
+            else walk_task<NW, false>(R, t, s_bn, s_rows, R.u ? s_rows + R.side.off[0] * NW : s_zero, lane);
         }
     }
 }
@@ -589,11 +696,32 @@ unsigned int table_grid(unsigned long long work, int sm_count) {
 }
 
 template <int NW>
-cudaError_t side_tables_nw(const uint32_t *rows, int k, const SideJobs &J, int sm_count, cudaStream_t stream) {
-    const size_t smem = (size_t)(256 / 32) * 32 * kStageStride(NW) * sizeof(uint32_t);
-    cudaError_t e = cudaFuncSetAttribute(side_tables_kernel<NW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+cudaError_t side_tables_nw(const uint32_t *rows, int k, SideJobs &J, int sm_count, cudaStream_t stream) {
+    auto kern = side_tables_kernel<NW>;
+    int occ = 0;
+    cudaError_t e = blocks_per_sm((const void *)kern, kTableThreads, 0, &occ);
     if (e != cudaSuccess) return e;
-    side_tables_kernel<NW><<<table_grid(J.begin[J.njobs], sm_count), 256, smem, stream>>>(rows, k, J);
+    if (occ < 1) return cudaErrorInvalidConfiguration;
+    const unsigned long long most_warps = (unsigned long long)sm_count * (unsigned long long)occ * kTableWarps;
+    // pieces of one size for the launch, about 4 per warp (a small launch spreads its
+    // latency-bound walks over every SM; a large one amortises each piece's unranking)
+    unsigned long long total = 0;
+    for (int i = 0; i < J.njobs; ++i) total += J.job[i].side.n;
+    const unsigned long long piece = std::min(1ull << 20, std::max(64ull, total / (4 * most_warps)));
+    unsigned long long tasks = 0;
+    unsigned long long first[kMaxTableJobs];
+    for (int i = 0; i < J.njobs; ++i) {
+        SideJob &R = J.job[i];
+        R.piece = piece;
+        R.ntasks = (R.side.n + R.piece - 1) / R.piece;
+        first[i] = tasks;
+        tasks += R.ntasks;
+    }
+    const unsigned long long grid =
+        std::min((unsigned long long)sm_count * occ, (tasks + kTableWarps - 1) / kTableWarps);
+    J.warps = (uint32_t)(grid * kTableWarps);
+    for (int i = 0; i < J.njobs; ++i) J.job[i].first_mod = (uint32_t)(first[i] % J.warps);
+    kern<<<(unsigned int)grid, kTableThreads, 0, stream>>>(rows, k, J);
     return cudaGetLastError();
 }
 
@@ -606,15 +734,26 @@ cudaError_t expand_tables_nw(const ExpandJobs &J, int sm_count, cudaStream_t str
 }  // namespace
 
 cudaError_t launch_side_tables(const uint32_t *rows, int k, int nwords, const GramSide *sides, uint32_t *const *outs,
-                               int n, int sm_count, cudaStream_t stream) {
+                               const uint32_t *const *lows, const int *low_t, int n, int sm_count,
+                               cudaStream_t stream) {
     if (k < 1 || k > 64 || n < 0 || n > kMaxTableJobs) return cudaErrorInvalidValue;
     if (n == 0) return cudaSuccess;
+    auto has_low = [&](int i) { return lows && lows[i] && low_t; };
+    for (int i = 0; i < n; ++i) {
+        const GramSide &S = sides[i];
+        const bool ok0 = S.kc[0] <= 32 && S.t[0] <= S.kc[0] && S.off[0] + S.kc[0] <= k;
+        const bool ok1 = S.nc == 1 || (S.kc[1] <= 32 && S.t[1] <= S.kc[1] && S.off[1] + S.kc[1] <= k);
+        const bool okl = !has_low(i) || (low_t[i] >= 1 && low_t[i] < S.t[0]);
+        if ((S.nc != 1 && S.nc != 2) || !ok0 || !ok1 || !okl || !outs[i]) return cudaErrorInvalidValue;
+    }
     SideJobs J{};
     J.njobs = n;
     for (int i = 0; i < n; ++i) {
-        J.side[i] = sides[i];
-        J.out[i] = outs[i];
-        J.begin[i + 1] = J.begin[i] + (sides[i].n + kTableChunk - 1) / kTableChunk;
+        SideJob &R = J.job[i];
+        R.side = sides[i];
+        R.out = outs[i];
+        R.low = has_low(i) ? lows[i] : nullptr;
+        R.u = has_low(i) ? low_t[i] : std::min<int>(sides[i].t[0], 1);
     }
     switch (nwords) {
         case 1: return side_tables_nw<1>(rows, k, J, sm_count, stream);

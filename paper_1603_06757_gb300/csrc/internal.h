@@ -113,10 +113,14 @@ cudaError_t launch_gram_unit(const EnumParams &ep, const GramBlockSpec *blocks, 
 // Tables built together (one launch each for the packed sums and for the expansions).
 constexpr int kMaxTableJobs = 128;
 // for i < n: outs[i][e * nwords ..] = the sum of the rows (rows: all k rows of the set)
-// of entry e of sides[i]; outs[i] 16-byte aligned (rows of 2 and 4 words are stored
-// as one vector per entry)
+// of entry e of sides[i]; outs[i] 16-byte aligned (entries of 2 and 4 words are stored
+// as vectors).  lows (may be null) / lows[i] non-null: the finished table of the
+// one-component side (off0, kc0, low_t[i]) of sides[i]'s component 0 on the same rows
+// (0 < low_t[i] < t0, 16-byte aligned, written by an earlier launch on the stream), read
+// instead of building the low-subset sums in shared memory.
 cudaError_t launch_side_tables(const uint32_t *rows, int k, int nwords, const GramSide *sides, uint32_t *const *outs,
-                               int n, int sm_count, cudaStream_t stream);
+                               const uint32_t *const *lows, const int *low_t, int n, int sm_count,
+                               cudaStream_t stream);
 // bytes of the expanded operand tiles of a packed table of `count` entries
 size_t gram_expanded_bytes(int nwords, unsigned long long count);
 // for i < n: outs[i] = the operand tiles of packed[i] (counts[i] entries)
@@ -153,6 +157,17 @@ size_t enum_smem_bytes(int k, int nwords);
 
 // Host-side binomial coefficients C(a, b), a <= 64 (enum_launch.cu).
 unsigned long long binom_host(int a, int b);
+
+// Unique id of the CUDA context current on the calling thread: MDIST_OK, kNoContext when
+// no context is current yet, MDIST_ECUDA when the driver cannot be asked.
+constexpr int kNoContext = 1;
+int current_context_id(unsigned long long *id);
+
+// Kernel launch settings shared by all threads, per CUDA context: raise `func`'s
+// dynamic shared-memory limit to at least `bytes` (never lowered), and its blocks per SM
+// at `threads` threads and `smem` bytes (remembered).
+cudaError_t allow_dynamic_smem(const void *func, size_t bytes);
+cudaError_t blocks_per_sm(const void *func, int threads, size_t smem, int *occ);
 
 // Fill the product-block table of a level; false if C(k, g) >= 2^54.
 bool plan_level(int k, int g, int nwords, EnumParams &p);

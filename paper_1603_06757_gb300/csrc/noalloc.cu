@@ -28,6 +28,35 @@
 #include "internal.h"
 
 namespace mdist {
+
+using CtxGetCurrentFn = CUresult (*)(CUcontext *);
+using CtxGetIdFn = CUresult (*)(CUcontext, unsigned long long *);
+
+// Unique id of the context current on the calling thread (MDIST_OK), kNoContext when
+// none is current yet, MDIST_ECUDA when the driver calls are unavailable.  The two
+// driver entry points are fetched once, through the runtime.
+int current_context_id(unsigned long long *id) {
+    static std::once_flag once;
+    static CtxGetCurrentFn get_current = nullptr;
+    static CtxGetIdFn get_id = nullptr;
+    std::call_once(once, [] {
+        void *f0 = nullptr, *f1 = nullptr;
+        cudaDriverEntryPointQueryResult q0, q1;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f0, 12000, cudaEnableDefault, &q0) == cudaSuccess &&
+            cudaGetDriverEntryPointByVersion("cuCtxGetId", &f1, 12000, cudaEnableDefault, &q1) == cudaSuccess &&
+            q0 == cudaDriverEntryPointSuccess && q1 == cudaDriverEntryPointSuccess && f0 && f1) {
+            get_current = (CtxGetCurrentFn)f0;
+            get_id = (CtxGetIdFn)f1;
+        }
+    });
+    if (!get_current || !get_id) return MDIST_ECUDA;
+    CUcontext ctx = nullptr;
+    if (get_current(&ctx) != CUDA_SUCCESS) return MDIST_ECUDA;
+    if (!ctx) return kNoContext;
+    if (get_id(ctx, id) != CUDA_SUCCESS) return MDIST_ECUDA;
+    return MDIST_OK;
+}
+
 namespace {
 
 constexpr int kNoAllocHistBins = MDIST_NOALLOC_MAX_HIST_BINS;
@@ -78,32 +107,6 @@ std::mutex g_setup_mu;
 ContextEntry g_ctx[kMaxContexts];
 int g_nctx = 0;
 int g_next_evict = 0;
-
-using CtxGetCurrentFn = CUresult (*)(CUcontext *);
-using CtxGetIdFn = CUresult (*)(CUcontext, unsigned long long *);
-CtxGetCurrentFn g_ctx_get_current = nullptr;
-CtxGetIdFn g_ctx_get_id = nullptr;
-
-constexpr int kNoContext = 1;  // nothing current on this thread yet
-
-// Unique id of the context current on the calling thread.
-int current_context_id(unsigned long long *id) {
-    if (!g_ctx_get_current || !g_ctx_get_id) {
-        void *f0 = nullptr, *f1 = nullptr;
-        cudaDriverEntryPointQueryResult q0, q1;
-        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f0, 12000, cudaEnableDefault, &q0) != cudaSuccess ||
-            cudaGetDriverEntryPointByVersion("cuCtxGetId", &f1, 12000, cudaEnableDefault, &q1) != cudaSuccess ||
-            q0 != cudaDriverEntryPointSuccess || q1 != cudaDriverEntryPointSuccess || !f0 || !f1)
-            return MDIST_ECUDA;
-        g_ctx_get_current = (CtxGetCurrentFn)f0;
-        g_ctx_get_id = (CtxGetIdFn)f1;
-    }
-    CUcontext ctx = nullptr;
-    if (g_ctx_get_current(&ctx) != CUDA_SUCCESS) return MDIST_ECUDA;
-    if (!ctx) return kNoContext;
-    if (g_ctx_get_id(ctx, id) != CUDA_SUCCESS) return MDIST_ECUDA;
-    return MDIST_OK;
-}
 
 int noalloc_setup(int dev, void **addr, int *sms) {
     std::lock_guard<std::mutex> lock(g_setup_mu);

@@ -398,6 +398,39 @@ def test_gram_plan_rejects_bad_arguments(lib):
     assert rc == L.EINVAL
 
 
+def test_side_tables_rejects_bad_arguments(lib):
+    """Argument checks of mdist_debug_side_tables, all taken before any CUDA call (the
+    pointers are never dereferenced: every case is invalid)."""
+    def call(rows=0x1000, k=64, nw=4, sides=((0, 32, 3, 0, 0, -1),), outs=None, lows=None, low_t=None):
+        flat = np.ascontiguousarray(np.asarray(sides, dtype=np.int32).reshape(-1))
+        outs = outs if outs is not None else [0x2000] * len(sides)
+        arr = (ctypes.c_void_p * max(len(outs), 1))(*outs)
+        return lib.mdist_debug_side_tables(ctypes.c_void_p(rows), k, nw, len(sides), flat.ctypes.data_as(L.PI), arr,
+                                           lows, low_t, None)
+
+    assert call(rows=0) == L.EINVAL
+    assert call(rows=0x1002) == L.EINVAL  # rows not 4-byte aligned
+    assert call(outs=[0x2008]) == L.EINVAL  # table not 16-byte aligned
+    assert call(outs=[0]) == L.EINVAL
+    assert call(sides=()) == L.EINVAL
+    assert call(sides=[(0, 1, 0, 0, 0, -1)] * 129) == L.EINVAL
+    assert call(nw=0) == L.EINVAL and call(nw=9) == L.EINVAL
+    assert call(k=0) == L.EINVAL and call(k=65) == L.EINVAL
+    assert call(sides=((0, 33, 3, 0, 0, -1),)) == L.EINVAL  # over 32 rows
+    assert call(sides=((40, 32, 3, 0, 0, -1),)) == L.EINVAL  # past row k
+    assert call(sides=((0, 4, 5, 0, 0, -1),)) == L.EINVAL  # t > kc
+    assert call(sides=((0, 16, 2, 8, 16, 1),)) == L.EINVAL  # components share rows
+    assert call(sides=((0, 16, 2, 16, 0, 0),)) == L.EINVAL  # empty second component
+    assert call(sides=((0, 16, 2, 0, 0, -1), (0, 16, 2, 60, 8, 1))) == L.EINVAL  # one bad side of two
+    six = ((0, 32, 6, 0, 0, -1),)
+    lt = (ctypes.c_int * 1)
+    lp = (ctypes.c_void_p * 1)
+    assert call(sides=six, lows=lp(0x3000), low_t=lt(0)) == L.EINVAL  # low table of t = 0
+    assert call(sides=six, lows=lp(0x3000), low_t=lt(6)) == L.EINVAL  # low table of t >= t0
+    assert call(sides=six, lows=lp(0x3008), low_t=lt(5)) == L.EINVAL  # low table not 16-byte aligned
+    assert call(sides=six, lows=lp(0x3000), low_t=None) == L.EINVAL
+
+
 def _choice(lib, nw, nb, thr):
     g = ctypes.c_int()
     assert lib.mdist_debug_filter_choice(nw, nb, thr, ctypes.byref(g)) == 0
