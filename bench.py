@@ -437,6 +437,9 @@ def run_profile_unit(args):
     g = args.profile_unit
     with api.Code(G, n, tensor_cores=args.tensor_cores) as code:
         d = code.min_distance()["d"] if args.profile_d <= 0 else args.profile_d
+        if args.profile_tables:  # set 0's levels below g first: its tables built level by level, as in a run
+            for g2 in range(1, g):
+                code.enumerate_level(g2, 0, U=0)
         out = []
         for _ in range(2):
             torch.cuda.synchronize()
@@ -791,6 +794,8 @@ def main():
     ap.add_argument("--tensor-cores", type=int, choices=[0, 1, 2], default=0,
                     help="0: large product blocks on the tcgen05 enumerator, 1: ALU enumerator only, 2: all blocks")
     ap.add_argument("--profile-unit", type=int, default=0, help="run one unit of this level (profiling)")
+    ap.add_argument("--profile-tables", action="store_true",
+                    help="with --profile-unit: run set 0's lower levels first (tables built level by level)")
     ap.add_argument("--profile-d", type=int, default=0, help="d of the workload if known (skips the full run)")
     ap.add_argument("--profile-batch", type=int, default=0, help="run the batched engine on this many light codes")
     args = ap.parse_args()
