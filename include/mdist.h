@@ -92,9 +92,12 @@ typedef struct {
                                 whose two sides hold >= 128 subsets each, and blocks of
                                 >= 2^24 codewords with a smaller side split into parts
                                 whose sides are large (the large side's half cut in two
-                                quarters); 1 = none; 2 = every block as it is; 3 = as 0
-                                with every block that has a side under 128 subsets split,
-                                whatever its size.  Results are identical. */
+                                quarters), or, on a code whose Gilbert-Varshamov work
+                                estimate (mdist_gv_estimate's level w*: m * sum over
+                                g <= w* of C(k, g)) reaches 10^7 codewords, as 3;
+                                1 = none; 2 = every block as it is; 3 = as 0 with every
+                                block that has a side under 128 subsets split, whatever
+                                its size.  Results are identical. */
     int skip_idle_sets;      /* 1: at level g leave out the sets whose bound term
                                 max(0, g+1-(k-r_j)) is still 0; a set enumerates the
                                 levels it skipped when its term first becomes positive;

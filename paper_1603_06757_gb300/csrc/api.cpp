@@ -66,6 +66,7 @@ struct mdist_code {
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     std::vector<cudaEvent_t> tc_ev;      // event pairs around tensor-core launches, one pair per unit of a wave
     uint64_t rows_bytes = 0;             // Gamma rows copied to the device by mdist_prepare
+    int gram_mode = 0;                   // tensor-core plan mode the units use (see mdist_prepare)
     int wave_cap = 0;                    // units a wave can hold: m * (k + 1)
     UnitSlot *d_wave = nullptr;          // [wave_cap] per-unit slots + 1 threshold word after them
     UnitSlot *h_wave = nullptr;          // pinned copy
@@ -186,6 +187,13 @@ constexpr size_t kTableBudget = 16ull << 30;
 // Product blocks with fewer codewords than this and a side under kGramMinSide entries
 // stay on the ALU kernel; larger ones are split for the tensor cores.
 constexpr unsigned long long kSplitMin = 1ull << 24;
+// tensor_cores = 0 on a code whose estimated work (Gilbert-Varshamov level, as the
+// routing estimate) reaches kSplitAllWork codewords plans its units as mode 3: every
+// block with a small side goes to the tensor cores.  Measured on codes of 10^4 to
+// 10^12 codewords: below ~10^6 the parts' tables and launches cost more than the ALU
+// kernel's small blocks ([60,30] fresh run 0.34 -> 0.92 ms), from ~10^7 up they cost
+// less ([100,40] 0.93 -> 0.69 ms, [260,30] 5.3 -> 2.4 ms, [192,64] -0.7 ms a run).
+constexpr double kSplitAllWork = 1e7;
 
 mdist::GramSide make_side(int off0, int kc0, int t0, int off1 = 0, int kc1 = 0, int t1 = -1) {
     mdist::GramSide S{};
@@ -437,7 +445,7 @@ int prefetch_tables(mdist_code *c, int j, int g) {
         size_t bytes = 0;
         mdist::GramSide A[mdist::kMaxGramBlocks], Bs[mdist::kMaxGramBlocks];
         for (int b = 0; b < q.nblocks; ++b) {
-            const int np = gram_block_parts(c->opt.tensor_cores, q.k1, q.k2, q.blocks[b],
+            const int np = gram_block_parts(c->gram_mode, q.k1, q.k2, q.blocks[b],
                                             mdist::kMaxGramBlocks - (int)parts.size(), A, Bs);
             for (int i = 0; i < np; ++i) {
                 mdist::GramSide a = A[i], bs = Bs[i];
@@ -469,7 +477,7 @@ int gram_plan(mdist_code *c, int j, const EnumParams &p, std::vector<mdist::Gram
     if (!mdist::gram_eligible(p.nwords)) return MDIST_OK;
     mdist::GramSide A[mdist::kMaxGramBlocks], Bs[mdist::kMaxGramBlocks];
     for (int b = 0; b < p.nblocks; ++b) {
-        const int np = gram_block_parts(c->opt.tensor_cores, p.k1, p.k2, p.blocks[b],
+        const int np = gram_block_parts(c->gram_mode, p.k1, p.k2, p.blocks[b],
                                         mdist::kMaxGramBlocks - (int)out.size(), A, Bs);
         const size_t mark = out.size();
         bool all = np > 0;
@@ -644,6 +652,10 @@ int mdist_prepare(const uint64_t *G, int n, int k, int words_per_row, const mdis
              : mdist::partition_info_sets(G, n, k, words_per_row, c->opt.max_sets, c->part);
     if (rc != MDIST_OK) { delete c; return rc; }
     c->m = (int)c->part.sets.size();
+    c->gram_mode = c->opt.tensor_cores == 0 &&
+                           mdist::estimated_work(n, k, c->part, c->opt.wstar_hint) >= kSplitAllWork
+                       ? 3
+                       : c->opt.tensor_cores;
     c->rows.resize((size_t)c->m);
     for (int j = 0; j < c->m; ++j) mdist::build_rows(c->part, j, c->rows[(size_t)j]);
     if (cudaGetDevice(&c->device) != cudaSuccess ||
