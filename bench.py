@@ -54,10 +54,11 @@ L2_FLUSH_BYTES = 256 << 20
 # dense fp8 / bf16 tensor throughput, nominal (2.25 and 4.5 PFLOP/s per GB300)
 FP8_PER_BF16 = 2.0
 # DRAM bytes (read + write) per launch of the dominant kernel (the tensor-core
-# enumerator), from the one-launch ncu captures of levels 8-11 summarised in profiles/
-# (a timed step runs each level once per set: the mean of the four); None until
-# captured for the current kernel
-TRAFFIC_PER_LAUNCH = {"192x64": int((72.44 + 204.32 + 578.59 + 1516.26) / 4 * 1e6)}  # gram_kernel<4>
+# enumerator), from the one-launch ncu captures of levels 1-11 (set 0) summarised in
+# profiles/: a timed step runs each level once per set, 33 launches, so the mean of the
+# eleven; None until captured for the current kernel and plan
+_TRAFFIC_192x64_MB = (0.23, 0.31, 0.60, 1.43, 3.97, 10.86, 27.51, 74.36, 204.35, 578.59, 1520.36)  # levels 1..11
+TRAFFIC_PER_LAUNCH = {"192x64": int(sum(_TRAFFIC_192x64_MB) / len(_TRAFFIC_192x64_MB) * 1e6)}  # gram_kernel<4>
 
 
 def _env_int(name, default):
@@ -347,12 +348,17 @@ def run_ours(args):
     per_clk = min(POPC_PER_CLK_SM / 1.0, ALU_PER_CLK_SM / nwords)
     alu_peak = info["sm_count"] * sm_mhz * 1e6 * per_clk
     alu_ms = kernel_ms - tc_ms
-    alu_achieved = (combos - tc_combos) / (alu_ms / 1e3) if alu_ms > 0 else None
-    alu_part = {"bound": "alu", "achieved": alu_achieved / 1e9 if alu_achieved else None, "peak": alu_peak / 1e9,
-                "unit": "Gcodewords/s", "frac": alu_achieved / alu_peak if alu_achieved else None,
-                "ms_per_step": alu_ms / args.steps, "codewords_per_step": (combos - tc_combos) // args.steps,
-                "peak_basis": f"{info['sm_count']} SMs x {sm_mhz:.0f} MHz x min({POPC_PER_CLK_SM} POPC, "
-                              f"{ALU_PER_CLK_SM} ALU / {nwords} words) per clk per SM"}
+    if combos > tc_combos:
+        alu_achieved = (combos - tc_combos) / (alu_ms / 1e3) if alu_ms > 0 else None
+        alu_part = {"bound": "alu", "achieved": alu_achieved / 1e9 if alu_achieved else None, "peak": alu_peak / 1e9,
+                    "unit": "Gcodewords/s", "frac": alu_achieved / alu_peak if alu_achieved else None,
+                    "ms_per_step": alu_ms / args.steps, "codewords_per_step": (combos - tc_combos) // args.steps,
+                    "peak_basis": f"{info['sm_count']} SMs x {sm_mhz:.0f} MHz x min({POPC_PER_CLK_SM} POPC, "
+                                  f"{ALU_PER_CLK_SM} ALU / {nwords} words) per clk per SM"}
+    else:  # the default plan put every codeword of this code on the tensor cores
+        alu_part = {"codewords_per_step": 0, "other_ms_per_step": alu_ms / args.steps,
+                    "note": "no codeword on the ALU enumerator in this plan (its own line: alu_path); "
+                            "other_ms_per_step = unit event time outside the tensor-core launches"}
     alu_only = alu_path_cw / (alu_path_ms / 1e3)
     alu_path = {"value": alu_only, "unit": UNIT, "ms_per_step": alu_path_ms / alu_steps, "steps": alu_steps,
                 "wall_ms_per_step": 1e3 * alu_path_wall / alu_steps,
