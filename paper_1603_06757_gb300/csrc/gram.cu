@@ -77,16 +77,23 @@ constexpr long long kDefaultWaitPolls = 200000000ll;
 __host__ __device__ constexpr int gram_ka(int nw) { return 32 * nw; }  // bytes per operand row
 
 // A tiles per work unit: every B tile meets both in turn (two accumulators per B tile),
-// which halves the B bytes each multiply-add needs from L2; one where two would leave
-// fewer than four B stages
-__host__ __device__ constexpr int gram_ma(int nw) { return nw <= 4 ? 2 : 1; }
+// which halves the B bytes each multiply-add needs from L2
+__host__ __device__ constexpr int gram_ma(int) { return 2; }
 
-// B stages that fit beside the two A stages
-__host__ __device__ constexpr int gram_b_stages(int nw) {
-    return (kSmemOperandBudget - 2 * gram_ma(nw) * kGM * gram_ka(nw)) / (kGN * gram_ka(nw)) < 4
-               ? (kSmemOperandBudget - 2 * gram_ma(nw) * kGM * gram_ka(nw)) / (kGN * gram_ka(nw))
+// B stages that fit beside `as` A stages (at most four)
+__host__ __device__ constexpr int gram_b_fit(int nw, int as) {
+    return (kSmemOperandBudget - as * gram_ma(nw) * kGM * gram_ka(nw)) / (kGN * gram_ka(nw)) < 4
+               ? (kSmemOperandBudget - as * gram_ma(nw) * kGM * gram_ka(nw)) / (kGN * gram_ka(nw))
                : 4;
 }
+
+// A stages: two (the builder fills the next unit's A tiles while the MMAs read these)
+// where that leaves three B stages, else one (wide rows: the builder refills the A
+// tiles after the unit's last MMA, a few thousand clocks per unit of 10^5)
+__host__ __device__ constexpr int gram_a_stages(int nw) { return gram_b_fit(nw, 2) >= 3 ? 2 : 1; }
+
+// B stages that fit beside the A stages
+__host__ __device__ constexpr int gram_b_stages(int nw) { return gram_b_fit(nw, gram_a_stages(nw)); }
 
 struct GramBlock {
     GramSide a, b;               // the two sides (A: 128-row tiles, B: 256-row tiles)
@@ -171,14 +178,15 @@ __global__ void __launch_bounds__(kGramThreads, 1) gram_kernel(const __grid_cons
     constexpr int KSTEPS = KA / 32;
     constexpr int S = gram_b_stages(NW);
     constexpr int MA = gram_ma(NW);  // A tiles per stage (rows 128 h .. of the group)
+    constexpr int AS = gram_a_stages(NW);
     constexpr int A_BYTES = kGM * KA, B_BYTES = kGN * KA;
     static_assert(S >= 2, "two B stages at least");
     extern __shared__ __align__(1024) uint8_t sm[];
     uint8_t *sA0 = sm;  // stage st, tile h at sA0 + (st * MA + h) * A_BYTES
-    uint8_t *sB0 = sm + 2 * MA * A_BYTES;
+    uint8_t *sB0 = sm + AS * MA * A_BYTES;
     // barriers: 0-1 a_full, 2-3 a_empty, 4-5 acc_full, 6-7 acc_empty, 8 drain,
     //           9 .. 9+S-1 b_full, 9+S .. 9+2S-1 b_empty
-    uint64_t *bars = reinterpret_cast<uint64_t *>(sm + 2 * MA * A_BYTES + S * B_BYTES);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(sm + AS * MA * A_BYTES + S * B_BYTES);
     uint32_t *s_tmem = reinterpret_cast<uint32_t *>(bars + 20);
     volatile int *s_abort = reinterpret_cast<volatile int *>(s_tmem + 1);
     uint32_t *s_bn = reinterpret_cast<uint32_t *>(bars + 24);
@@ -220,7 +228,7 @@ __global__ void __launch_bounds__(kGramThreads, 1) gram_kernel(const __grid_cons
             unsigned long long a_tile, bt0, bt1;
             decode_wu(P, wu, b, a_tile, bt0, bt1);
             const GramBlock &B = P.blocks[b];
-            const int st = (int)(u & 1);
+            const int st = (int)(u % AS);
             uint32_t x[MA * kGM / 32][NW];
 #pragma unroll
             for (int h = 0; h < MA * kGM / 32; ++h) {
@@ -228,7 +236,7 @@ __global__ void __launch_bounds__(kGramThreads, 1) gram_kernel(const __grid_cons
 #pragma unroll
                 for (int w = 0; w < NW; ++w) x[h][w] = e < B.a.n ? B.a_tab[e * NW + w] : 0u;
             }
-            if (!mbar_wait(bar(A_EMPTY + st), (uint32_t)(((u >> 1) & 1) ^ 1), P.max_wait)) { fail(); break; }
+            if (!mbar_wait(bar(A_EMPTY + st), (uint32_t)(((u / AS) & 1) ^ 1), P.max_wait)) { fail(); break; }
 #pragma unroll
             for (int h = 0; h < MA * kGM / 32; ++h)  // group row lane + 32 h: tile h / 4, row lane + 32 (h % 4)
                 write_row<NW>(sA0 + (st * MA + h / (kGM / 32)) * A_BYTES, lane + 32 * (h % (kGM / 32)), x[h], 32 * NW);
@@ -273,8 +281,8 @@ __global__ void __launch_bounds__(kGramThreads, 1) gram_kernel(const __grid_cons
                 int b;
                 unsigned long long a_tile, bt0, bt1;
                 decode_wu(P, wu, b, a_tile, bt0, bt1);
-                const int st = (int)(u & 1);
-                if (!mbar_wait(bar(A_FULL + st), (uint32_t)((u >> 1) & 1), P.max_wait)) { fail(); break; }
+                const int st = (int)(u % AS);
+                if (!mbar_wait(bar(A_FULL + st), (uint32_t)((u / AS) & 1), P.max_wait)) { fail(); break; }
                 bool ok = true;
                 for (unsigned long long bt = bt0; bt < bt1 && ok; ++bt, ++t) {
                     const int s = (int)(t % S);
@@ -413,7 +421,7 @@ __global__ void __launch_bounds__(kGramThreads, 1) gram_kernel(const __grid_cons
 template <int NW>
 size_t gram_smem_bytes() {
     constexpr int KA = gram_ka(NW);
-    const size_t need = 2 * (size_t)gram_ma(NW) * kGM * KA + (size_t)gram_b_stages(NW) * kGN * KA +
+    const size_t need = (size_t)gram_a_stages(NW) * gram_ma(NW) * kGM * KA + (size_t)gram_b_stages(NW) * kGN * KA +
                         24 * sizeof(uint64_t) +
                         sizeof(uint32_t) * (size_t)(kBn * kBn);
     return need < (size_t)(120 << 10) ? (size_t)(120 << 10) : need;
