@@ -119,3 +119,22 @@ def test_split_blocks_default_mode_vs_oracle(api, g, j):
         assert key == (want["min_w"], g, j, want["min_rank"])
         U2, key2, _ = c.enumerate_level(g, j, U=want["min_w"] - 1)
         assert key2 is None and U2 == want["min_w"] - 1
+
+
+@pytest.mark.parametrize("n,k,seed,g,all_tc", [(192, 64, 8, 5, True), (260, 30, 9, 6, True), (60, 30, 1, 5, False)])
+def test_default_plan_follows_the_code_size(api, n, k, seed, g, all_tc):
+    """tensor_cores = 0 puts every block of a level on the tensor cores on a code whose
+    Gilbert-Varshamov work estimate reaches 10^7 codewords ([192,64], [260,30]); a
+    small code ([60,30]: about 10^5) keeps its small-side blocks on the ALU kernel.
+    Either way the unit's key and count equal the ALU-only run's."""
+    G = synth.random_systematic(n, k, seed)
+    with api.Code(G, n) as c:
+        U, key, combos = c.enumerate_level(g, 0, U=n)
+        tc = c.level_counters()["tc_combos"]
+    with api.Code(G, n, tensor_cores=1) as c1:
+        U1, key1, combos1 = c1.enumerate_level(g, 0, U=n)
+    assert (U, key, combos[0]) == (U1, key1, combos1[0]) and combos[0] == math.comb(k, g)
+    if all_tc:
+        assert tc == math.comb(k, g)
+    else:
+        assert tc < math.comb(k, g)
