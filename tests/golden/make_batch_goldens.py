@@ -16,7 +16,10 @@ else). Every stored value comes from the oracle's ``min_distance`` output (Alg. 
 level check): d, the witness key (weight, g, j, lexicographic rank), message, witness,
 last unit and final bound. The codes run in a pool of single-threaded processes.
 
-Usage:  python tests/golden/make_batch_goldens.py [--procs P] [--cap C] [--limit N]
+``--sample N`` writes instead ``oracle_batch_4096_sample.txt``: a seeded sample of N of
+the heavier codes, those with an estimate above the cap and at most ten times it.
+
+Usage:  python tests/golden/make_batch_goldens.py [--procs P] [--cap C] [--limit N] [--sample N]
 """
 
 from __future__ import annotations
@@ -26,6 +29,7 @@ import math
 import multiprocessing as mp
 import os
 import platform
+import random
 import sys
 import time
 
@@ -69,24 +73,32 @@ def main() -> None:
     ap.add_argument("--procs", type=int, default=os.cpu_count() or 1)
     ap.add_argument("--limit", type=int, default=0, help="only the first N light codes (a trial run)")
     ap.add_argument("--cap", type=float, default=CAP, help="largest Gilbert-Varshamov work estimate kept")
+    ap.add_argument("--sample", type=int, default=0, help="a seeded sample of N codes in (cap, 10 cap] instead")
     args = ap.parse_args()
     todo = []
     for i, s in enumerate(synth.batch_specs(COUNT, K_LO, K_HI, NMUL_LO, NMUL_HI, seed=SEED, seed_base=SEED_BASE)):
         ranks = [int(x) for x in oracle.partition(synth.random_systematic(s.n, s.k, s.seed), s.n)["ranks"]]
-        if gv_work(s.n, s.k, ranks) <= args.cap:
+        w = gv_work(s.n, s.k, ranks)
+        if (w <= args.cap) if not args.sample else (args.cap < w <= 10 * args.cap):
             todo.append((i, s.n, s.k, s.seed))
+    if args.sample:  # a seeded choice among the heavier codes, in index order
+        rng = random.Random(SEED)
+        todo = sorted(rng.sample(todo, min(args.sample, len(todo))))
     if args.limit:
         todo = todo[: args.limit]
     t0 = time.time()
     with mp.get_context("spawn").Pool(args.procs) as pool:
         rows = sorted(pool.imap_unordered(_one, todo, chunksize=4))
     secs = time.time() - t0
-    name = "oracle_batch_4096.txt" if not args.limit else "oracle_batch_trial.txt"
+    name = ("oracle_batch_4096_sample.txt" if args.sample
+            else "oracle_batch_4096.txt" if not args.limit else "oracle_batch_trial.txt")
     path = os.path.join(HERE, name)
     head = [
         "# Oracle results (Alg. 1, level check) of the light codes of the batched workload:",
         f"# synth.batch_specs({COUNT}, {K_LO}, {K_HI}, {NMUL_LO}, {NMUL_HI}, seed={SEED}, seed_base={SEED_BASE}),",
-        f"# the {len(todo)} codes whose Gilbert-Varshamov work estimate is <= {args.cap:.0e}.",
+        (f"# a seeded sample of {len(todo)} codes whose Gilbert-Varshamov work estimate is in"
+         f" ({args.cap:.0e}, {10 * args.cap:.0e}]." if args.sample else
+         f"# the {len(todo)} codes whose Gilbert-Varshamov work estimate is <= {args.cap:.0e}."),
         f"# Written by tests/golden/make_batch_goldens.py in {secs:.0f} s on {args.procs} processes"
         f" ({platform.machine()}).",
         "# columns: index n k seed d weight g j rank g_final j_final L_final message(hex) witness words(hex)",

@@ -3,7 +3,9 @@ one batched run with the default routing: every light code's result equals the
 oracle's stored run (`tests/golden/oracle_batch_4096.txt`, written by
 `make_batch_goldens.py` from `oracle/` only): d, the witness key, message, witness,
 last unit and final bound, with the per-unit combination counts C(k, g) up to that
-unit.  Every code, light or heavy, equals its single-code run."""
+unit; so does each code of the seeded sample of heavier ones
+(`oracle_batch_4096_sample.txt`, when written).  Every code, light or heavy, equals its
+single-code run."""
 
 import math
 import os
@@ -16,6 +18,7 @@ import synth
 pytestmark = pytest.mark.gpu
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "oracle_batch_4096.txt")
+SAMPLE = os.path.join(os.path.dirname(__file__), "golden", "oracle_batch_4096_sample.txt")
 
 
 @pytest.fixture(scope="module")
@@ -31,9 +34,9 @@ def api():
     return a
 
 
-def _golden():
+def _golden(path):
     rows = {}
-    with open(GOLDEN) as f:
+    with open(path) as f:
         for line in f:
             if line.startswith("#") or not line.strip():
                 continue
@@ -46,7 +49,10 @@ def _golden():
 
 @pytest.mark.skipif(not os.path.exists(GOLDEN), reason="oracle_batch_4096.txt not written yet")
 def test_batched_workload_against_oracle_and_single_runs(api):
-    gold = _golden()
+    gold = _golden(GOLDEN)
+    light = len(gold)
+    if os.path.exists(SAMPLE):
+        gold.update(_golden(SAMPLE))
     specs = synth.batch_specs(4096, 24, 56, 2, 3, seed=2024, seed_base=1000)
     codes = [(s.n, s.k, s.seed, synth.random_systematic(s.n, s.k, s.seed)) for s in specs]
     with api.Batch() as b:
@@ -54,7 +60,7 @@ def test_batched_workload_against_oracle_and_single_runs(api):
             b.add(G, n)
         b.run()
         got = [b.result(i) for i in range(len(codes))]
-    assert len(gold) > 2500
+    assert light > 2500
     for i, want in gold.items():
         n, k, seed, _ = codes[i]
         assert (n, k, seed) == (want["n"], want["k"], want["seed"])
