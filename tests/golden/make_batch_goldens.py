@@ -94,7 +94,8 @@ def main() -> None:
             else "oracle_batch_4096.txt" if not args.limit else "oracle_batch_trial.txt")
     path = os.path.join(HERE, name)
     head = [
-        "# Oracle results (Alg. 1, level check) of the light codes of the batched workload:",
+        "# Oracle results (Alg. 1, level check) of " + ("codes" if args.sample else "the light codes")
+        + " of the batched workload:",
         f"# synth.batch_specs({COUNT}, {K_LO}, {K_HI}, {NMUL_LO}, {NMUL_HI}, seed={SEED}, seed_base={SEED_BASE}),",
         (f"# a seeded sample of {len(todo)} codes whose Gilbert-Varshamov work estimate is in"
          f" ({args.cap:.0e}, {10 * args.cap:.0e}]." if args.sample else
